@@ -1,0 +1,242 @@
+"""Independent reference formulas used to pin the oracle (test side only).
+
+Nothing here is shared with the oracle or with the CUDA path; each function is
+a textbook result restated from its published form:
+
+* 2 -> 2 colour/spin-averaged |M|^2 (Combridge, Kripfganz, Ranft 1977; the
+  forms quoted in Ellis-Stirling-Webber, "QCD and collider physics", Table 7.1),
+* Parke-Taylor MHV amplitudes and the n <= 5 colour sum,
+* the Berends-Giele recursion with colour-ordered Feynman rules (Berends and
+  Giele, Nucl. Phys. B306 (1988) 759; rules as in Dixon, TASI 1995 lectures),
+* explicit Gell-Mann generators T = lambda/2 for brute-force colour sums,
+* rotations and z-boosts for Lorentz-invariance checks.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from functools import lru_cache
+
+import numpy as np
+
+METRIC = np.array([1.0, -1.0, -1.0, -1.0])
+
+
+def mdot(a, b):
+    return a[..., 0] * b[..., 0] - (a[..., 1:] * b[..., 1:]).sum(-1)
+
+
+def g_s(alpha_s=0.118):
+    return math.sqrt(4.0 * math.pi * alpha_s)
+
+
+# --------------------------------------------------------------- 2 -> 2 forms
+def mandelstam(mom):
+    pa, pb, p1, p2 = (mom[:, i] for i in range(4))
+    return mdot(pa + pb, pa + pb), mdot(pa - p1, pa - p1), mdot(pa - p2, pa - p2)
+
+
+def me2_gg_gg(mom, alpha_s=0.118):
+    s, t, u = mandelstam(mom)
+    g4 = g_s(alpha_s) ** 4
+    return 4.5 * g4 * (3.0 - t * u / s**2 - s * u / t**2 - s * t / u**2)
+
+
+def me2_uubar_gg(mom, alpha_s=0.118):
+    s, t, u = mandelstam(mom)
+    g4 = g_s(alpha_s) ** 4
+    return g4 * ((32.0 / 27.0) * (t * t + u * u) / (t * u) - (8.0 / 3.0) * (t * t + u * u) / s**2)
+
+
+def me2_uu_uu(mom, alpha_s=0.118):
+    s, t, u = mandelstam(mom)
+    g4 = g_s(alpha_s) ** 4
+    return g4 * ((4.0 / 9.0) * ((s * s + u * u) / t**2 + (s * s + t * t) / u**2)
+                 - (8.0 / 27.0) * s * s / (t * u))
+
+
+# ------------------------------------------------------------ all-outgoing
+def all_outgoing(mom_one):
+    """Momenta with incoming legs (0, 1) negated."""
+    k = np.array(mom_one, dtype=np.float64).copy()
+    k[:2] *= -1.0
+    return k
+
+
+def helicities(hel_index, n_ext):
+    """Physical helicities of combination hel_index (bit n_ext-1-i -> leg i)."""
+    return [1 if (hel_index >> (n_ext - 1 - i)) & 1 else -1 for i in range(n_ext)]
+
+
+def outgoing_helicities(hel_index, n_ext):
+    """Helicities in the all-outgoing convention (incoming ones flip)."""
+    h = helicities(hel_index, n_ext)
+    return [-h[0], -h[1]] + h[2:]
+
+
+# ------------------------------------------------------------- Parke-Taylor
+def parke_taylor_sq(k, order, neg):
+    """|A(order)|^2 for the MHV configuration whose two negative-helicity legs
+    (all-outgoing convention) are `neg`: s_ij^4 / |s_12 s_23 ... s_n1|,
+    normalisation Tr(T^a T^b) = delta^{ab}."""
+    i, j = neg
+    sij = mdot(k[i] + k[j], k[i] + k[j])
+    den = 1.0
+    n = len(order)
+    for a in range(n):
+        x, y = order[a], order[(a + 1) % n]
+        den *= mdot(k[x] + k[y], k[x] + k[y])
+    return sij**4 / abs(den)
+
+
+def gluon_me2_leading_colour_exact(mom_one, alpha_s=0.118, nc=3):
+    """gg -> (n-2) g for n = 4, 5: all non-vanishing helicity amplitudes are MHV
+    or anti-MHV and the leading-colour sum is exact there, so
+    sum |M|^2 = g^{2n-4} N^{n-2} (N^2-1) sum_{sigma in S_{n-1}} sum_hel |A(1,sigma)|^2,
+    averaged by 1/4 * 1/64."""
+    k = all_outgoing(mom_one)
+    n = k.shape[0]
+    assert n in (4, 5)
+    tot = 0.0
+    for rest in itertools.permutations(range(1, n)):
+        order = (0,) + rest
+        s = 0.0
+        for neg in itertools.combinations(range(n), 2):
+            s += parke_taylor_sq(k, order, neg)
+        if n == 5:
+            s *= 2.0  # anti-MHV configurations (two positive helicities)
+        tot += s
+    g = g_s(alpha_s)
+    return g ** (2 * n - 4) * nc ** (n - 2) * (nc * nc - 1) * tot / 256.0
+
+
+# ------------------------------------------------------- polarisation vectors
+def transverse_pair(kvec):
+    """Right-handed orthonormal (e1, e2) with e1 x e2 = k_hat, built from a
+    fixed reference axis (a different gauge from the oracle's)."""
+    kh = kvec / np.linalg.norm(kvec)
+    ref = np.array([0.3, 0.5, 0.8]) / np.linalg.norm([0.3, 0.5, 0.8])
+    e1 = np.cross(ref, kh)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(kh, e1)
+    return e1, e2
+
+
+def polarisation(p, lam, outgoing):
+    """eps^mu(p, lam) (upper index); conjugated for an outgoing gluon."""
+    e1, e2 = transverse_pair(p[1:])
+    v = (e1 + 1j * lam * e2) / math.sqrt(2.0)
+    eps = np.concatenate([[0.0 + 0j], v])
+    return np.conj(eps) if outgoing else eps
+
+
+# ------------------------------------------------------------ Berends-Giele
+def _v3(P, Q, a, b):
+    """Colour-ordered three-vertex contracted with upper-index currents a (momentum
+    P outgoing into it) and b (momentum Q), giving an upper-index vector:
+    V3 = (i/sqrt2) [ g^{nu rho}(P-Q)^mu + 2 g^{rho mu} Q^nu - 2 g^{mu nu} P^rho ]."""
+    ab = mdot(a, b)
+    return (1j / math.sqrt(2.0)) * (ab * (P - Q) + 2.0 * mdot(Q, a) * b - 2.0 * mdot(P, b) * a)
+
+
+def _v4(a, b, c):
+    """Colour-ordered four-vertex: (i/2)[2 g^{mu rho} g^{nu sigma} - g^{mu nu} g^{rho sigma}
+    - g^{mu sigma} g^{nu rho}] contracted with a (nu), b (rho), c (sigma)."""
+    return (1j / 2.0) * (2.0 * mdot(a, c) * b - mdot(b, c) * a - mdot(a, b) * c)
+
+
+def bg_amplitude(k, eps, order):
+    """Colour-ordered amplitude A(order) by the Berends-Giele recursion.
+
+    k: all-outgoing momenta [n, 4]; eps: external upper-index polarisation
+    vectors [n, 4]; order: tuple of leg indices.  Normalisation Tr(T T) = delta.
+    """
+    n = len(order)
+    seq = order[:-1]
+
+    def vertices(i, j):
+        """Sum of vertices joining sub-currents of seq[i..j] (no propagator)."""
+        acc = np.zeros(4, dtype=complex)
+        for m in range(i, j):
+            Pa = sum(k[seq[x]] for x in range(i, m + 1))
+            Pb = sum(k[seq[x]] for x in range(m + 1, j + 1))
+            acc = acc + _v3(Pa, Pb, J(i, m), J(m + 1, j))
+        for m in range(i, j):
+            for l in range(m + 1, j):
+                acc = acc + _v4(J(i, m), J(m + 1, l), J(l + 1, j))
+        return acc
+
+    @lru_cache(maxsize=None)
+    def J(i, j):
+        if i == j:
+            return eps[seq[i]]
+        P = sum(k[seq[x]] for x in range(i, j + 1))
+        return (-1j / mdot(P, P)) * vertices(i, j)
+
+    # the last current is on shell: contract its vertex sum (amputated) with eps_n
+    return mdot(vertices(0, n - 2), eps[order[-1]])
+
+
+# --------------------------------------------------------------- Gell-Mann
+def gell_mann_T():
+    l = np.zeros((8, 3, 3), dtype=complex)
+    l[0][0, 1] = l[0][1, 0] = 1
+    l[1][0, 1] = -1j; l[1][1, 0] = 1j
+    l[2][0, 0] = 1; l[2][1, 1] = -1
+    l[3][0, 2] = l[3][2, 0] = 1
+    l[4][0, 2] = -1j; l[4][2, 0] = 1j
+    l[5][1, 2] = l[5][2, 1] = 1
+    l[6][1, 2] = -1j; l[6][2, 1] = 1j
+    l[7] = np.diag([1, 1, -2]) / math.sqrt(3.0)
+    return l / 2.0
+
+
+def colour_tensor(chains, legs_kind):
+    """Numerical colour tensor of a product of chains over all external colour
+    indices.  chains: list of (closed, row, col, gluon_legs); legs_kind: 'g' or
+    'q' per leg.  Returns an array with one axis per leg (8 for a gluon, 3 for a
+    quark), built by explicit index contraction with Gell-Mann generators."""
+    T = gell_mann_T()
+    letters = iter("abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ")
+    leg_letter = {i: next(letters) for i in range(len(legs_kind))}
+    operands, subs = [], []
+    for closed, row, col, gl in chains:
+        if not gl:
+            operands.append(np.eye(3))
+            subs.append(leg_letter[row] + leg_letter[col])
+            continue
+        inner = [next(letters) for _ in range(len(gl) + 1)]
+        if closed:
+            inner[-1] = inner[0]
+        else:
+            inner[0] = leg_letter[row]
+            inner[-1] = leg_letter[col]
+        for pos, g in enumerate(gl):
+            operands.append(T)
+            subs.append(leg_letter[g] + inner[pos] + inner[pos + 1])
+    out = "".join(leg_letter[i] for i in range(len(legs_kind)))
+    res = np.einsum(",".join(subs) + "->" + out, *operands, optimize=True)
+    return res
+
+
+# ------------------------------------------------------- Lorentz transforms
+def random_rotation(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([
+        [a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+        [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+        [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+
+
+def transform(mom, R=None, beta_z=0.0):
+    out = np.array(mom, dtype=np.float64).copy()
+    if R is not None:
+        out[..., 1:] = out[..., 1:] @ R.T
+    if beta_z:
+        g = 1.0 / math.sqrt(1.0 - beta_z * beta_z)
+        e, z = out[..., 0].copy(), out[..., 3].copy()
+        out[..., 0] = g * (e + beta_z * z)
+        out[..., 3] = g * (z + beta_z * e)
+    return out
