@@ -1,0 +1,367 @@
+"""Benchmark: helicity-summed |M|^2 events/s per subprocess, mixed vs FP64 path.
+
+Workload (default "3jet"): g g -> g g g, u u~ -> g g g and u u -> u u g, 2^20
+synthetic events each per GPU (RAMBO flat massless phase space in the partonic
+centre-of-mass frame, sqrt(s_hat) log-uniform in [200 GeV, 2 TeV], cuts
+pT > 20 GeV, |eta| < 2.5, Delta R > 0.4, alpha_s = 0.118).  One step evaluates
+every subprocess once.  Momenta are generated on the device before timing and
+stay resident (2^20 x 5 x 32 B = 168 MB per subprocess, larger than L2, so no
+explicit L2 flush is needed between steps).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "helicity-summed |M|^2 events/s per subprocess, mixed vs FP64 path; p50/p99"
+SEED_BASE = 0x09095257
+FP32_LANES_PER_SM = 128
+MAX_SM_MHZ = 2070.0
+
+WORKLOADS = {
+    # name: (subprocesses, events per subprocess per GPU, seed offset)
+    "3jet": ([("gg>ggg", [21, 21, 21, 21, 21], 3, 200.0, 2000.0),
+              ("uu~>ggg", [2, -2, 21, 21, 21], 3, 200.0, 2000.0),
+              ("uu>uug", [2, 2, 2, 2, 21], 3, 200.0, 2000.0)], 1 << 20, 1),
+    "2jet": ([("gg>gg", [21, 21, 21, 21], 2, 200.0, 2000.0),
+              ("uu~>gg", [2, -2, 21, 21], 2, 200.0, 2000.0)], 1 << 14, 0),
+    "4jet": ([("gg>gggg", [21] * 6, 4, 300.0, 3000.0),
+              ("uu~>gggg", [2, -2, 21, 21, 21, 21], 4, 300.0, 3000.0)], 1 << 20, 2),
+}
+WORKLOAD_TEXT = {
+    "3jet": "gg>ggg + uu~>ggg + uu>uug, 2^20 events each per GPU, sqrt(s) in [200 GeV, 2 TeV]",
+    "2jet": "gg>gg + uu~>gg, 2^14 events each per GPU, sqrt(s) in [200 GeV, 2 TeV]",
+    "4jet": "gg>gggg + uu~>gggg, 2^20 events each per GPU, sqrt(s) in [300 GeV, 3 TeV]",
+}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        self.file.close()
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The oracle (FP64 CPU, all host cores), as it stands, on a bounded sample
+    of the same workload: each step evaluates `ref_events` events of every
+    subprocess."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_0909_5257_gb300 import phasespace as ps
+    subs, n_full, seed_off = WORKLOADS[args.workload]
+    n = args.ref_events
+    procs, moms = [], []
+    for name, pdg, nf, lo, hi in subs:
+        procs.append(oracle.OracleProcess(pdg))
+        moms.append(ps.generate(ps.PhaseSpaceConfig(nf, rs_lo=lo, rs_hi=hi, seed=SEED_BASE + seed_off), n))
+    for _ in range(args.warmup):
+        for P, m in zip(procs, moms):
+            P.me2(m[: max(1, n // 16)])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for P, m in zip(procs, moms):
+            P.me2(m)
+    dt = time.perf_counter() - t0
+    ev = args.steps * n * len(subs)
+    value = ev / dt
+    cores = oracle.max_threads()
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "sample_events_per_subprocess_per_step": n},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n} events of each subprocess per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(subs, seed_off, budget_s=12.0):
+    """Oracle on the host cores over a bounded sample of the workload."""
+    import oracle
+    from paper_0909_5257_gb300 import phasespace as ps
+    tot_ev, tot_t, parts = 0, 0.0, []
+    for name, pdg, nf, lo, hi in subs:
+        P = oracle.OracleProcess(pdg)
+        probe = ps.generate(ps.PhaseSpaceConfig(nf, rs_lo=lo, rs_hi=hi, seed=SEED_BASE + seed_off), 256)
+        t0 = time.perf_counter()
+        P.me2(probe)
+        rate = 256 / max(time.perf_counter() - t0, 1e-6)
+        n = int(min(max(rate * budget_s / len(subs), 256), 1 << 16))
+        mom = ps.generate(ps.PhaseSpaceConfig(nf, rs_lo=lo, rs_hi=hi, seed=SEED_BASE + seed_off), n)
+        t0 = time.perf_counter()
+        P.me2(mom)
+        dt = time.perf_counter() - t0
+        tot_ev += n
+        tot_t += dt
+        parts.append(f"{name}: {n} events in {dt:.1f} s")
+    return {"value": tot_ev / tot_t, "unit": "events/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": "; ".join(parts)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="3jet", choices=sorted(WORKLOADS))
+    ap.add_argument("--ref-events", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_0909_5257_gb300 import mea
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    subs, n, seed_off = WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream()
+    procs, moms, outs, flags = [], [], [], []
+    for name, pdg, nf, lo, hi in subs:
+        P = mea.Process(pdg)
+        m = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
+        # weak scaling: every rank evaluates its own slice of the event stream
+        mea.generate_phase_space(nf, n, m, first_event=rank * n, seed=SEED_BASE + seed_off, rs_lo=lo, rs_hi=hi)
+        procs.append(P)
+        moms.append(m)
+        outs.append(torch.empty(n, dtype=torch.float64, device="cuda"))
+        flags.append(torch.empty(n, dtype=torch.uint8, device="cuda"))
+    torch.cuda.synchronize()
+
+    def step(prec, ev_pairs=None):
+        for i, P in enumerate(procs):
+            if ev_pairs is not None:
+                ev_pairs[i][0].record(stream)
+            P.evaluate(moms[i], outs[i], precision=prec, flags=flags[i], stream=stream)
+            if ev_pairs is not None:
+                ev_pairs[i][1].record(stream)
+
+    def timed(prec, steps):
+        for _ in range(args.warmup):
+            step(prec)
+        barrier()
+        per = [[] for _ in procs]
+        pairs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in procs] for _ in range(steps)]
+        l0 = mea.kernel_launch_count()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s in range(steps):
+            step(prec, pairs[s])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        launches = mea.kernel_launch_count() - l0
+        ms = t0.elapsed_time(t1)
+        for s in range(steps):
+            for i in range(len(procs)):
+                per[i].append(pairs[s][i][0].elapsed_time(pairs[s][i][1]))
+        return max_over_ranks(ms) / steps, per, launches
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms_mixed, per_mixed, launches = timed(mea.PREC_MIXED, args.steps)
+    clocks = sampler.stop()
+    mixed_out = [o.clone() for o in outs]
+    mixed_flags = [f.clone() for f in flags]
+
+    fp64 = None
+    if not args.no_fp64:
+        ms64, per64, _ = timed(mea.PREC_FP64, args.steps)
+        fp64 = {"value": ws * n * len(procs) / (ms64 * 1e-3), "unit": "events/s", "ms_per_step": ms64}
+    fp64_out = [o.clone() for o in outs]
+
+    per_sub = {}
+    for i, (name, pdg, nf, lo, hi) in enumerate(subs):
+        info = procs[i].info
+        ms_i = statistics.median(per_mixed[i])
+        d = {"mixed_events_per_s": n / (ms_i * 1e-3), "diagrams": info["n_diagrams"], "colours": info["n_colour"],
+             "helicities": info["n_hel_nonzero"],
+             "flagged_fraction": float((mixed_flags[i] != 0).float().mean().item())}
+        if fp64 is not None:
+            d["fp64_events_per_s"] = n / (statistics.median(per64[i]) * 1e-3)
+            rel = (mixed_out[i] / fp64_out[i] - 1.0).abs()
+            d["mixed_vs_fp64_rel_err_median"] = float(rel.median().item())
+            d["mixed_vs_fp64_rel_err_max"] = float(rel.max().item())
+            d["mixed_vs_fp64_rel_err_p99"] = float(torch.quantile(rel.float(), 0.99).item())
+        per_sub[name] = d
+
+    # roofline of the dominant kernel: the fused amplitude + colour kernel of the
+    # most expensive subprocess, FP32 pipe (ALU-bound), algorithmic FLOPs per launch
+    cost = [procs[i].info["n_hel_nonzero"] * (procs[i].info["flops_per_hel"] + procs[i].info["colour_flops_per_hel"])
+            for i in range(len(procs))]
+    dom = int(np.argmax([c * statistics.median(per_mixed[i]) for i, c in enumerate(cost)]))
+    ms_dom = statistics.mean(per_mixed[dom])
+    flops_launch = n * cost[dom]
+    achieved = flops_launch / (ms_dom * 1e-3) / 1e12
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = n_sms * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(subs[dom][0], {}).get("bytes_per_event")
+            traffic = None if traffic is None else traffic * n
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic,
+                "kernel": f"amp_kernel<float> ({subs[dom][0]}, incl. FP64 re-evaluation launch)",
+                "peak_note": f"derived: {n_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x {MAX_SM_MHZ:.0f} MHz"}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if rank == 0 or ws > 1:
+        host = [m.cpu().numpy() for m in moms]
+        for P, h in zip(procs, host):
+            P.evaluate_host(h[: 1 << 12], precision=mea.PREC_MIXED)
+        barrier()
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            for P, h in zip(procs, host):
+                P.evaluate_host(h, precision=mea.PREC_MIXED)
+        dt = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": ws * n * len(procs) * e2e_steps / dt, "unit": "events/s",
+               "h2d_bytes_per_step": int(sum(h.nbytes for h in host)),
+               "d2h_bytes_per_step": int(sum(h.shape[0] * 9 for h in host)), "steps": e2e_steps}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = _peaks()
+    out = {
+        "metric": METRIC,
+        "value": ws * n * len(procs) / (ms_mixed * 1e-3),
+        "unit": "events/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_mixed,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 amplitudes (two-sum colour amplitudes) + f64 prep/re-evaluation",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "events_per_subprocess_per_gpu": n,
+                   "l2": "inputs larger than L2 (no flush)", "alpha_s": 0.118},
+        "per_subprocess": per_sub,
+        "fp64": fp64,
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "peaks_source": peak_src,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(subs, seed_off)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

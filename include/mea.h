@@ -1,0 +1,187 @@
+/*
+ * mea.h -- C ABI of the GB300 tree-level QCD matrix-element library
+ * (libmea.so).  "mea" = matrix-element amplitudes.
+ *
+ * What the library computes (arXiv:0909.5257, Sec. 2.1):
+ *   for every event, the helicity-summed, colour-summed tree-level squared
+ *   matrix element averaged over the initial helicities and colours,
+ *     me2 = 1/4 sum_lambda sum_{alpha,beta} J_alpha N_{alpha beta} J_beta^*,
+ *   with J_alpha the colour amplitudes of Eq. (color-amplitude), built from the
+ *   Feynman-diagram sum of Eq. (matrix-element) with HELAS-style wavefunction,
+ *   vertex and off-shell-current functions (Sec. 4), and N the colour matrix of
+ *   Eq. (color-matrix) (which already holds 1/(n_a n_b)).  No identical-
+ *   particle factor and no flux factor are applied (they belong on the phase
+ *   space, Sec. 2.1).
+ *
+ * Supported processes: massless QCD with gluons (PDG 21) and light quarks
+ * (PDG 1..5, antiquarks negative), at most two quark lines, 4 <= n_ext <= 7,
+ * e.g. g g -> n g, u u~ -> n g, u u -> u u + n g.
+ *
+ * Conventions.
+ *   - Momenta: double[n_events][n_ext][4] = (E, px, py, pz) in GeV, legs ordered
+ *     (incoming a, incoming b, outgoing 1..n).  Partons are massless.
+ *   - Helicities are physical helicities +-1 of each parton.
+ *   - Every entry point is host-callable and thread-safe for distinct handles.
+ *     Device pointers are CUDA device memory of the current device; "stream"
+ *     is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Work on device buffers is stream-ordered and asynchronous: a call returns
+ *     after enqueueing; results are valid once the stream reaches that point.
+ *   - Ownership: the caller owns every buffer it passes; the library owns the
+ *     process tables, colour matrices and its scratch memory (per process
+ *     handle) and frees them in mea_destroy_process.
+ *   - Errors: every call returns a mea_status; nothing is thrown across the ABI.
+ *     On failure mea_last_error() gives a thread-local message.  A CUDA launch or
+ *     runtime failure maps to MEA_E_CUDA.  Invalid arguments are detected on the
+ *     host before anything is enqueued (MEA_E_ARG).
+ */
+#ifndef MEA_H
+#define MEA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mea_process_s *mea_process_t;
+
+typedef enum {
+  MEA_OK = 0,
+  MEA_E_ARG = -1,          /* invalid argument */
+  MEA_E_UNSUPPORTED = -2,  /* process or mode outside what the library covers */
+  MEA_E_NOMEM = -3,        /* host or device allocation failed */
+  MEA_E_CUDA = -4,         /* CUDA runtime error */
+  MEA_E_TIMEOUT = -5,      /* a bounded wait expired */
+  MEA_E_REJECTED = -6      /* admission control refused the request */
+} mea_status;
+
+/* Which helicity combinations are summed. */
+typedef enum {
+  MEA_HEL_SUM_NONZERO = 0, /* only those allowed by the massless helicity
+                              selection rules (the others vanish identically) */
+  MEA_HEL_SUM_ALL = 1,     /* all 2^n_ext combinations */
+  MEA_HEL_GIVEN = 2        /* one combination per event, given in hel_dev
+                              (int8 [n_events][n_ext], entries +1/-1); the
+                              result is that combination's colour-summed,
+                              colour-averaged |M|^2 times 1/4 (the paper's
+                              sampled-helicity mode, Sec. 3.2 step 2) */
+} mea_hel_mode;
+
+/* Arithmetic of the amplitude and colour stages. */
+typedef enum {
+  MEA_PREC_FP64 = 0,   /* everything in FP64 */
+  MEA_PREC_MIXED = 1   /* FP32 amplitudes with compensated (two-sum) colour-
+                          amplitude accumulation; colour sum on the tensor
+                          cores (FP16 hi/lo split of J against the exact
+                          integer colour matrix, FP32 accumulate) or on FP32
+                          CUDA cores for small colour bases; events whose
+                          error indicator exceeds flag_threshold are
+                          re-evaluated in FP64 when reeval_fp64 != 0 */
+} mea_prec_mode;
+
+typedef struct {
+  double alpha_s;        /* strong coupling, g = sqrt(4 pi alpha_s); <= 0 -> 0.118 */
+  double flag_threshold; /* relative error indicator above which an event is
+                            flagged in MEA_PREC_MIXED; <= 0 -> 1e-5 */
+  int reeval_fp64;       /* 1: re-evaluate flagged events in FP64 (default) */
+  int colour_mode;       /* 0 auto, 1 CUDA-core colour sum, 2 tensor-core GEMM */
+} mea_options;
+
+/* Per-event flag bits written to flags_dev. */
+#define MEA_FLAG_REEVALUATED 0x01u  /* result comes from the FP64 re-evaluation */
+#define MEA_FLAG_NONFINITE   0x02u  /* a non-finite value was met */
+#define MEA_FLAG_CANCEL      0x04u  /* error indicator above flag_threshold */
+
+typedef struct {
+  int n_ext;              /* external partons */
+  int n_diagrams;         /* Feynman diagrams (a gggg vertex counts three times,
+                             once per colour structure, as in Table 1) */
+  int n_colour;           /* colour basis vectors (Table 1) */
+  int n_hel_nonzero;      /* helicity combinations kept by the selection rules */
+  int n_currents;         /* off-shell currents in the shared current graph */
+  int n_ops;              /* operations in the per-(event,helicity) program */
+  int n_slots;            /* wavefunction slots the program needs at once */
+  int colour_denominator_log2; /* unused (0) */
+  int64_t cf_denominator; /* N = K / cf_denominator with K integer */
+  int64_t cf_max_abs_numerator; /* max |K| */
+  double flops_per_hel;   /* algorithmic FLOPs of the amplitude stage per
+                             (event, helicity): wavefunctions, vertices,
+                             currents and colour-amplitude accumulation */
+  double colour_flops_per_hel; /* 4 m^2: FLOPs of the colour quadratic form */
+} mea_process_info_t;
+
+/* ---- process handles ---------------------------------------------------- */
+
+/* Build the process g(pdg[0]) g(pdg[1]) -> pdg[2..n_ext-1]: enumerate its tree
+ * diagrams (Sec. 2.1, Table 1), build the shared off-shell-current program,
+ * the colour decomposition onto the Table 1 basis and the exact colour matrix
+ * of Eq. (color-matrix); upload everything to the current device.
+ * opts may be NULL (defaults).  *out receives the handle. */
+mea_status mea_create_process(const int *pdg, int n_ext, const mea_options *opts,
+                              mea_process_t *out);
+
+/* Same as mea_create_process but builds the host-side tables only and touches
+ * no GPU: the handle answers mea_process_info, mea_colour_matrix and
+ * mea_helicities (for planning and inspection); mea_evaluate on it returns
+ * MEA_E_UNSUPPORTED. */
+mea_status mea_create_process_host_only(const int *pdg, int n_ext, const mea_options *opts,
+                                        mea_process_t *out);
+
+mea_status mea_process_info(mea_process_t proc, mea_process_info_t *info);
+
+/* Exact colour matrix: num[m*m] integers K with N = K / *den.  Host buffers. */
+mea_status mea_colour_matrix(mea_process_t proc, int64_t *num, int64_t *den);
+
+/* Helicity combinations kept by MEA_HEL_SUM_NONZERO: hel[n_hel][n_ext] (+1/-1),
+ * host buffer of capacity cap rows; *n_hel receives the count. */
+mea_status mea_helicities(mea_process_t proc, int8_t *hel, int cap, int *n_hel);
+
+mea_status mea_destroy_process(mea_process_t proc);
+
+/* ---- evaluation ----------------------------------------------------------- */
+
+/* me2_dev[n_events] (double, device) <- |M|^2 of every event.
+ * momenta_dev: device, layout above.  hel_dev: device, only for MEA_HEL_GIVEN
+ * (else NULL).  flags_dev: device uint8[n_events] or NULL.
+ * n_events may be 0 (nothing is enqueued). */
+mea_status mea_evaluate(mea_process_t proc, const double *momenta_dev, int64_t n_events,
+                        mea_hel_mode hel_mode, const int8_t *hel_dev, mea_prec_mode prec,
+                        double *me2_dev, uint8_t *flags_dev, void *stream);
+
+/* Same result through host buffers: momenta_host[n_events][n_ext][4] and
+ * me2_host[n_events] (flags_host nullable) are ordinary host memory.  The
+ * library stages them through its own pinned buffers in chunks, overlapping
+ * copies with compute on two streams, and returns when me2_host is filled
+ * (synchronous). */
+mea_status mea_evaluate_host(mea_process_t proc, const double *momenta_host, int64_t n_events,
+                             mea_prec_mode prec, double *me2_host, uint8_t *flags_host);
+
+/* ---- synthetic phase space (input generator) ------------------------------ */
+
+typedef struct {
+  uint64_t seed;
+  int n_final;          /* 2..8 */
+  double rs_lo, rs_hi;  /* sqrt(s_hat) log-uniform range, GeV */
+  double pt_min, eta_max, dr_min;
+} mea_ps_config;
+
+/* momenta_dev[n][2 + n_final][4] <- events first_event .. first_event+n-1 of
+ * the seeded generator (Philox4x32-10, RAMBO, cuts; identical to the host
+ * generator).  attempts_dev (int32[n], nullable) receives the accepted attempt
+ * index or -1.  Stream-ordered. */
+mea_status mea_generate_phase_space(const mea_ps_config *cfg, uint64_t first_event, int64_t n,
+                                    double *momenta_dev, int32_t *attempts_dev, void *stream);
+
+/* ---- diagnostics ------------------------------------------------------------ */
+
+const char *mea_last_error(void);
+
+/* Number of kernels this library has launched in this process (all devices). */
+uint64_t mea_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MEA_H */

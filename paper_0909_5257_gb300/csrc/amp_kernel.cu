@@ -1,0 +1,466 @@
+// Amplitude stage: one lane per (event, helicity combination).
+//
+// A CTA owns a tile of E events x H helicity lanes.  Per tile:
+//   phase 0  FP64 preparation, shared by the helicity lanes of an event:
+//            transverse polarisation bases and helicity spinor building blocks
+//            of every leg, and for every momentum sum ("mask") used by the
+//            program its flowing-out momentum and 1/P^2 computed in FP64
+//            before the cast to the lane precision (Sec. 3.2 step 4);
+//   phase 1  every lane runs the process program (op table): external
+//            wavefunctions, shared off-shell currents, one amplitude per
+//            Feynman diagram, each amplitude added into the colour
+//            amplitudes J_alpha of its colour entries (Eq. (color-amplitude);
+//            two-sum compensated in FP32), then the colour quadratic form of
+//            Eq. (color-averaged-amplitude) with the integer colour matrix;
+//   phase 2  the helicity sum of each event in fixed order, x 1/4, written to
+//            me2 together with the event flags.
+// Wavefunction slots and colour amplitudes live in shared memory in
+// [item][component][lane] order, so consecutive lanes touch consecutive words.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <type_traits>
+
+#include "../../include/mea.h"
+#include "heget.cuh"
+#include "kernels.h"
+
+namespace mea {
+
+uint64_t& launch_counter() {
+  static uint64_t c = 0;
+  return c;
+}
+
+namespace {
+
+constexpr int kMaxThreads = 512;
+
+union OpWords {
+  int4 v[2];
+  Op op;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+template <typename R>
+__device__ __forceinline__ W4<R> ld_slot(const R* slots, int s, int L, int t) {
+  const R* b = slots + (size_t)s * 8 * L + t;
+  W4<R> w;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    w.c[k].r = b[(2 * k) * L];
+    w.c[k].i = b[(2 * k + 1) * L];
+  }
+  return w;
+}
+template <typename R>
+__device__ __forceinline__ void st_slot(R* slots, int s, int L, int t, const W4<R>& w) {
+  R* b = slots + (size_t)s * 8 * L + t;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    b[(2 * k) * L] = w.c[k].r;
+    b[(2 * k + 1) * L] = w.c[k].i;
+  }
+}
+
+// FP64 preparation of one leg or one mask row of one event.
+template <typename R>
+__device__ void prep_item(const DevProgram& P, const double* mom, int k, R* tab) {
+  const int n_ext = P.n_ext;
+  if (k < n_ext) {
+    const double* p = mom + 4 * k;
+    R* o = tab + 8 * k;
+    int type = P.leg_info[4 * k];
+    double px = p[1], py = p[2], pz = p[3];
+    double kt2 = px * px + py * py;
+    double kk = sqrt(kt2 + pz * pz);
+    if (type == 0) {
+      double kt = sqrt(kt2);
+      double ct, st, cp, sp;
+      if (kt > 0.0) { ct = pz / kk; st = kt / kk; cp = px / kt; sp = py / kt; }
+      else { ct = pz < 0.0 ? -1.0 : 1.0; st = 0.0; cp = 1.0; sp = 0.0; }
+      o[0] = (R)(ct * cp); o[1] = (R)(ct * sp); o[2] = (R)(-st);
+      o[3] = (R)(-sp); o[4] = (R)(cp); o[5] = (R)0;
+      o[6] = (R)0; o[7] = (R)0;
+    } else {
+      // chi_+ = (a, b) with a = sqrt((|p|+pz)/(2|p|)), b = (px + i py)/sqrt(2|p|(|p|+pz));
+      // |p| + pz evaluated without cancellation for pz < 0.
+      double apz = (pz >= 0.0) ? kk + pz : kt2 / (kk - pz);
+      double a, br, bi;
+      if (apz > 0.0) {
+        double nrm = 1.0 / sqrt(2.0 * kk * apz);
+        a = apz * nrm; br = px * nrm; bi = py * nrm;
+      } else {  // exactly along -z: chi_+ = (0, 1)
+        a = 0.0; br = 1.0; bi = 0.0;
+      }
+      o[0] = (R)sqrt(2.0 * p[0]); o[1] = (R)a; o[2] = (R)br; o[3] = (R)bi;
+      o[4] = o[5] = o[6] = o[7] = (R)0;
+    }
+  } else {
+    int row = k - n_ext;
+    uint32_t msk = P.masks[row];
+    double q[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int l = 0; l < n_ext; ++l)
+      if (msk >> l & 1u) {
+        double s = P.leg_info[4 * l + 2] ? -1.0 : 1.0;  // flowing-out momentum
+        for (int mu = 0; mu < 4; ++mu) q[mu] += s * mom[4 * l + mu];
+      }
+    R* o = tab + 8 * n_ext + 5 * row;
+    double q2 = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3];
+    for (int mu = 0; mu < 4; ++mu) o[mu] = (R)q[mu];
+    o[4] = (__popc(msk) > 1) ? (R)(1.0 / q2) : (R)0;
+  }
+}
+
+template <typename R, bool JSMEM, bool SSMEM>
+__global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, const AmpLaunch A,
+                                                   const AmpConfig C) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr bool F32 = std::is_same<R, float>::value;
+  constexpr int JW = F32 ? 4 : 2;  // FP32: hi re, hi im, lo re, lo im
+  const int L = blockDim.x;
+  const int t = threadIdx.x;
+  const int n_ext = P.n_ext, m = P.n_colour, H = C.H, E = C.E_cta;
+  const int tab_stride = 8 * n_ext + 5 * P.n_masks;
+
+  size_t off = 0;
+  R* slots;
+  if (SSMEM) {
+    slots = reinterpret_cast<R*>(smem);
+    off += (size_t)P.n_slots * 8 * L * sizeof(R);
+  } else {
+    slots = reinterpret_cast<R*>(A.slot_scratch) + (size_t)blockIdx.x * P.n_slots * 8 * L;
+  }
+  R* jam;
+  if (JSMEM) {
+    jam = reinterpret_cast<R*>(smem + off);
+    off += (size_t)m * JW * L * sizeof(R);
+  } else {
+    jam = reinterpret_cast<R*>(A.jamp_scratch) + (size_t)blockIdx.x * m * JW * L;
+  }
+  R* tab = reinterpret_cast<R*>(smem + off);
+  off += (size_t)E * tab_stride * sizeof(R);
+  off = (off + 7) & ~size_t(7);
+  double* res = reinterpret_cast<double*>(smem + off);
+  off += (size_t)L * sizeof(double);
+  float* kap = reinterpret_cast<float*>(smem + off);
+
+  const bool listed = A.event_list != nullptr;
+  const int64_t n = listed ? (int64_t)(*A.list_count) : A.n_events;
+  const int64_t n_tiles = (n + E - 1) / E;
+  const R g = (R)P.g;
+  const R gg = (R)(P.g * P.g);
+  const OpWords* ops = reinterpret_cast<const OpWords*>(P.ops);
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t ev0 = tile * E;
+    // ---- phase 0: FP64 preparation
+    const int items = n_ext + P.n_masks;
+    for (int i = t; i < E * items; i += L) {
+      int e = i / items, k = i - e * items;
+      int64_t ev = ev0 + e;
+      if (ev < n) {
+        int64_t gev = listed ? (int64_t)A.event_list[ev] : ev;
+        prep_item<R>(P, A.mom + (size_t)gev * n_ext * 4, k, tab + (size_t)e * tab_stride);
+      }
+    }
+    __syncthreads();
+
+    // ---- phase 1: one (event, helicity) per lane
+    const int e = t / H, h = t - (t / H) * H;
+    const int64_t ev = ev0 + e;
+    const bool active = (t < E * H) && (ev < n);
+    double val = 0.0;
+    float kappa = 0.f;
+    int bad = 0;
+    if (active) {
+      const int64_t gev = listed ? (int64_t)A.event_list[ev] : ev;
+      uint32_t lam_bits = 0;  // bit l set: leg l has helicity +1
+      for (int l = 0; l < n_ext; ++l) {
+        int8_t v;
+        if (A.hel_mode == 0) v = P.hel[h * n_ext + l];
+        else if (A.hel_mode == 1) v = P.hel_all[h * n_ext + l];
+        else v = A.hel_given[gev * n_ext + l];
+        if (v > 0) lam_bits |= 1u << l;
+      }
+      const R* et = tab + (size_t)e * tab_stride;
+      const R* mt = et + 8 * n_ext;
+      for (int a = 0; a < m * JW; ++a) jam[(size_t)a * L + t] = (R)0;
+      float abs_mass = 0.f;  // sum of |c A| over all colour entries (FP32 indicator)
+
+      for (int i = 0; i < P.n_ops; ++i) {
+        OpWords w;
+        w.v[0] = __ldg(&ops[i].v[0]);
+        w.v[1] = __ldg(&ops[i].v[1]);
+        const Op& op = w.op;
+        cx<R> amp;
+        bool is_amp = false;
+        switch (op.type) {
+          case OP_EXT: {
+            int l = op.leg;
+            int type = P.leg_info[4 * l], kind = P.leg_info[4 * l + 1];
+            bool in = P.leg_info[4 * l + 2] != 0;
+            const R* o = et + 8 * l;
+            W4<R> x;
+            int lam = (lam_bits >> l & 1u) ? 1 : -1;
+            if (type == 0) x = ext_gluon<R>(o, o + 3, lam, !in);
+            else x = ext_spinor<R>(o[0], o[1], mk<R>(o[2], o[3]), lam, kind);
+            st_slot(slots, op.out, L, t, x);
+            break;
+          }
+          case OP_JVV: {
+            W4<R> a = ld_slot(slots, op.in[0], L, t);
+            W4<R> b = ld_slot(slots, op.in[1], L, t);
+            const R* pa = mt + 5 * op.min[0];
+            const R* pb = mt + 5 * op.min[1];
+            W4<R> j = jvv<R>(a, b, pa, pb, mt[5 * op.mout + 4], g);
+            st_slot(slots, op.out, L, t, j);
+            break;
+          }
+          case OP_JGGG: {
+            W4<R> a = ld_slot(slots, op.in[0], L, t);
+            W4<R> b = ld_slot(slots, op.in[1], L, t);
+            W4<R> c = ld_slot(slots, op.in[2], L, t);
+            W4<R> j = jggg<R>(a, b, c, mt[5 * op.mout + 4], gg);
+            st_slot(slots, op.out, L, t, j);
+            break;
+          }
+          case OP_FVI: {
+            W4<R> f = ld_slot(slots, op.in[0], L, t);
+            W4<R> v = ld_slot(slots, op.in[1], L, t);
+            const R* pq = mt + 5 * op.mout;
+            W4<R> j = fvi<R>(f, v, pq, pq[4], g);
+            st_slot(slots, op.out, L, t, j);
+            break;
+          }
+          case OP_FVO: {
+            W4<R> f = ld_slot(slots, op.in[0], L, t);
+            W4<R> v = ld_slot(slots, op.in[1], L, t);
+            const R* pq = mt + 5 * op.mout;
+            W4<R> j = fvo<R>(f, v, pq, pq[4], g);
+            st_slot(slots, op.out, L, t, j);
+            break;
+          }
+          case OP_JIO: {
+            W4<R> f = ld_slot(slots, op.in[0], L, t);
+            W4<R> o = ld_slot(slots, op.in[1], L, t);
+            W4<R> j = jio<R>(f, o, mt[5 * op.mout + 4], g);
+            st_slot(slots, op.out, L, t, j);
+            break;
+          }
+          case OP_AVVV: {
+            W4<R> a = ld_slot(slots, op.in[0], L, t);
+            W4<R> b = ld_slot(slots, op.in[1], L, t);
+            W4<R> c = ld_slot(slots, op.in[2], L, t);
+            amp = vvv_amp<R>(a, b, c, mt + 5 * op.min[0], mt + 5 * op.min[1], mt + 5 * op.min[2], g);
+            is_amp = true;
+            break;
+          }
+          case OP_AGGGG: {
+            W4<R> a = ld_slot(slots, op.in[0], L, t);
+            W4<R> b = ld_slot(slots, op.in[1], L, t);
+            W4<R> c = ld_slot(slots, op.in[2], L, t);
+            W4<R> d = ld_slot(slots, op.in[3], L, t);
+            amp = gggg_amp<R>(a, b, c, d, gg);
+            is_amp = true;
+            break;
+          }
+          case OP_AIOV: {
+            W4<R> f = ld_slot(slots, op.in[0], L, t);
+            W4<R> o = ld_slot(slots, op.in[1], L, t);
+            W4<R> v = ld_slot(slots, op.in[2], L, t);
+            amp = iov_amp<R>(f, o, v, g);
+            is_amp = true;
+            break;
+          }
+          default:
+            break;
+        }
+        if (is_amp) {
+          const ColEntry* ce = P.col + op.col_begin;
+          for (uint32_t k = 0; k < op.col_count; ++k) {
+            ColEntry c = ce[k];
+            R cr = (R)c.re, ci = (R)c.im;
+            R xr = cr * amp.r - ci * amp.i;
+            R xi = cr * amp.i + ci * amp.r;
+            R* jr = jam + (size_t)c.alpha * JW * L + t;
+            if constexpr (F32) {
+              float s, er;
+              two_sum(jr[0], xr, s, er);
+              jr[0] = s;
+              jr[2 * L] += er;
+              two_sum(jr[L], xi, s, er);
+              jr[L] = s;
+              jr[3 * L] += er;
+              abs_mass += fabsf(xr) + fabsf(xi);
+            } else {
+              jr[0] += xr;
+              jr[L] += xi;
+            }
+          }
+        }
+      }
+      // ---- colour sum: sum_ab J_a K_ab J_b^* / D
+      R tot = (R)0;
+      float jabs = 0.f;
+      for (int a = 0; a < m; ++a) {
+        const R* ja = jam + (size_t)a * JW * L + t;
+        R ar = ja[0], ai = ja[L];
+        if constexpr (F32) { ar += ja[2 * L]; ai += ja[3 * L]; jabs += fabsf(ar) + fabsf(ai); }
+        R zr = (R)0, zi = (R)0;
+        for (int b = 0; b < m; ++b) {
+          R k;
+          if constexpr (F32) k = __ldg(P.cf_f + (size_t)a * m + b);
+          else k = __ldg(P.cf_d + (size_t)a * m + b);
+          if (k == (R)0) continue;
+          const R* jb = jam + (size_t)b * JW * L + t;
+          R br = jb[0], bi = jb[L];
+          if constexpr (F32) { br += jb[2 * L]; bi += jb[3 * L]; }
+          zr += k * br;
+          zi += k * bi;
+        }
+        tot += ar * zr + ai * zi;
+      }
+      val = (double)tot * P.cf_inv_den;
+      if (F32) kappa = (jabs > 0.f) ? abs_mass / jabs : 0.f;
+      bad = isfinite(val) ? 0 : 1;
+    }
+    res[t] = bad ? __longlong_as_double(0x7ff8000000000000ll) : val;
+    kap[t] = kappa;
+    __syncthreads();
+
+    // ---- phase 2: helicity sum per event, fixed order
+    if (t < E) {
+      int64_t evr = ev0 + t;
+      if (evr < n) {
+        int64_t gev = listed ? (int64_t)A.event_list[evr] : evr;
+        double s = 0.0, wk = 0.0;
+        for (int hh = 0; hh < H; ++hh) {
+          double v = res[t * H + hh];
+          s += v;
+          wk += v * (double)kap[t * H + hh];
+          if (A.pair_out) A.pair_out[gev * H + hh] = v;
+        }
+        double me = 0.25 * s;
+        A.me2[gev] = me;
+        uint8_t fl = 0;
+        if (!isfinite(me)) fl |= MEA_FLAG_NONFINITE;
+        if (F32) {
+          // relative error indicator: FP32 unit roundoff x cancellation in J
+          double ind = (s > 0.0) ? 5.96e-8 * wk / s : 0.0;
+          if (!(ind <= (double)A.flag_threshold)) fl |= MEA_FLAG_CANCEL;
+        }
+        if (A.flags) {
+          if (A.write_flags_mode == 0) A.flags[gev] = fl;
+          else A.flags[gev] = (uint8_t)((A.flags[gev] & ~MEA_FLAG_CANCEL) | MEA_FLAG_REEVALUATED | fl);
+        }
+        if (A.flag_list && (fl & (MEA_FLAG_CANCEL | MEA_FLAG_NONFINITE))) {
+          int slot = atomicAdd(A.flag_count, 1);
+          A.flag_list[slot] = (int32_t)gev;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R>
+size_t smem_bytes(const DevProgram& p, int threads, int E, bool jsmem, bool ssmem) {
+  const int JW = std::is_same<R, float>::value ? 4 : 2;
+  size_t b = ssmem ? (size_t)p.n_slots * 8 * threads * sizeof(R) : 0;
+  if (jsmem) b += (size_t)p.n_colour * JW * threads * sizeof(R);
+  b += (size_t)E * (8 * p.n_ext + 5 * p.n_masks) * sizeof(R);
+  b = (b + 7) & ~size_t(7);
+  b += (size_t)threads * (sizeof(double) + sizeof(float)) + 16;
+  return b;
+}
+
+}  // namespace
+
+AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms,
+                   size_t max_smem, size_t smem_per_sm, int hint) {
+  AmpConfig best;
+  best.H = H;
+  double best_score = -1;
+  // preference: everything in shared memory, then colour amplitudes in global
+  // memory, then wavefunction slots too
+  const int placements[3][2] = {{1, 1}, {0, 1}, {0, 0}};
+  for (int pl = 0; pl < 3 && best_score <= 0; ++pl) {
+    bool jsm = placements[pl][0] != 0, ssm = placements[pl][1] != 0;
+    for (int E = 1; E * H <= kMaxThreads; ++E) {
+      if (hint > 0 && E != hint) continue;
+      int threads = ((E * H + 31) / 32) * 32;
+      size_t sm = fp64 ? smem_bytes<double>(p, threads, E, jsm, ssm)
+                       : smem_bytes<float>(p, threads, E, jsm, ssm);
+      if (sm > max_smem) break;
+      int per_sm = (int)std::min<size_t>(smem_per_sm / std::max<size_t>(sm, 1), 2048 / threads);
+      per_sm = std::min(per_sm, 32);
+      if (per_sm < 1) continue;
+      double util = (double)(E * H) / threads;
+      double lanes_sm = (double)per_sm * E * H;
+      // enough lanes per SM to hide latency, then as few idle lanes as possible
+      double score = std::min(lanes_sm, 512.0) * util;
+      if (!jsm || !ssm) score = std::min(lanes_sm, 256.0) * util;
+      if (score > best_score + 1e-9) {
+        best_score = score;
+        best.E_cta = E; best.threads = threads; best.smem = sm;
+        best.jamp_in_smem = jsm; best.slots_in_smem = ssm;
+        best.grid = per_sm * num_sms;
+      }
+    }
+  }
+  if (best_score < 0) {
+    best.E_cta = 1;
+    best.threads = ((H + 31) / 32) * 32;
+    best.jamp_in_smem = false;
+    best.slots_in_smem = false;
+    best.smem = fp64 ? smem_bytes<double>(p, best.threads, 1, false, false)
+                     : smem_bytes<float>(p, best.threads, 1, false, false);
+    best.grid = num_sms;
+  }
+  int64_t tiles = (n_events + best.E_cta - 1) / best.E_cta;
+  if (tiles < best.grid) best.grid = (int)std::max<int64_t>(tiles, 1);
+  return best;
+}
+
+size_t jamp_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig& c) {
+  if (c.jamp_in_smem) return 0;
+  const int JW = fp64 ? 2 : 4;
+  return (size_t)c.grid * p.n_colour * JW * c.threads * (fp64 ? sizeof(double) : sizeof(float));
+}
+
+size_t slot_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig& c) {
+  if (c.slots_in_smem) return 0;
+  return (size_t)c.grid * p.n_slots * 8 * c.threads * (fp64 ? sizeof(double) : sizeof(float));
+}
+
+template <typename R, bool J, bool S>
+static void launch_one(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
+  cudaFuncSetAttribute(amp_kernel<R, J, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  amp_kernel<R, J, S><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
+}
+
+cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const AmpLaunch& a,
+                       cudaStream_t s) {
+  if (c.grid <= 0) return cudaSuccess;
+  if (fp64) {
+    if (c.jamp_in_smem && c.slots_in_smem) launch_one<double, true, true>(p, c, a, s);
+    else if (c.slots_in_smem) launch_one<double, false, true>(p, c, a, s);
+    else launch_one<double, false, false>(p, c, a, s);
+  } else {
+    if (c.jamp_in_smem && c.slots_in_smem) launch_one<float, true, true>(p, c, a, s);
+    else if (c.slots_in_smem) launch_one<float, false, true>(p, c, a, s);
+    else launch_one<float, false, false>(p, c, a, s);
+  }
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess) ++launch_counter();
+  return err;
+}
+
+}  // namespace mea

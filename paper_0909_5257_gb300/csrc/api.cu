@@ -1,0 +1,403 @@
+// C ABI of libmea.so (declared in include/mea.h): process handles, device
+// residency of the process tables, scratch management and the evaluation
+// entry points.  No compute happens here; every step of the path runs in the
+// CUDA kernels of amp_kernel.cu and ps_kernel.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/mea.h"
+#include "generator.h"
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+mea_status fail(mea_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define MEA_CUDA(call)                                                            \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return fail(MEA_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t b) {
+    if (b <= bytes) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e == cudaSuccess) bytes = b;
+    return e;
+  }
+};
+
+}  // namespace
+
+struct mea_process_s {
+  mea::Program prog;
+  mea::DevProgram dev;
+  mea_options opts;
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0, smem_per_sm = 0;
+  std::vector<void*> owned;
+  std::mutex mu;
+  // scratch sets: 0 for mea_evaluate, 1 and 2 for the two host-pipeline streams
+  struct Scratch { DevBuf s32, s64, flag_list, flag_count; } scr[3];
+  // host-buffer pipeline
+  void* pin_in[2] = {nullptr, nullptr};
+  void* pin_out[2] = {nullptr, nullptr};
+  void* pin_flags[2] = {nullptr, nullptr};
+  DevBuf d_in[2], d_out[2], d_flags[2];
+  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  int64_t pipe_chunk = 0;
+  bool host_only = false;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t upload(mea_process_s* P, const std::vector<T>& v, const T** out) {
+  void* d = nullptr;
+  size_t b = std::max<size_t>(v.size() * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(&d, b);
+  if (e != cudaSuccess) return e;
+  P->owned.push_back(d);
+  if (!v.empty()) e = cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  *out = reinterpret_cast<const T*>(d);
+  return e;
+}
+
+void destroy(mea_process_s* P) {
+  if (!P) return;
+  for (void* d : P->owned) cudaFree(d);
+  for (auto& x : P->scr) {
+    x.s32.release();
+    x.s64.release();
+    x.flag_list.release();
+    x.flag_count.release();
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (P->pin_in[i]) cudaFreeHost(P->pin_in[i]);
+    if (P->pin_out[i]) cudaFreeHost(P->pin_out[i]);
+    if (P->pin_flags[i]) cudaFreeHost(P->pin_flags[i]);
+    P->d_in[i].release();
+    P->d_out[i].release();
+    P->d_flags[i].release();
+    if (P->st[i]) cudaStreamDestroy(P->st[i]);
+    if (P->done[i]) cudaEventDestroy(P->done[i]);
+  }
+  delete P;
+}
+
+cudaError_t place_scratch(DevBuf& buf, const mea::DevProgram& d, bool fp64, const mea::AmpConfig& c,
+                          mea::AmpLaunch& a) {
+  size_t jb = (mea::jamp_scratch_bytes_needed(d, fp64, c) + 255) & ~size_t(255);
+  size_t sb = mea::slot_scratch_bytes_needed(d, fp64, c);
+  cudaError_t e = buf.ensure(jb + sb + 256);
+  if (e != cudaSuccess) return e;
+  a.jamp_scratch = reinterpret_cast<float*>(buf.p);
+  a.slot_scratch = reinterpret_cast<float*>(reinterpret_cast<char*>(buf.p) + jb);
+  return cudaSuccess;
+}
+
+mea_status do_evaluate(mea_process_s* P, int set, const double* mom, int64_t n, mea_hel_mode hm,
+                       const int8_t* hel, mea_prec_mode prec, double* me2, uint8_t* flags,
+                       cudaStream_t s) {
+  const mea::Program& G = P->prog;
+  int H = (hm == MEA_HEL_SUM_NONZERO) ? G.n_hel : (hm == MEA_HEL_SUM_ALL ? (1 << G.n_ext) : 1);
+  bool fp64 = prec == MEA_PREC_FP64;
+  mea_process_s::Scratch& S = P->scr[set];
+  mea::AmpConfig c = mea::plan_amp(P->dev, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
+  mea::AmpLaunch a;
+  a.mom = mom;
+  a.n_events = n;
+  a.hel_given = hel;
+  a.hel_mode = (int)hm;
+  a.me2 = me2;
+  a.flags = flags;
+  a.flag_threshold = (float)P->opts.flag_threshold;
+  MEA_CUDA(place_scratch(fp64 ? S.s64 : S.s32, P->dev, fp64, c, a));
+  bool reeval = !fp64 && P->opts.reeval_fp64 && hm != MEA_HEL_GIVEN;
+  if (reeval) {
+    MEA_CUDA(S.flag_list.ensure(sizeof(int32_t) * (size_t)n));
+    MEA_CUDA(S.flag_count.ensure(sizeof(int32_t)));
+    MEA_CUDA(cudaMemsetAsync(S.flag_count.p, 0, sizeof(int32_t), s));
+    a.flag_list = reinterpret_cast<int32_t*>(S.flag_list.p);
+    a.flag_count = reinterpret_cast<int32_t*>(S.flag_count.p);
+  }
+  MEA_CUDA(mea::launch_amp(P->dev, fp64, c, a, s));
+  if (reeval) {
+    // FP64 re-evaluation of the flagged events; their count is read on the device
+    mea::AmpConfig c2 = mea::plan_amp(P->dev, true, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
+    mea::AmpLaunch b = a;
+    b.event_list = a.flag_list;
+    b.list_count = a.flag_count;
+    b.flag_list = nullptr;
+    b.flag_count = nullptr;
+    b.write_flags_mode = 1;
+    MEA_CUDA(place_scratch(S.s64, P->dev, true, c2, b));
+    MEA_CUDA(mea::launch_amp(P->dev, true, c2, b, s));
+  }
+  return MEA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mea_last_error(void) { return g_err.c_str(); }
+
+uint64_t mea_kernel_launch_count(void) { return mea::launch_counter(); }
+
+mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts, mea_process_t* out) {
+  if (!pdg || !out || n_ext < 4 || n_ext > 7) return fail(MEA_E_ARG, "mea_create_process: bad arguments");
+  *out = nullptr;
+  mea_process_s* P = new (std::nothrow) mea_process_s();
+  if (!P) return fail(MEA_E_NOMEM, "mea_create_process: out of host memory");
+  P->opts.alpha_s = 0.118;
+  P->opts.flag_threshold = 1e-5;
+  P->opts.reeval_fp64 = 1;
+  P->opts.colour_mode = 0;
+  if (opts) {
+    if (opts->alpha_s > 0) P->opts.alpha_s = opts->alpha_s;
+    if (opts->flag_threshold > 0) P->opts.flag_threshold = opts->flag_threshold;
+    P->opts.reeval_fp64 = opts->reeval_fp64;
+    P->opts.colour_mode = opts->colour_mode;
+  }
+  try {
+    P->prog = mea::build_program(std::vector<int>(pdg, pdg + n_ext));
+  } catch (std::exception& e) {
+    destroy(P);
+    return fail(MEA_E_UNSUPPORTED, std::string("mea_create_process: ") + e.what());
+  }
+  const mea::Program& G = P->prog;
+  cudaError_t e = cudaGetDevice(&P->device);
+  if (e != cudaSuccess) { destroy(P); return fail(MEA_E_CUDA, cudaGetErrorString(e)); }
+  int v = 0;
+  cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+  P->smem_optin = (size_t)v;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, P->device);
+  P->smem_per_sm = (size_t)v;
+
+  std::vector<int8_t> leg(4 * (size_t)n_ext, 0);
+  for (int l = 0; l < n_ext; ++l) {
+    int type = G.leg_type[l];
+    int kind = 0;
+    if (type == 1) kind = G.incoming[l] ? 0 : 1;       // u (incoming quark) or v (outgoing antiquark)
+    if (type == 2) kind = G.incoming[l] ? 3 : 2;       // vbar (incoming antiquark) or ubar (outgoing quark)
+    leg[4 * l] = (int8_t)type;
+    leg[4 * l + 1] = (int8_t)kind;
+    leg[4 * l + 2] = (int8_t)G.incoming[l];
+  }
+  std::vector<float> cff(G.cf_num.size());
+  std::vector<double> cfd(G.cf_num.size());
+  for (size_t i = 0; i < G.cf_num.size(); ++i) {
+    cff[i] = (float)G.cf_num[i];
+    cfd[i] = (double)G.cf_num[i];
+  }
+  mea::DevProgram& D = P->dev;
+  const mea::Op* dops;
+  const mea::ColEntry* dcol;
+  const uint32_t* dmask;
+  const int8_t *dleg, *dhel, *dhall;
+  const float* dcff;
+  const double* dcfd;
+  if ((e = upload(P, G.ops, &dops)) != cudaSuccess || (e = upload(P, G.col, &dcol)) != cudaSuccess ||
+      (e = upload(P, G.masks, &dmask)) != cudaSuccess || (e = upload(P, leg, &dleg)) != cudaSuccess ||
+      (e = upload(P, G.hel, &dhel)) != cudaSuccess || (e = upload(P, G.hel_all, &dhall)) != cudaSuccess ||
+      (e = upload(P, cff, &dcff)) != cudaSuccess || (e = upload(P, cfd, &dcfd)) != cudaSuccess) {
+    destroy(P);
+    return fail(e == cudaErrorMemoryAllocation ? MEA_E_NOMEM : MEA_E_CUDA,
+                std::string("mea_create_process: ") + cudaGetErrorString(e));
+  }
+  D.ops = dops;
+  D.n_ops = (int)G.ops.size();
+  D.col = dcol;
+  D.masks = dmask;
+  D.n_masks = (int)G.masks.size();
+  D.leg_info = dleg;
+  D.n_ext = n_ext;
+  D.n_slots = G.n_slots;
+  D.n_colour = G.n_colour;
+  D.cf_f = dcff;
+  D.cf_d = dcfd;
+  D.cf_inv_den = 1.0 / (double)G.cf_den;
+  D.hel = dhel;
+  D.n_hel = G.n_hel;
+  D.hel_all = dhall;
+  D.g = std::sqrt(4.0 * M_PI * P->opts.alpha_s);
+  *out = P;
+  return MEA_OK;
+}
+
+mea_status mea_create_process_host_only(const int* pdg, int n_ext, const mea_options* opts, mea_process_t* out) {
+  if (!pdg || !out || n_ext < 4 || n_ext > 7) return fail(MEA_E_ARG, "mea_create_process_host_only: bad arguments");
+  *out = nullptr;
+  mea_process_s* P = new (std::nothrow) mea_process_s();
+  if (!P) return fail(MEA_E_NOMEM, "mea_create_process_host_only: out of host memory");
+  P->host_only = true;
+  P->opts.alpha_s = (opts && opts->alpha_s > 0) ? opts->alpha_s : 0.118;
+  try {
+    P->prog = mea::build_program(std::vector<int>(pdg, pdg + n_ext));
+  } catch (std::exception& e) {
+    destroy(P);
+    return fail(MEA_E_UNSUPPORTED, std::string("mea_create_process_host_only: ") + e.what());
+  }
+  *out = P;
+  return MEA_OK;
+}
+
+mea_status mea_process_info(mea_process_t P, mea_process_info_t* info) {
+  if (!P || !info) return fail(MEA_E_ARG, "mea_process_info: null argument");
+  const mea::Program& G = P->prog;
+  std::memset(info, 0, sizeof(*info));
+  info->n_ext = G.n_ext;
+  info->n_diagrams = G.n_diagrams;
+  info->n_colour = G.n_colour;
+  info->n_hel_nonzero = G.n_hel;
+  info->n_currents = G.n_currents;
+  info->n_ops = (int)G.ops.size();
+  info->n_slots = G.n_slots;
+  info->cf_denominator = G.cf_den;
+  info->cf_max_abs_numerator = G.cf_max_abs;
+  info->flops_per_hel = G.flops_per_hel;
+  info->colour_flops_per_hel = 4.0 * (double)G.n_colour * (double)G.n_colour;
+  return MEA_OK;
+}
+
+mea_status mea_colour_matrix(mea_process_t P, int64_t* num, int64_t* den) {
+  if (!P || !num || !den) return fail(MEA_E_ARG, "mea_colour_matrix: null argument");
+  std::copy(P->prog.cf_num.begin(), P->prog.cf_num.end(), num);
+  *den = P->prog.cf_den;
+  return MEA_OK;
+}
+
+mea_status mea_helicities(mea_process_t P, int8_t* hel, int cap, int* n_hel) {
+  if (!P || !n_hel) return fail(MEA_E_ARG, "mea_helicities: null argument");
+  *n_hel = P->prog.n_hel;
+  if (hel) {
+    if (cap < P->prog.n_hel) return fail(MEA_E_ARG, "mea_helicities: buffer too small");
+    std::copy(P->prog.hel.begin(), P->prog.hel.end(), hel);
+  }
+  return MEA_OK;
+}
+
+mea_status mea_destroy_process(mea_process_t P) {
+  if (!P) return fail(MEA_E_ARG, "mea_destroy_process: null handle");
+  if (!P->host_only) cudaDeviceSynchronize();
+  destroy(P);
+  return MEA_OK;
+}
+
+mea_status mea_evaluate(mea_process_t P, const double* mom, int64_t n, mea_hel_mode hm, const int8_t* hel,
+                        mea_prec_mode prec, double* me2, uint8_t* flags, void* stream) {
+  if (!P) return fail(MEA_E_ARG, "mea_evaluate: null process");
+  if (P->host_only) return fail(MEA_E_UNSUPPORTED, "mea_evaluate: host-only process handle");
+  if (n < 0 || n > (int64_t)0x7fffffff) return fail(MEA_E_ARG, "mea_evaluate: n_events out of range");
+  if (n == 0) return MEA_OK;
+  if (!mom || !me2) return fail(MEA_E_ARG, "mea_evaluate: null momenta or me2");
+  if (hm != MEA_HEL_SUM_NONZERO && hm != MEA_HEL_SUM_ALL && hm != MEA_HEL_GIVEN)
+    return fail(MEA_E_ARG, "mea_evaluate: bad helicity mode");
+  if (hm == MEA_HEL_GIVEN && !hel) return fail(MEA_E_ARG, "mea_evaluate: MEA_HEL_GIVEN needs hel_dev");
+  if (prec != MEA_PREC_FP64 && prec != MEA_PREC_MIXED) return fail(MEA_E_ARG, "mea_evaluate: bad precision");
+  std::lock_guard<std::mutex> lk(P->mu);
+  return do_evaluate(P, 0, mom, n, hm, hel, prec, me2, flags, reinterpret_cast<cudaStream_t>(stream));
+}
+
+mea_status mea_evaluate_host(mea_process_t P, const double* mom_h, int64_t n, mea_prec_mode prec,
+                             double* me2_h, uint8_t* flags_h) {
+  if (!P) return fail(MEA_E_ARG, "mea_evaluate_host: null process");
+  if (P->host_only) return fail(MEA_E_UNSUPPORTED, "mea_evaluate_host: host-only process handle");
+  if (n < 0) return fail(MEA_E_ARG, "mea_evaluate_host: negative n_events");
+  if (n == 0) return MEA_OK;
+  if (!mom_h || !me2_h) return fail(MEA_E_ARG, "mea_evaluate_host: null buffer");
+  std::lock_guard<std::mutex> lk(P->mu);
+  const int n_ext = P->prog.n_ext;
+  const int64_t chunk = std::min<int64_t>(n, 1 << 17);
+  if (P->pipe_chunk < chunk) {
+    for (int i = 0; i < 2; ++i) {
+      if (P->pin_in[i]) cudaFreeHost(P->pin_in[i]);
+      if (P->pin_out[i]) cudaFreeHost(P->pin_out[i]);
+      if (P->pin_flags[i]) cudaFreeHost(P->pin_flags[i]);
+      P->pin_in[i] = P->pin_out[i] = P->pin_flags[i] = nullptr;
+      MEA_CUDA(cudaHostAlloc(&P->pin_in[i], sizeof(double) * 4 * n_ext * chunk, cudaHostAllocDefault));
+      MEA_CUDA(cudaHostAlloc(&P->pin_out[i], sizeof(double) * chunk, cudaHostAllocDefault));
+      MEA_CUDA(cudaHostAlloc(&P->pin_flags[i], chunk, cudaHostAllocDefault));
+      MEA_CUDA(P->d_in[i].ensure(sizeof(double) * 4 * n_ext * chunk));
+      MEA_CUDA(P->d_out[i].ensure(sizeof(double) * chunk));
+      MEA_CUDA(P->d_flags[i].ensure(chunk));
+      if (!P->st[i]) MEA_CUDA(cudaStreamCreateWithFlags(&P->st[i], cudaStreamNonBlocking));
+      if (!P->done[i]) MEA_CUDA(cudaEventCreateWithFlags(&P->done[i], cudaEventDisableTiming));
+    }
+    P->pipe_chunk = chunk;
+  }
+  const int64_t n_chunks = (n + chunk - 1) / chunk;
+  int64_t pending[2] = {-1, -1};
+  auto drain = [&](int b) -> mea_status {
+    if (pending[b] < 0) return MEA_OK;
+    MEA_CUDA(cudaEventSynchronize(P->done[b]));
+    int64_t c0 = pending[b] * chunk;
+    int64_t cn = std::min(chunk, n - c0);
+    std::memcpy(me2_h + c0, P->pin_out[b], sizeof(double) * cn);
+    if (flags_h) std::memcpy(flags_h + c0, P->pin_flags[b], cn);
+    pending[b] = -1;
+    return MEA_OK;
+  };
+  for (int64_t k = 0; k < n_chunks; ++k) {
+    int b = (int)(k & 1);
+    mea_status s = drain(b);
+    if (s != MEA_OK) return s;
+    int64_t c0 = k * chunk, cn = std::min(chunk, n - c0);
+    std::memcpy(P->pin_in[b], mom_h + (size_t)c0 * n_ext * 4, sizeof(double) * 4 * n_ext * cn);
+    MEA_CUDA(cudaMemcpyAsync(P->d_in[b].p, P->pin_in[b], sizeof(double) * 4 * n_ext * cn,
+                             cudaMemcpyHostToDevice, P->st[b]));
+    s = do_evaluate(P, 1 + b, reinterpret_cast<const double*>(P->d_in[b].p), cn, MEA_HEL_SUM_NONZERO, nullptr, prec,
+                    reinterpret_cast<double*>(P->d_out[b].p), reinterpret_cast<uint8_t*>(P->d_flags[b].p), P->st[b]);
+    if (s != MEA_OK) return s;
+    MEA_CUDA(cudaMemcpyAsync(P->pin_out[b], P->d_out[b].p, sizeof(double) * cn, cudaMemcpyDeviceToHost, P->st[b]));
+    MEA_CUDA(cudaMemcpyAsync(P->pin_flags[b], P->d_flags[b].p, cn, cudaMemcpyDeviceToHost, P->st[b]));
+    MEA_CUDA(cudaEventRecord(P->done[b], P->st[b]));
+    pending[b] = k;
+  }
+  for (int b = 0; b < 2; ++b) {
+    mea_status s = drain(b);
+    if (s != MEA_OK) return s;
+  }
+  return MEA_OK;
+}
+
+mea_status mea_generate_phase_space(const mea_ps_config* cfg, uint64_t first_event, int64_t n, double* mom,
+                                    int32_t* attempts, void* stream) {
+  if (!cfg || n < 0) return fail(MEA_E_ARG, "mea_generate_phase_space: bad arguments");
+  if (cfg->n_final < 2 || cfg->n_final > 8 || !(cfg->rs_lo > 0) || !(cfg->rs_hi >= cfg->rs_lo))
+    return fail(MEA_E_ARG, "mea_generate_phase_space: bad configuration");
+  if (n == 0) return MEA_OK;
+  if (!mom) return fail(MEA_E_ARG, "mea_generate_phase_space: null momenta");
+  mea::PsConfigDev c{cfg->seed, cfg->n_final, cfg->rs_lo, cfg->rs_hi, cfg->pt_min, cfg->eta_max, cfg->dr_min};
+  MEA_CUDA(mea::launch_phase_space(c, first_event, n, mom, attempts, reinterpret_cast<cudaStream_t>(stream)));
+  return MEA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,262 @@
+// Device library of wavefunction, vertex and off-shell-current functions
+// (the HEGET set of arXiv:0909.5257, Sec. 4 and Appendix A), written for
+// sm_103a and templated on the real type (float for the mixed path, double
+// for the FP64 path).
+//
+// Conventions (HELAS): every vector wavefunction is a contravariant complex
+// 4-vector, dot products carry the metric (+,-,-,-), and the momentum attached
+// to a wavefunction is the flowing-OUT momentum of the partons below it.
+// Spinors use the chiral representation, upper two components left-handed.
+//
+// Colour factors that go with each function (applied by the generator):
+//   vvv_amp, jvv          : i f^{abc}                         (Sec. 4.1)
+//   gggg_amp, jggg calls  : f^{abe}f^{cde}, f^{ace}f^{dbe},
+//                           f^{ade}f^{bce} for the three calls  (Sec. 4.2)
+//   iov_amp               : -T^a_{ij}                          (Eq. (qqg-amplitude))
+//   fvi, fvo, jio         : T^a
+// With these, every current equals the Feynman-rule current and every
+// amplitude equals -i times the Feynman-rule vertex, so that each diagram
+// yields M with one common phase.
+#pragma once
+
+#ifndef MEA_HD
+#define MEA_HD __host__ __device__ __forceinline__
+#endif
+
+template <typename R>
+struct cx {
+  R r, i;
+};
+
+template <typename R>
+MEA_HD cx<R> mk(R r, R i) { return cx<R>{r, i}; }
+template <typename R>
+MEA_HD cx<R> operator+(cx<R> a, cx<R> b) { return {a.r + b.r, a.i + b.i}; }
+template <typename R>
+MEA_HD cx<R> operator-(cx<R> a, cx<R> b) { return {a.r - b.r, a.i - b.i}; }
+template <typename R>
+MEA_HD cx<R> operator-(cx<R> a) { return {-a.r, -a.i}; }
+template <typename R>
+MEA_HD cx<R> operator*(cx<R> a, cx<R> b) {
+  return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r};
+}
+template <typename R>
+MEA_HD cx<R> operator*(R s, cx<R> a) { return {s * a.r, s * a.i}; }
+template <typename R>
+MEA_HD cx<R> conj(cx<R> a) { return {a.r, -a.i}; }
+template <typename R>
+MEA_HD cx<R> times_i(cx<R> a) { return {-a.i, a.r}; }
+
+// Four complex components: a vector (contravariant) or a Dirac spinor.
+template <typename R>
+struct W4 {
+  cx<R> c[4];
+};
+
+// a.b = a0 b0 - a1 b1 - a2 b2 - a3 b3 for complex vectors
+template <typename R>
+MEA_HD cx<R> dot(const W4<R>& a, const W4<R>& b) {
+  return a.c[0] * b.c[0] - a.c[1] * b.c[1] - a.c[2] * b.c[2] - a.c[3] * b.c[3];
+}
+// p.a for a real vector p
+template <typename R>
+MEA_HD cx<R> dot(const R* p, const W4<R>& a) {
+  return p[0] * a.c[0] - p[1] * a.c[1] - p[2] * a.c[2] - p[3] * a.c[3];
+}
+
+// ---------------------------------------------------------------- VVV
+// vvvxxx: amplitude of the ggg vertex from three gluon wavefunctions with
+// flowing-out momenta pa, pb, pc (Appendix A, listing vvvxxx):
+//   -g [ (ga.gb)(pa-pb).gc + (gb.gc)(pb-pc).ga + (gc.ga)(pc-pa).gb ]
+template <typename R>
+MEA_HD cx<R> vvv_amp(const W4<R>& ga, const W4<R>& gb, const W4<R>& gc,
+                                         const R* pa, const R* pb, const R* pc, R g) {
+  cx<R> v12 = dot(ga, gb), v23 = dot(gb, gc), v31 = dot(gc, ga);
+  cx<R> p12 = dot(pa, gb), p13 = dot(pa, gc);
+  cx<R> p21 = dot(pb, ga), p23 = dot(pb, gc);
+  cx<R> p31 = dot(pc, ga), p32 = dot(pc, gb);
+  cx<R> v = v12 * (p13 - p23) + v23 * (p21 - p31) + v31 * (p32 - p12);
+  return (-g) * v;
+}
+
+// jvvxx0 (listing name jggxxx): off-shell gluon from two gluons, Feynman-gauge
+// propagator.  inv_q2 = 1/q^2 with q = -(pa+pb), supplied from the FP64 prep.
+template <typename R>
+MEA_HD W4<R> jvv(const W4<R>& ga, const W4<R>& gb, const R* pa,
+                                     const R* pb, R inv_q2, R g) {
+  // q = -(pa+pb):  (pb - q) = pa + 2 pb,  (pa - q) = 2 pa + pb
+  R s1[4], s2[4], d[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    s1[m] = pa[m] + R(2) * pb[m];
+    s2[m] = R(2) * pa[m] + pb[m];
+    d[m] = pa[m] - pb[m];
+  }
+  cx<R> gab = dot(ga, gb);
+  cx<R> sga = dot(s1, ga);
+  cx<R> sgb = -dot(s2, gb);
+  R gs = -g * inv_q2;
+  W4<R> j;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) j.c[m] = gs * (d[m] * gab + sga * gb.c[m] + sgb * ga.c[m]);
+  return j;
+}
+
+// ---------------------------------------------------------------- VVVV
+// ggggxx: one colour structure of the gggg amplitude,
+//   gg [ (ga.gd)(gb.gc) - (ga.gc)(gb.gd) ],  gg = g_s^2   (listing ggggxx)
+template <typename R>
+MEA_HD cx<R> gggg_amp(const W4<R>& ga, const W4<R>& gb, const W4<R>& gc,
+                                          const W4<R>& gd, R gg) {
+  return gg * (dot(ga, gd) * dot(gb, gc) - dot(ga, gc) * dot(gb, gd));
+}
+
+// jgggx0: off-shell gluon of one gggg colour structure,
+//   (gg/q^2) [ ga (gc.gb) - gb (ga.gc) ]                  (listing jgggx0)
+template <typename R>
+MEA_HD W4<R> jggg(const W4<R>& ga, const W4<R>& gb, const W4<R>& gc,
+                                      R inv_q2, R gg) {
+  R f = gg * inv_q2;
+  cx<R> gcb = dot(gc, gb), gac = dot(ga, gc);
+  W4<R> j;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) j.c[m] = f * (ga.c[m] * gcb - gb.c[m] * gac);
+  return j;
+}
+
+// ---------------------------------------------------------------- qqg
+// slash(V) psi for a column spinor, V contravariant complex.
+template <typename R>
+MEA_HD W4<R> slash_col(const W4<R>& V, const W4<R>& s) {
+  cx<R> vp = V.c[0] + V.c[3], vm = V.c[0] - V.c[3];
+  cx<R> v12m = V.c[1] - times_i(V.c[2]);  // V1 - i V2
+  cx<R> v12p = V.c[1] + times_i(V.c[2]);  // V1 + i V2
+  W4<R> o;
+  o.c[0] = vm * s.c[2] - v12m * s.c[3];
+  o.c[1] = vp * s.c[3] - v12p * s.c[2];
+  o.c[2] = vp * s.c[0] + v12m * s.c[1];
+  o.c[3] = v12p * s.c[0] + vm * s.c[1];
+  return o;
+}
+// barred spinor (row) times slash(V)
+template <typename R>
+MEA_HD W4<R> row_slash(const W4<R>& s, const W4<R>& V) {
+  cx<R> vp = V.c[0] + V.c[3], vm = V.c[0] - V.c[3];
+  cx<R> v12m = V.c[1] - times_i(V.c[2]);
+  cx<R> v12p = V.c[1] + times_i(V.c[2]);
+  W4<R> o;
+  o.c[0] = s.c[2] * vp + s.c[3] * v12p;
+  o.c[1] = s.c[2] * v12m + s.c[3] * vm;
+  o.c[2] = s.c[0] * vm - s.c[1] * v12p;
+  o.c[3] = s.c[1] * vp - s.c[0] * v12m;
+  return o;
+}
+// slash(P) for a real momentum
+template <typename R>
+MEA_HD W4<R> slash_real_col(const R* P, const W4<R>& s) {
+  R vp = P[0] + P[3], vm = P[0] - P[3];
+  cx<R> v12m = mk<R>(P[1], -P[2]);
+  cx<R> v12p = mk<R>(P[1], P[2]);
+  W4<R> o;
+  o.c[0] = vm * s.c[2] - v12m * s.c[3];
+  o.c[1] = vp * s.c[3] - v12p * s.c[2];
+  o.c[2] = vp * s.c[0] + v12m * s.c[1];
+  o.c[3] = v12p * s.c[0] + vm * s.c[1];
+  return o;
+}
+template <typename R>
+MEA_HD W4<R> row_slash_real(const W4<R>& s, const R* P) {
+  R vp = P[0] + P[3], vm = P[0] - P[3];
+  cx<R> v12m = mk<R>(P[1], -P[2]);
+  cx<R> v12p = mk<R>(P[1], P[2]);
+  W4<R> o;
+  o.c[0] = vp * s.c[2] + s.c[3] * v12p;
+  o.c[1] = s.c[2] * v12m + vm * s.c[3];
+  o.c[2] = vm * s.c[0] - s.c[1] * v12p;
+  o.c[3] = vp * s.c[1] - s.c[0] * v12m;
+  return o;
+}
+
+// iovxx0: amplitude  g * fo slash(V) fi  (colour -T^a, Eq. (qqg-amplitude))
+template <typename R>
+MEA_HD cx<R> iov_amp(const W4<R>& fi, const W4<R>& fo, const W4<R>& v, R g) {
+  W4<R> t = slash_col(v, fi);
+  cx<R> s = fo.c[0] * t.c[0] + fo.c[1] * t.c[1] + fo.c[2] * t.c[2] + fo.c[3] * t.c[3];
+  return g * s;
+}
+
+// Off-shell quark from fi and a gluon: Feynman current (i Q/Q^2)(-i g V) fi with
+// Q = -P the momentum along the fermion arrow, P the flowing-out momentum:
+//   -(g/P^2) slash(P) slash(V) fi
+template <typename R>
+MEA_HD W4<R> fvi(const W4<R>& fi, const W4<R>& v, const R* P, R inv_p2, R g) {
+  W4<R> t = slash_col(v, fi);
+  W4<R> u = slash_real_col(P, t);
+  R f = -g * inv_p2;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) u.c[m] = f * u.c[m];
+  return u;
+}
+// Off-shell barred quark: fo (-i g V)(i P / P^2) = (g/P^2) fo slash(V) slash(P)
+template <typename R>
+MEA_HD W4<R> fvo(const W4<R>& fo, const W4<R>& v, const R* P, R inv_p2, R g) {
+  W4<R> t = row_slash(fo, v);
+  W4<R> u = row_slash_real(t, P);
+  R f = g * inv_p2;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) u.c[m] = f * u.c[m];
+  return u;
+}
+// Off-shell gluon from a quark pair: J^mu = -(g/q^2) fo gamma^mu fi
+template <typename R>
+MEA_HD W4<R> jio(const W4<R>& fi, const W4<R>& fo, R inv_q2, R g) {
+  const W4<R>& a = fo;
+  const W4<R>& b = fi;
+  cx<R> j0 = a.c[0] * b.c[2] + a.c[1] * b.c[3] + a.c[2] * b.c[0] + a.c[3] * b.c[1];
+  cx<R> j1 = a.c[0] * b.c[3] + a.c[1] * b.c[2] - a.c[2] * b.c[1] - a.c[3] * b.c[0];
+  cx<R> j2 = times_i(a.c[1] * b.c[2] - a.c[0] * b.c[3] + a.c[2] * b.c[1] - a.c[3] * b.c[0]);
+  cx<R> j3 = a.c[0] * b.c[2] - a.c[1] * b.c[3] - a.c[2] * b.c[0] + a.c[3] * b.c[1];
+  R f = -g * inv_q2;
+  W4<R> j;
+  j.c[0] = f * j0; j.c[1] = f * j1; j.c[2] = f * j2; j.c[3] = f * j3;
+  return j;
+}
+
+// ------------------------------------------------------- external states
+// Gluon of helicity lam with transverse unit vectors e1, e2 (e1 x e2 = p_hat):
+// eps = (-lam e1 - i e2)/sqrt2, conjugated for an outgoing gluon.
+template <typename R>
+MEA_HD W4<R> ext_gluon(const R* e1, const R* e2, int lam, bool outgoing) {
+  const R r = R(0.70710678118654752440);
+  R sgn = outgoing ? R(1) : R(-1);
+  W4<R> w;
+  w.c[0] = mk<R>(R(0), R(0));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w.c[k + 1] = mk<R>(-R(lam) * e1[k] * r, sgn * e2[k] * r);
+  return w;
+}
+
+// Massless spinors from r = sqrt(2E) and chi_+ = (a, b) (a real),
+// chi_- = (-b*, a).  kind: 0 u, 1 v, 2 ubar, 3 vbar.
+template <typename R>
+MEA_HD W4<R> ext_spinor(R r, R a, cx<R> b, int lam, int kind) {
+  W4<R> s;
+  cx<R> z = mk<R>(R(0), R(0));
+  cx<R> ra = mk<R>(r * a, R(0));
+  cx<R> rb = r * b;
+  cx<R> rbc = conj(rb);
+  bool plus = lam > 0;
+  if (kind == 0 || kind == 2) {          // u
+    if (plus) { s.c[0] = z; s.c[1] = z; s.c[2] = ra; s.c[3] = rb; }
+    else { s.c[0] = -rbc; s.c[1] = ra; s.c[2] = z; s.c[3] = z; }
+  } else {                               // v
+    if (plus) { s.c[0] = -rbc; s.c[1] = ra; s.c[2] = z; s.c[3] = z; }
+    else { s.c[0] = z; s.c[1] = z; s.c[2] = -ra; s.c[3] = -rb; }
+  }
+  if (kind >= 2) {                       // bar: psi^dagger gamma^0
+    W4<R> t;
+    t.c[0] = conj(s.c[2]); t.c[1] = conj(s.c[3]); t.c[2] = conj(s.c[0]); t.c[3] = conj(s.c[1]);
+    return t;
+  }
+  return s;
+}

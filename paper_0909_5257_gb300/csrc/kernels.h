@@ -1,0 +1,79 @@
+// Host-side declarations of the CUDA kernels' launch helpers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "generator.h"
+
+namespace mea {
+
+// Device copy of a process program (all pointers are device memory).
+struct DevProgram {
+  const Op* ops = nullptr;
+  int n_ops = 0;
+  const ColEntry* col = nullptr;
+  const uint32_t* masks = nullptr;
+  int n_masks = 0;
+  const int8_t* leg_info = nullptr;   // [n_ext][4]: type, spinor kind, incoming, pad
+  int n_ext = 0;
+  int n_slots = 0;
+  int n_colour = 0;
+  const float* cf_f = nullptr;        // K as float [m*m]
+  const double* cf_d = nullptr;       // K as double [m*m]
+  double cf_inv_den = 0;              // 1 / D
+  const int8_t* hel = nullptr;        // [n_hel][n_ext] helicities summed in MEA_HEL_SUM_NONZERO
+  int n_hel = 0;
+  const int8_t* hel_all = nullptr;    // [2^n_ext][n_ext]
+  double g = 0;                       // g_s
+};
+
+struct AmpLaunch {
+  const double* mom = nullptr;        // [n_events][n_ext][4]
+  int64_t n_events = 0;
+  const int32_t* event_list = nullptr;  // optional: evaluate mom[event_list[i]] for i < *list_count
+  const int32_t* list_count = nullptr;  // device count for event_list mode
+  const int8_t* hel_given = nullptr;  // [n_events][n_ext] for one given helicity per event
+  int hel_mode = 0;                   // 0 nonzero set, 1 all 2^n, 2 given
+  double* me2 = nullptr;
+  uint8_t* flags = nullptr;
+  float flag_threshold = 1e-5f;
+  int write_flags_mode = 0;           // 0: write flags; 1: OR in MEA_FLAG_REEVALUATED (re-evaluation)
+  int32_t* flag_list = nullptr;       // mixed path: indices of flagged events are appended here
+  int32_t* flag_count = nullptr;
+  double* pair_out = nullptr;         // optional [event][H] per-helicity values (tests)
+  float* jamp_scratch = nullptr;      // global colour-amplitude accumulators when not in SMEM
+  float* slot_scratch = nullptr;      // global wavefunction slots when not in SMEM
+};
+
+struct AmpConfig {
+  int H = 1;           // helicity lanes per event
+  int E_cta = 1;       // events per tile
+  int threads = 32;
+  int grid = 1;
+  size_t smem = 0;
+  bool jamp_in_smem = true;
+  bool slots_in_smem = true;
+};
+
+// Choose tile shape and grid for a program, precision and helicity mode.
+AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms,
+                   size_t max_smem_per_block, size_t smem_per_sm, int events_per_tile_hint = 0);
+
+size_t jamp_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig& c);
+size_t slot_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig& c);
+
+cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const AmpLaunch& a,
+                       cudaStream_t s);
+
+// Phase-space generator kernel (input generator).
+struct PsConfigDev {
+  uint64_t seed;
+  int n_final;
+  double rs_lo, rs_hi, pt_min, eta_max, dr_min;
+};
+cudaError_t launch_phase_space(const PsConfigDev& cfg, uint64_t first_event, int64_t n,
+                               double* mom, int32_t* attempts, cudaStream_t s);
+
+uint64_t& launch_counter();
+
+}  // namespace mea

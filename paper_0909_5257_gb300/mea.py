@@ -1,0 +1,191 @@
+"""Thin ctypes binding of libmea.so (C ABI in include/mea.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the library.  Device buffers are passed as raw pointers (torch
+tensors are accepted and unwrapped with ``data_ptr()``); PyTorch is used only
+for device memory and streams.  There is no CPU fallback: if the library is
+missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmea.so")
+_lock = threading.Lock()
+_lib = None
+
+MEA_OK = 0
+HEL_SUM_NONZERO, HEL_SUM_ALL, HEL_GIVEN = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+FLAG_REEVALUATED, FLAG_NONFINITE, FLAG_CANCEL = 0x01, 0x02, 0x04
+
+_STATUS = {0: "MEA_OK", -1: "MEA_E_ARG", -2: "MEA_E_UNSUPPORTED", -3: "MEA_E_NOMEM",
+           -4: "MEA_E_CUDA", -5: "MEA_E_TIMEOUT", -6: "MEA_E_REJECTED"}
+
+
+class MeaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("alpha_s", ctypes.c_double), ("flag_threshold", ctypes.c_double),
+                ("reeval_fp64", ctypes.c_int), ("colour_mode", ctypes.c_int)]
+
+
+class ProcessInfo(ctypes.Structure):
+    _fields_ = [("n_ext", ctypes.c_int), ("n_diagrams", ctypes.c_int), ("n_colour", ctypes.c_int),
+                ("n_hel_nonzero", ctypes.c_int), ("n_currents", ctypes.c_int), ("n_ops", ctypes.c_int),
+                ("n_slots", ctypes.c_int), ("colour_denominator_log2", ctypes.c_int),
+                ("cf_denominator", ctypes.c_int64), ("cf_max_abs_numerator", ctypes.c_int64),
+                ("flops_per_hel", ctypes.c_double), ("colour_flops_per_hel", ctypes.c_double)]
+
+
+class PsConfig(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("n_final", ctypes.c_int), ("rs_lo", ctypes.c_double),
+                ("rs_hi", ctypes.c_double), ("pt_min", ctypes.c_double), ("eta_max", ctypes.c_double),
+                ("dr_min", ctypes.c_double)]
+
+
+def load(path: str | None = None):
+    """Load libmea.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import build as _build
+            if path is None:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise MeaError(-2, f"CUDA library not found at {path}")
+            lib = ctypes.CDLL(path)
+            vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+            lib.mea_create_process.argtypes = [vp, i32, vp, vp]
+            lib.mea_create_process_host_only.argtypes = [vp, i32, vp, vp]
+            lib.mea_process_info.argtypes = [vp, vp]
+            lib.mea_colour_matrix.argtypes = [vp, vp, vp]
+            lib.mea_helicities.argtypes = [vp, vp, i32, vp]
+            lib.mea_destroy_process.argtypes = [vp]
+            lib.mea_evaluate.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp, vp]
+            lib.mea_evaluate_host.argtypes = [vp, vp, i64, i32, vp, vp]
+            lib.mea_generate_phase_space.argtypes = [vp, ctypes.c_uint64, i64, vp, vp, vp]
+            lib.mea_last_error.restype = ctypes.c_char_p
+            lib.mea_kernel_launch_count.restype = ctypes.c_uint64
+            for name in ("mea_create_process", "mea_create_process_host_only", "mea_process_info",
+                         "mea_colour_matrix", "mea_helicities", "mea_destroy_process", "mea_evaluate",
+                         "mea_evaluate_host", "mea_generate_phase_space"):
+                getattr(lib, name).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != MEA_OK:
+        raise MeaError(rc, load().mea_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+def kernel_launch_count() -> int:
+    return int(load().mea_kernel_launch_count())
+
+
+class Process:
+    """A partonic process on the current CUDA device, e.g. ``Process([21]*5)``.
+
+    pdg: PDG codes (two incoming, then outgoing): 21 gluon, 1..5 quarks,
+    negative for antiquarks.  host_only builds the tables without a GPU.
+    """
+
+    def __init__(self, pdg, alpha_s=0.118, flag_threshold=1e-5, reeval_fp64=True,
+                 colour_mode=0, host_only=False):
+        lib = load()
+        self.pdg = list(pdg)
+        self.n_ext = len(self.pdg)
+        arr = (ctypes.c_int * self.n_ext)(*self.pdg)
+        opts = Options(alpha_s, flag_threshold, 1 if reeval_fp64 else 0, colour_mode)
+        h = ctypes.c_void_p()
+        fn = lib.mea_create_process_host_only if host_only else lib.mea_create_process
+        _check(fn(arr, self.n_ext, ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        info = ProcessInfo()
+        _check(lib.mea_process_info(self._h, ctypes.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in ProcessInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().mea_destroy_process(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_colour(self):
+        return self.info["n_colour"]
+
+    def colour_matrix_exact(self):
+        m = self.n_colour
+        num = np.zeros((m, m), dtype=np.int64)
+        den = ctypes.c_int64()
+        _check(load().mea_colour_matrix(self._h, _ptr(num), ctypes.byref(den)))
+        return num, int(den.value)
+
+    def helicities(self):
+        n = ctypes.c_int()
+        _check(load().mea_helicities(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros((n.value, self.n_ext), dtype=np.int8)
+        _check(load().mea_helicities(self._h, _ptr(out), n.value, ctypes.byref(n)))
+        return out
+
+    def evaluate(self, momenta, me2, n_events=None, hel_mode=HEL_SUM_NONZERO, hel=None,
+                 precision=PREC_MIXED, flags=None, stream=None):
+        """Enqueue |M|^2 of device momenta [N, n_ext, 4] (float64) into device me2 [N]."""
+        if n_events is None:
+            n_events = int(momenta.shape[0])
+        _check(load().mea_evaluate(self._h, _ptr(momenta), n_events, hel_mode, _ptr(hel), precision,
+                                   _ptr(me2), _ptr(flags), _stream(stream)))
+
+    def evaluate_host(self, momenta: np.ndarray, precision=PREC_MIXED, with_flags=False):
+        """|M|^2 of host momenta through the library's pinned, pipelined copies."""
+        mom = np.ascontiguousarray(momenta, dtype=np.float64)
+        n = mom.shape[0]
+        out = np.zeros(n, dtype=np.float64)
+        fl = np.zeros(n, dtype=np.uint8) if with_flags else None
+        _check(load().mea_evaluate_host(self._h, _ptr(mom), n, precision, _ptr(out), _ptr(fl)))
+        return (out, fl) if with_flags else out
+
+
+def generate_phase_space(n_final, n, momenta, first_event=0, seed=0x09095257, rs_lo=200.0,
+                         rs_hi=2000.0, pt_min=20.0, eta_max=2.5, dr_min=0.4, attempts=None,
+                         stream=None):
+    cfg = PsConfig(seed, n_final, rs_lo, rs_hi, pt_min, eta_max, dr_min)
+    _check(load().mea_generate_phase_space(ctypes.byref(cfg), first_event, n, _ptr(momenta),
+                                           _ptr(attempts), _stream(stream)))

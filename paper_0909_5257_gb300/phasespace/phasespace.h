@@ -12,7 +12,8 @@
  *     4x32 Philox S-box with multipliers 0xD2511F53 / 0xCD9E8D57 and Weyl key
  *     increments 0x9E3779B9 / 0xBB67AE85.
  *   - RAMBO flat massless n-body phase space (Kleiss, Stirling, Ellis,
- *     Comput. Phys. Commun. 40 (1986) 359) in the partonic centre-of-mass frame.
+ *     Comput. Phys. Commun. 40 (1986) 359) in the partonic centre-of-mass frame
+ *     (n = 2: a uniform direction, the same distribution drawn directly).
  *   - sqrt(s_hat) drawn log-uniform in [rs_lo, rs_hi]; incoming partons along
  *     +z / -z with energy sqrt(s_hat)/2 each.
  *   - Jet cuts pT > pt_min, |eta| < eta_max, Delta R > dr_min between every
@@ -117,6 +118,19 @@ PS_HD double ps_next(ps_stream *s) {
 /* Writes n massless momenta with total momentum (rs, 0, 0, 0) into mom. */
 PS_HD void ps_rambo_massless(ps_stream *s, int n, double rs, double (*mom)[4]) {
   const double twopi = 6.283185307179586476925286766559;
+  if (n == 2) {
+    /* Flat two-body massless phase space is a uniform direction in the
+     * centre-of-mass frame; drawing it directly keeps both momenta exactly
+     * back to back and on shell (RAMBO's conformal boost loses digits when
+     * its two random vectors are nearly parallel). */
+    double c = 2.0 * ps_next(s) - 1.0;
+    double sn = sqrt(1.0 - c * c);
+    double f = twopi * ps_next(s);
+    double e = 0.5 * rs;
+    mom[0][0] = e; mom[0][1] = e * sn * cos(f); mom[0][2] = e * sn * sin(f); mom[0][3] = e * c;
+    mom[1][0] = e; mom[1][1] = -mom[0][1]; mom[1][2] = -mom[0][2]; mom[1][3] = -mom[0][3];
+    return;
+  }
   double q[PS_MAX_FINAL][4];
   double Q[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = 0; i < n; ++i) {
@@ -143,6 +157,22 @@ PS_HD void ps_rambo_massless(ps_stream *s, int n, double rs, double (*mom)[4]) {
     for (int k = 0; k < 3; ++k)
       mom[i][k + 1] = x * (q[i][k + 1] + b[k] * q[i][0] + a * bq * b[k]);
   }
+  /* The boost above loses digits when Q is nearly light-like.  Remove the
+   * residual total 3-momentum, put every parton back on shell (E = |p|) and
+   * rescale to the exact total energy: a change at the 1e-13 level that
+   * makes the point consistent to rounding. */
+  double r[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) r[k] += mom[i][k + 1];
+  double esum = 0.0;
+  for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < 3; ++k) mom[i][k + 1] -= r[k] / (double)n;
+    mom[i][0] = sqrt(mom[i][1] * mom[i][1] + mom[i][2] * mom[i][2] + mom[i][3] * mom[i][3]);
+    esum += mom[i][0];
+  }
+  double f = rs / esum;
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 4; ++k) mom[i][k] *= f;
 }
 
 /* ---- cuts ---------------------------------------------------------------- */

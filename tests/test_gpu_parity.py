@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+FP64 path: every event within 1e-12 relative (the bar stated for the FP64
+path).  Mixed path (FP32 amplitudes, compensated colour amplitudes, flagged
+events re-evaluated in FP64): median relative error <= 1e-6 and maximum
+<= 1e-4.  Event counts span several CTA tiles and end in a ragged tail.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0909_5257_gb300 import phasespace as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# name, pdg, sqrt(s) range, events (several tiles + ragged tail; oracle-affordable)
+CASES = [
+    ("gg>gg", [21] * 4, (200.0, 2000.0), 4099),
+    ("uu~>gg", [2, -2, 21, 21], (200.0, 2000.0), 4099),
+    ("uu>uu", [2, 2, 2, 2], (200.0, 2000.0), 2051),
+    ("gg>ggg", [21] * 5, (200.0, 2000.0), 1037),
+    ("uu~>ggg", [2, -2, 21, 21, 21], (200.0, 2000.0), 1037),
+    ("uu>uug", [2, 2, 2, 2, 21], (200.0, 2000.0), 1037),
+    ("gg>gggg", [21] * 6, (300.0, 3000.0), 131),
+    ("uu~>gggg", [2, -2] + [21] * 4, (300.0, 3000.0), 203),
+    ("uu>uugg", [2, 2, 2, 2, 21, 21], (300.0, 3000.0), 257),
+    ("uu>uuggg", [2, 2, 2, 2, 21, 21, 21], (500.0, 5000.0), 37),
+    ("uu~>ggggg", [2, -2] + [21] * 5, (500.0, 5000.0), 23),
+    ("gg>ggggg", [21] * 7, (500.0, 5000.0), 5),
+]
+
+_ref_cache = {}
+_proc_cache = {}
+
+
+def _mea():
+    from paper_0909_5257_gb300 import mea
+    return mea
+
+
+def _case(name):
+    for c in CASES:
+        if c[0] == name:
+            return c
+    raise KeyError(name)
+
+
+def _data(name):
+    if name not in _ref_cache:
+        _, pdg, (lo, hi), n = _case(name)
+        mom = ps.generate(ps.PhaseSpaceConfig(len(pdg) - 2, rs_lo=lo, rs_hi=hi,
+                                              seed=ps.SEED_BASE + 101), n)
+        ref = oracle.OracleProcess(pdg).me2(mom)
+        _ref_cache[name] = (mom, ref)
+    return _ref_cache[name]
+
+
+def _proc(pdg, **kw):
+    key = (tuple(pdg), tuple(sorted(kw.items())))
+    if key not in _proc_cache:
+        _proc_cache[key] = _mea().Process(pdg, **kw)
+    return _proc_cache[key]
+
+
+def _run(pdg, mom, precision, hel_mode=0, hel=None, **kw):
+    mea = _mea()
+    P = _proc(pdg, **kw)
+    d_mom = torch.from_numpy(mom).cuda()
+    out = torch.full((mom.shape[0],), float("nan"), dtype=torch.float64, device="cuda")
+    flags = torch.zeros(mom.shape[0], dtype=torch.uint8, device="cuda")
+    d_hel = torch.from_numpy(hel).cuda() if hel is not None else None
+    P.evaluate(d_mom, out, hel_mode=hel_mode, hel=d_hel, precision=precision, flags=flags)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), flags.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_fp64_path_matches_oracle(name):
+    _, pdg, _, _ = _case(name)
+    mom, ref = _data(name)
+    got, flags = _run(pdg, mom, _mea().PREC_FP64)
+    rel = np.abs(got / ref - 1.0)
+    assert np.all(np.isfinite(got))
+    assert rel.max() <= 1e-12, f"{name}: max rel {rel.max():.3e} at {int(rel.argmax())}"
+    assert not np.any(flags)
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_mixed_path_matches_oracle(name):
+    _, pdg, _, _ = _case(name)
+    mom, ref = _data(name)
+    got, flags = _run(pdg, mom, _mea().PREC_MIXED)
+    rel = np.abs(got / ref - 1.0)
+    assert np.all(np.isfinite(got))
+    assert np.median(rel) <= 1e-6, f"{name}: median rel {np.median(rel):.3e}"
+    assert rel.max() <= 1e-4, f"{name}: max rel {rel.max():.3e}"
+    # re-evaluated events carry the FP64 result
+    re = (flags & _mea().FLAG_REEVALUATED) != 0
+    if re.any():
+        assert rel[re].max() <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["gg>ggg", "uu~>ggg", "uu>uug", "gg>gggg"])
+def test_per_helicity_given_mode(name):
+    """MEA_HEL_GIVEN: one helicity combination per event, equal to the oracle's
+    colour-summed value of that combination (times 1/4)."""
+    _, pdg, _, _ = _case(name)
+    mom, _ = _data(name)
+    mom = mom[:37]
+    n = len(pdg)
+    _, hel_ref = oracle.OracleProcess(pdg).me2(mom, per_helicity=True)
+    rng = np.random.default_rng(5)
+    hidx = rng.integers(0, 1 << n, size=mom.shape[0])
+    hel = np.array([[1 if (h >> (n - 1 - l)) & 1 else -1 for l in range(n)] for h in hidx], dtype=np.int8)
+    got, _ = _run(pdg, mom, _mea().PREC_FP64, hel_mode=_mea().HEL_GIVEN, hel=hel)
+    want = 0.25 * hel_ref[np.arange(mom.shape[0]), hidx]
+    scale = 0.25 * hel_ref.max(axis=1)
+    assert np.all(np.abs(got - want) <= 1e-12 * np.abs(want) + 1e-24 * scale)
+
+
+@pytest.mark.parametrize("name", ["gg>gg", "uu~>ggg", "uu>uug", "gg>gggg"])
+def test_sum_all_equals_sum_nonzero(name):
+    _, pdg, _, _ = _case(name)
+    mom, ref = _data(name)
+    got, _ = _run(pdg, mom, _mea().PREC_FP64, hel_mode=_mea().HEL_SUM_ALL)
+    assert np.max(np.abs(got / ref - 1.0)) <= 1e-12
+
+
+def test_deterministic_and_batch_independent():
+    """Same inputs give bitwise-identical output, alone or inside a larger batch."""
+    pdg = [21] * 5
+    mom, _ = _data("gg>ggg")
+    a, _ = _run(pdg, mom, _mea().PREC_MIXED)
+    b, _ = _run(pdg, mom, _mea().PREC_MIXED)
+    c, _ = _run(pdg, mom[100:357], _mea().PREC_MIXED)
+    assert np.array_equal(a, b)
+    assert np.array_equal(a[100:357], c)
+    d, _ = _run(pdg, mom, _mea().PREC_FP64)
+    e, _ = _run(pdg, mom[5:6], _mea().PREC_FP64)
+    assert d[5] == e[0]
+
+
+@pytest.mark.parametrize("name", ["gg>ggg", "uu>uug", "uu~>ggg"])
+def test_exact_power_scaling_fp64(name):
+    _, pdg, _, _ = _case(name)
+    mom, _ = _data(name)
+    a, _ = _run(pdg, mom, _mea().PREC_FP64)
+    b, _ = _run(pdg, 4.0 * mom, _mea().PREC_FP64)
+    n = len(pdg)
+    assert np.array_equal(b, a * 4.0 ** (8 - 2 * n))
+
+
+def test_empty_and_single_event():
+    pdg = [2, -2, 21, 21, 21]
+    mom, ref = _data("uu~>ggg")
+    mea = _mea()
+    P = _proc(pdg)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    P.evaluate(torch.from_numpy(mom[:1]).cuda(), out, n_events=0, precision=mea.PREC_FP64)
+    torch.cuda.synchronize()
+    assert out.item() == 0.0
+    got, _ = _run(pdg, mom[:1], mea.PREC_FP64)
+    assert abs(got[0] / ref[0] - 1.0) <= 1e-12
+
+
+def test_device_generator_matches_host_generator():
+    mea = _mea()
+    for nf, (lo, hi) in [(2, (200.0, 2000.0)), (3, (200.0, 2000.0)), (5, (500.0, 5000.0))]:
+        n = 4096
+        cfg = ps.PhaseSpaceConfig(nf, rs_lo=lo, rs_hi=hi, seed=ps.SEED_BASE + 3)
+        host, att_h = ps.generate(cfg, n, first_event=1000, return_attempts=True)
+        dev = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
+        att = torch.empty(n, dtype=torch.int32, device="cuda")
+        mea.generate_phase_space(nf, n, dev, first_event=1000, seed=cfg.seed, rs_lo=lo, rs_hi=hi,
+                                 attempts=att)
+        torch.cuda.synchronize()
+        d = dev.cpu().numpy()
+        same = att.cpu().numpy() == att_h
+        assert same.mean() > 0.999
+        scale = host[same][:, :, 0].max()
+        assert np.abs(d[same] - host[same]).max() <= 1e-12 * scale
+
+
+def test_host_buffer_entry_point():
+    pdg = [21] * 5
+    mom, ref = _data("gg>ggg")
+    mea = _mea()
+    P = _proc(pdg)
+    got, flags = P.evaluate_host(mom, precision=mea.PREC_FP64, with_flags=True)
+    assert np.max(np.abs(got / ref - 1.0)) <= 1e-12
+    dev, _ = _run(pdg, mom, mea.PREC_FP64)
+    assert np.array_equal(got, dev)
+
+
+def test_argument_errors():
+    mea = _mea()
+    with pytest.raises(mea.MeaError) as e:
+        mea.Process([21, 21, 11, 21])
+    assert e.value.status == -2
+    P = _proc([21] * 4)
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(mea.MeaError) as e:
+        P.evaluate(None, out, n_events=4)
+    assert e.value.status == -1
+    with pytest.raises(mea.MeaError) as e:
+        P.evaluate(out, out, n_events=4, hel_mode=mea.HEL_GIVEN, hel=None)
+    assert e.value.status == -1
+
+
+@pytest.mark.parametrize("name,nf,lo,hi", [("gg>ggg", 3, 200.0, 2000.0), ("uu~>ggg", 3, 200.0, 2000.0),
+                                           ("uu>uug", 3, 200.0, 2000.0)])
+def test_full_size_sampled(name, nf, lo, hi):
+    """2^20 events generated on the device and evaluated in the benchmark's
+    launch configuration; a random sample is checked against the oracle."""
+    mea = _mea()
+    _, pdg, _, _ = _case(name)
+    n = 1 << 20
+    mom = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
+    mea.generate_phase_space(nf, n, mom, seed=ps.SEED_BASE + 1, rs_lo=lo, rs_hi=hi)
+    out32 = torch.empty(n, dtype=torch.float64, device="cuda")
+    out64 = torch.empty(n, dtype=torch.float64, device="cuda")
+    P = _proc(pdg)
+    P.evaluate(mom, out32, precision=mea.PREC_MIXED)
+    P.evaluate(mom, out64, precision=mea.PREC_FP64)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(3).choice(n, 96, replace=False))
+    sample = mom[torch.from_numpy(idx).cuda()].cpu().numpy()
+    ref = oracle.OracleProcess(pdg).me2(sample)
+    g32 = out32.cpu().numpy()
+    g64 = out64.cpu().numpy()
+    assert np.all(np.isfinite(g32)) and np.all(np.isfinite(g64))
+    assert np.max(np.abs(g64[idx] / ref - 1.0)) <= 1e-12
+    r32 = np.abs(g32[idx] / ref - 1.0)
+    assert np.median(r32) <= 1e-6 and r32.max() <= 1e-4
+    # every event: mixed within 1e-4 of the FP64 GPU path
+    assert np.max(np.abs(g32 / g64 - 1.0)) <= 1e-4

@@ -146,14 +146,14 @@ def test_two_to_two_closed_forms(pdg, fn):
     mom = events(2, 256)
     got = proc(pdg).me2(mom)
     want = fn(mom)
-    assert np.max(np.abs(got / want - 1.0)) < 1e-11
+    assert np.max(np.abs(got / want - 1.0)) < 1e-13
 
 
 def test_parke_taylor_five_gluons():
     mom = events(3, 64)
     got = proc([21] * 5).me2(mom)
     want = np.array([ref.gluon_me2_leading_colour_exact(m) for m in mom])
-    assert np.max(np.abs(got / want - 1.0)) < 1e-11
+    assert np.max(np.abs(got / want - 1.0)) < 1e-12
 
 
 def test_parke_taylor_four_gluons_equals_closed_form():
