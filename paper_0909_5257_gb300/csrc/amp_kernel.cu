@@ -388,10 +388,11 @@ AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int 
   AmpConfig best;
   best.H = H;
   double best_score = -1;
-  // preference: everything in shared memory, then colour amplitudes in global
-  // memory, then wavefunction slots too
-  const int placements[3][2] = {{1, 1}, {0, 1}, {0, 0}};
-  for (int pl = 0; pl < 3 && best_score <= 0; ++pl) {
+  // preference: everything in shared memory; then the wavefunction slots in
+  // global memory (L1-cached) and the colour amplitudes, which every diagram
+  // updates ~2^(n-3) times, in shared memory; then the reverse; then both global
+  const int placements[4][2] = {{1, 1}, {1, 0}, {0, 1}, {0, 0}};
+  for (int pl = 0; pl < 4 && best_score <= 0; ++pl) {
     bool jsm = placements[pl][0] != 0, ssm = placements[pl][1] != 0;
     for (int E = 1; E * H <= kMaxThreads; ++E) {
       if (hint > 0 && E != hint) continue;
@@ -451,10 +452,12 @@ cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const
   if (c.grid <= 0) return cudaSuccess;
   if (fp64) {
     if (c.jamp_in_smem && c.slots_in_smem) launch_one<double, true, true>(p, c, a, s);
+    else if (c.jamp_in_smem) launch_one<double, true, false>(p, c, a, s);
     else if (c.slots_in_smem) launch_one<double, false, true>(p, c, a, s);
     else launch_one<double, false, false>(p, c, a, s);
   } else {
     if (c.jamp_in_smem && c.slots_in_smem) launch_one<float, true, true>(p, c, a, s);
+    else if (c.jamp_in_smem) launch_one<float, true, false>(p, c, a, s);
     else if (c.slots_in_smem) launch_one<float, false, true>(p, c, a, s);
     else launch_one<float, false, false>(p, c, a, s);
   }

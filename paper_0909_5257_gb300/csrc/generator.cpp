@@ -739,18 +739,21 @@ bool helicity_allowed(const Builder& B, const std::vector<int>& lam) {
   return false;
 }
 
-// Algorithmic real-FLOP cost of each operation (per evaluation, FP32 or FP64).
+// Algorithmic real-FLOP cost of each operation, counted from heget.cuh with
+// real add/sub/mul = 1, complex mul = 6, complex add = 2, real x complex = 2:
+// complex 4-vector dot = 30, real.complex dot = 14, slash(V) psi = 64,
+// slash(P) psi = 42.
 double op_flops(int type) {
   switch (type) {
-    case OP_EXT: return 24;
-    case OP_JVV: return 250;
-    case OP_JGGG: return 150;
-    case OP_FVI: return 140;
-    case OP_FVO: return 140;
-    case OP_JIO: return 110;
-    case OP_AVVV: return 200;
-    case OP_AGGGG: return 140;
-    case OP_AIOV: return 80;
+    case OP_EXT: return 12;
+    case OP_JVV: return 159;
+    case OP_JGGG: return 125;
+    case OP_FVI: return 115;
+    case OP_FVO: return 115;
+    case OP_JIO: return 129;
+    case OP_AVVV: return 204;
+    case OP_AGGGG: return 136;
+    case OP_AIOV: return 96;
   }
   return 0;
 }
