@@ -157,6 +157,37 @@ mea_status mea_evaluate(mea_process_t proc, const double *momenta_dev, int64_t n
 mea_status mea_evaluate_host(mea_process_t proc, const double *momenta_host, int64_t n_events,
                              mea_prec_mode prec, double *me2_host, uint8_t *flags_host);
 
+/* ---- evaluation without allocation ----------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot let the library allocate device memory: applications whose device
+ * memory is owned entirely by a pool allocator of their own (a cudaMalloc
+ * behind the pool's back can fail or fragment it), and latency-critical loops
+ * that cannot afford the implicit device-wide synchronisation of cudaMalloc /
+ * cudaFree.  mea_evaluate may grow per-process scratch with cudaMalloc; this
+ * variant never calls cudaMalloc, cudaFree or any allocating routine.
+ *
+ * Same result as mea_evaluate(proc, momenta_dev, n_events, MEA_HEL_SUM_NONZERO,
+ * NULL, prec, me2_dev, flags_dev, stream).  Its scratch (the flagged-event list
+ * and, for large processes, wavefunction and colour-amplitude work space) is a
+ * fixed array of MEA_NOALLOC_SCRATCH_BYTES in the library's device image,
+ * which every GPU that loads the library holds until the process exits.
+ *   - A request whose scratch would exceed that size is rejected with
+ *     MEA_E_ARG before anything is enqueued (mea_last_error() gives the bytes
+ *     needed); for gg -> ggg the flagged-event list limits n_events to about
+ *     8.38 million per call.
+ *   - The first call on each device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (the event-count word is cleared on the stream at the start of every
+ *     call).  Calls whose GPU work overlaps -- on different streams, or from
+ *     different host threads -- race on the array and give wrong results;
+ *     order them on one stream or with events.
+ *   - The process handle must have been created on the current device. */
+#define MEA_NOALLOC_SCRATCH_BYTES (32u << 20)
+mea_status mea_evaluate_noalloc(mea_process_t proc, const double *momenta_dev, int64_t n_events,
+                                mea_prec_mode prec, double *me2_dev, uint8_t *flags_dev,
+                                void *stream);
+
 /* ---- synthetic phase space (input generator) ------------------------------ */
 
 typedef struct {

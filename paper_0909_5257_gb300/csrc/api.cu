@@ -388,6 +388,97 @@ mea_status mea_evaluate_host(mea_process_t P, const double* mom_h, int64_t n, me
   return MEA_OK;
 }
 
+// ---- evaluation without allocation ------------------------------------------
+// Scratch for mea_evaluate_noalloc: one fixed array in the device image.  Host
+// code must not use its name as a device address; the address is looked up
+// once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MEA_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {nullptr};
+}  // namespace
+
+mea_status mea_evaluate_noalloc(mea_process_t P, const double* mom, int64_t n, mea_prec_mode prec, double* me2,
+                                uint8_t* flags, void* stream) {
+  if (!P) return fail(MEA_E_ARG, "mea_evaluate_noalloc: null process");
+  if (P->host_only) return fail(MEA_E_UNSUPPORTED, "mea_evaluate_noalloc: host-only process handle");
+  if (n < 0 || n > (int64_t)0x7fffffff) return fail(MEA_E_ARG, "mea_evaluate_noalloc: n_events out of range");
+  if (n == 0) return MEA_OK;
+  if (!mom || !me2) return fail(MEA_E_ARG, "mea_evaluate_noalloc: null momenta or me2");
+  if (prec != MEA_PREC_FP64 && prec != MEA_PREC_MIXED) return fail(MEA_E_ARG, "mea_evaluate_noalloc: bad precision");
+  int dev = 0;
+  MEA_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(MEA_E_ARG, "mea_evaluate_noalloc: device index out of range");
+  if (dev != P->device) return fail(MEA_E_ARG, "mea_evaluate_noalloc: process belongs to another device");
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(MEA_E_CUDA, std::string("mea_evaluate_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = p;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  const mea::Program& G = P->prog;
+  const int H = G.n_hel;
+  const bool fp64 = prec == MEA_PREC_FP64;
+  const bool reeval = !fp64 && P->opts.reeval_fp64;
+  mea::AmpConfig c = mea::plan_amp(P->dev, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
+  mea::AmpConfig c2 = mea::plan_amp(P->dev, true, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
+  auto work_bytes = [&](bool f64, const mea::AmpConfig& cc) {
+    size_t jb = (mea::jamp_scratch_bytes_needed(P->dev, f64, cc) + 255) & ~size_t(255);
+    return jb + ((mea::slot_scratch_bytes_needed(P->dev, f64, cc) + 255) & ~size_t(255));
+  };
+  // layout: [count word | flagged-event list | work space shared by both launches]
+  const size_t list_off = 256;
+  const size_t list_bytes = reeval ? (((size_t)n * sizeof(int32_t) + 255) & ~size_t(255)) : 0;
+  const size_t work_off = list_off + list_bytes;
+  size_t work = work_bytes(fp64, c);
+  if (reeval) work = std::max(work, work_bytes(true, c2));
+  const size_t need = work_off + work;
+  if (need > (size_t)MEA_NOALLOC_SCRATCH_BYTES)
+    return fail(MEA_E_ARG, "mea_evaluate_noalloc: request needs " + std::to_string(need) +
+                               " bytes of scratch, the fixed array holds " +
+                               std::to_string((size_t)MEA_NOALLOC_SCRATCH_BYTES));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* b = reinterpret_cast<char*>(base);
+  auto place = [&](bool f64, const mea::AmpConfig& cc, mea::AmpLaunch& a) {
+    size_t jb = (mea::jamp_scratch_bytes_needed(P->dev, f64, cc) + 255) & ~size_t(255);
+    a.jamp_scratch = reinterpret_cast<float*>(b + work_off);
+    a.slot_scratch = reinterpret_cast<float*>(b + work_off + jb);
+  };
+  std::lock_guard<std::mutex> lk(P->mu);
+  mea::AmpLaunch a;
+  a.mom = mom;
+  a.n_events = n;
+  a.hel_mode = 0;
+  a.me2 = me2;
+  a.flags = flags;
+  a.flag_threshold = (float)P->opts.flag_threshold;
+  place(fp64, c, a);
+  if (reeval) {
+    MEA_CUDA(cudaMemsetAsync(b, 0, sizeof(int32_t), s));  // the count must start at zero every call
+    a.flag_count = reinterpret_cast<int32_t*>(b);
+    a.flag_list = reinterpret_cast<int32_t*>(b + list_off);
+  }
+  MEA_CUDA(mea::launch_amp(P->dev, fp64, c, a, s));
+  if (reeval) {
+    mea::AmpLaunch r = a;
+    r.event_list = a.flag_list;
+    r.list_count = a.flag_count;
+    r.flag_list = nullptr;
+    r.flag_count = nullptr;
+    r.write_flags_mode = 1;
+    place(true, c2, r);
+    MEA_CUDA(mea::launch_amp(P->dev, true, c2, r, s));
+  }
+  return MEA_OK;
+}
+
 mea_status mea_generate_phase_space(const mea_ps_config* cfg, uint64_t first_event, int64_t n, double* mom,
                                     int32_t* attempts, void* stream) {
   if (!cfg || n < 0) return fail(MEA_E_ARG, "mea_generate_phase_space: bad arguments");

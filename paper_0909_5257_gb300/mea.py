@@ -73,12 +73,13 @@ def load(path: str | None = None):
             lib.mea_destroy_process.argtypes = [vp]
             lib.mea_evaluate.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp, vp]
             lib.mea_evaluate_host.argtypes = [vp, vp, i64, i32, vp, vp]
+            lib.mea_evaluate_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp]
             lib.mea_generate_phase_space.argtypes = [vp, ctypes.c_uint64, i64, vp, vp, vp]
             lib.mea_last_error.restype = ctypes.c_char_p
             lib.mea_kernel_launch_count.restype = ctypes.c_uint64
             for name in ("mea_create_process", "mea_create_process_host_only", "mea_process_info",
                          "mea_colour_matrix", "mea_helicities", "mea_destroy_process", "mea_evaluate",
-                         "mea_evaluate_host", "mea_generate_phase_space"):
+                         "mea_evaluate_host", "mea_evaluate_noalloc", "mea_generate_phase_space"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -172,6 +173,14 @@ class Process:
             n_events = int(momenta.shape[0])
         _check(load().mea_evaluate(self._h, _ptr(momenta), n_events, hel_mode, _ptr(hel), precision,
                                    _ptr(me2), _ptr(flags), _stream(stream)))
+
+    def evaluate_noalloc(self, momenta, me2, n_events=None, precision=PREC_MIXED, flags=None, stream=None):
+        """mea_evaluate_noalloc: same result as evaluate() with the helicity sum,
+        using only the library's fixed device scratch array (no allocation)."""
+        if n_events is None:
+            n_events = int(momenta.shape[0])
+        _check(load().mea_evaluate_noalloc(self._h, _ptr(momenta), n_events, precision, _ptr(me2),
+                                           _ptr(flags), _stream(stream)))
 
     def evaluate_host(self, momenta: np.ndarray, precision=PREC_MIXED, with_flags=False):
         """|M|^2 of host momenta through the library's pinned, pipelined copies."""
