@@ -110,6 +110,21 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def shard_first_event(rank: int, n_per_rank: int) -> int:
+    """Weak scaling: rank r evaluates events [r*n, (r+1)*n) of the seeded stream."""
+    return rank * n_per_rank
+
+
+def max_over_ranks_value(x: float, dist=None, device=None) -> float:
+    """Max of a host scalar over all ranks (timing only; no data-path collective)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -210,11 +225,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_value(x, dist, "cuda")
 
     subs, n, seed_off = WORKLOADS[args.workload]
     stream = torch.cuda.current_stream()
@@ -223,7 +234,8 @@ def main():
         P = mea.Process(pdg)
         m = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
         # weak scaling: every rank evaluates its own slice of the event stream
-        mea.generate_phase_space(nf, n, m, first_event=rank * n, seed=SEED_BASE + seed_off, rs_lo=lo, rs_hi=hi)
+        mea.generate_phase_space(nf, n, m, first_event=shard_first_event(rank, n), seed=SEED_BASE + seed_off,
+                                 rs_lo=lo, rs_hi=hi)
         procs.append(P)
         moms.append(m)
         outs.append(torch.empty(n, dtype=torch.float64, device="cuda"))

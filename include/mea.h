@@ -139,6 +139,11 @@ mea_status mea_helicities(mea_process_t proc, int8_t *hel, int cap, int *n_hel);
 
 mea_status mea_destroy_process(mea_process_t proc);
 
+/* Synchronise `stream` and report whether any bounded device wait of this
+ * process's kernels expired since the last check (MEA_E_TIMEOUT; the affected
+ * results are invalid).  Resets the indicator. */
+mea_status mea_check_status(mea_process_t proc, void *stream);
+
 /* ---- evaluation ----------------------------------------------------------- */
 
 /* me2_dev[n_events] (double, device) <- |M|^2 of every event.
@@ -157,6 +162,90 @@ mea_status mea_evaluate(mea_process_t proc, const double *momenta_dev, int64_t n
 mea_status mea_evaluate_host(mea_process_t proc, const double *momenta_host, int64_t n_events,
                              mea_prec_mode prec, double *me2_host, uint8_t *flags_host);
 
+/* ---- autotuning ------------------------------------------------------------
+ * Times the candidate tile shapes and data placements of the amplitude kernel
+ * for this process on n_sample events of momenta_dev (device) with the given
+ * precision, keeps the fastest for later mea_evaluate calls of that precision
+ * (helicity sum over the non-vanishing combinations), and reports it.  The
+ * paper scanned register caps and block sizes by hand (Sec. 5.2); this is the
+ * automated counterpart.  Synchronous; overwrites nothing the caller owns
+ * except scratch_me2_dev (double[n_sample], device). */
+typedef struct {
+  int threads;           /* threads per CTA */
+  int events_per_cta;    /* events per tile */
+  int grid;              /* CTAs launched */
+  int colour_amps_in_shared;  /* 1: colour amplitudes in shared memory */
+  int slots_in_shared;   /* 1: wavefunction slots in shared memory */
+  int candidates;        /* configurations timed */
+  double best_ms;        /* time of the chosen configuration on the sample */
+  double default_ms;     /* time of the heuristic default on the sample */
+} mea_tune_result;
+
+mea_status mea_autotune(mea_process_t proc, const double *momenta_dev, int64_t n_sample,
+                        mea_prec_mode prec, double *scratch_me2_dev, mea_tune_result *out);
+
+/* ---- batched launch ---------------------------------------------------------
+ * Several subprocesses of uneven size evaluated by one CUDA-graph launch.
+ * mea_batch_create evaluates every item once (eagerly, to size scratch and
+ * load kernels), then captures one evaluation of every item -- each on its own
+ * branch of the graph, so that independent subprocesses run concurrently --
+ * and instantiates the graph.  mea_batch_launch replays it on `stream`: it
+ * re-reads the items' momenta buffers and rewrites their me2/flags buffers
+ * (same pointers and event counts as at creation).  Items must not alias each
+ * other's outputs.  The batch owns its scratch (one set per item). */
+typedef struct {
+  mea_process_t proc;
+  const double *momenta_dev;
+  int64_t n_events;
+  double *me2_dev;
+  uint8_t *flags_dev;   /* nullable */
+} mea_batch_item;
+
+typedef struct mea_batch_s *mea_batch_t;
+
+mea_status mea_batch_create(const mea_batch_item *items, int n_items, mea_prec_mode prec,
+                            mea_batch_t *out);
+mea_status mea_batch_launch(mea_batch_t batch, void *stream);
+/* Kernel nodes in the batch's graph (kernels launched per mea_batch_launch). */
+mea_status mea_batch_info(mea_batch_t batch, int *n_kernel_nodes);
+mea_status mea_batch_destroy(mea_batch_t batch);
+
+/* ---- serving loop -----------------------------------------------------------
+ * Continuous batching of evaluation requests on one GPU.  A worker thread owns
+ * n_slots CUDA streams; each request (a process, device momenta and output
+ * buffers) is split into chunks of at most chunk_events events, and chunks of
+ * all admitted requests are dispatched to free slots in arrival order, so that
+ * requests arriving while others run are admitted as slots free up and their
+ * work overlaps on the device.  Admission is by memory: every request reserves
+ * the scratch bytes its chunks need (library estimate) from mem_budget_bytes
+ * until it completes; a request that can never fit is rejected at submission
+ * (MEA_E_REJECTED), others wait in a queue.  Per-event results do not depend on
+ * chunking or on the other requests in flight (bitwise), because every event
+ * is evaluated by the same arithmetic in any tile.
+ * Thread-safe.  The caller keeps the buffers alive until the request is
+ * complete.  No call blocks without a bound: mea_server_wait returns
+ * MEA_E_TIMEOUT when timeout_ms expires. */
+typedef struct mea_server_s *mea_server_t;
+
+typedef struct {
+  uint64_t submitted, completed, rejected;
+  uint64_t events_completed;
+  double p50_ms, p99_ms, max_ms;  /* latency submit -> completion observed */
+  double busy_seconds;            /* wall time with at least one chunk in flight */
+  size_t reserved_bytes;          /* scratch currently reserved by admitted requests */
+} mea_server_stats_t;
+
+mea_status mea_server_create(size_t mem_budget_bytes, int n_slots, int64_t chunk_events, mea_server_t *out);
+mea_status mea_server_submit(mea_server_t srv, mea_process_t proc, const double *momenta_dev, int64_t n_events,
+                             mea_prec_mode prec, double *me2_dev, uint8_t *flags_dev, uint64_t *req_id);
+/* Wait up to timeout_ms (< 0: 10 minutes) for the request; returns its status
+ * (MEA_OK, MEA_E_TIMEOUT, or the error it failed with).  *latency_ms (nullable)
+ * receives submit-to-completion time. */
+mea_status mea_server_wait(mea_server_t srv, uint64_t req_id, int timeout_ms, double *latency_ms);
+mea_status mea_server_stats(mea_server_t srv, mea_server_stats_t *out);
+/* Stops accepting work, waits (bounded) for in-flight chunks, frees everything. */
+mea_status mea_server_destroy(mea_server_t srv);
+
 /* ---- evaluation without allocation ----------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot let the library allocate device memory: applications whose device
@@ -167,7 +256,10 @@ mea_status mea_evaluate_host(mea_process_t proc, const double *momenta_host, int
  * variant never calls cudaMalloc, cudaFree or any allocating routine.
  *
  * Same result as mea_evaluate(proc, momenta_dev, n_events, MEA_HEL_SUM_NONZERO,
- * NULL, prec, me2_dev, flags_dev, stream).  Its scratch (the flagged-event list
+ * NULL, prec, me2_dev, flags_dev, stream), except that the colour sum always
+ * runs on CUDA cores: where mea_evaluate would use the tensor-core colour stage
+ * (MEA_PREC_MIXED with a colour basis of 96 or more, or colour_mode 2) the two
+ * agree within the mixed-path tolerance instead of bitwise.  Its scratch (the flagged-event list
  * and, for large processes, wavefunction and colour-amplitude work space) is a
  * fixed array of MEA_NOALLOC_SCRATCH_BYTES in the library's device image,
  * which every GPU that loads the library holds until the process exits.

@@ -17,8 +17,12 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmea.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["generator.cpp", "amp_kernel.cu", "ps_kernel.cu", "api.cu"]
-HEADERS = ["generator.h", "kernels.h", "heget.cuh", "../phasespace/phasespace.h", "../../include/mea.h"]
+SOURCES = ["generator.cpp", "amp_kernel.cu", "ps_kernel.cu", "api.cu", "colour_gemm.cu", "batch.cu", "server.cu"]
+HEADERS = ["generator.h", "kernels.h", "colour_gemm.h", "process.h", "heget.cuh", "amp_common.cuh", "gen_kernel.cuh", "codegen.cpp",
+           "../phasespace/phasespace.h", "../../include/mea.h"]
+# Processes whose straight-line kernels are emitted at build time (live state
+# small enough for registers); every other process runs on the interpreter.
+GENERATED = ["21,21,21,21", "2,-2,21,21", "2,2,2,2", "21,21,21,21,21", "2,-2,21,21,21", "2,2,2,2,21"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -59,8 +63,29 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    # 1. emit the straight-line per-process kernels with the generator
+    tool = os.path.join(BUILD_DIR, "mea_codegen")
+    r = subprocess.run(["g++", "-O2", "-std=c++17", "-fopenmp", "-o", tool, os.path.join(CSRC, "codegen.cpp"),
+                        os.path.join(CSRC, "generator.cpp")], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"codegen tool build failed:\n{r.stderr}")
+    gen_cu = os.path.join(BUILD_DIR, "generated.cu")
+    r = subprocess.run([tool, gen_cu] + GENERATED, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"codegen failed:\n{r.stderr}")
+
+    def compile_generated(_):
+        obj = os.path.join(BUILD_DIR, "generated.cu.o")
+        cmd = [cc] + common + ["-I", CSRC, "-c", gen_cu, "-o", obj]
+        rr = subprocess.run(cmd, capture_output=True, text=True)
+        if rr.returncode != 0:
+            raise RuntimeError(f"nvcc failed on generated.cu:\n{rr.stdout}\n{rr.stderr}")
+        return obj
+
+    # 2. compile everything in parallel
+    jobs = [(compile_one, s) for s in SOURCES] + [(compile_generated, None)]
+    with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        objs = list(ex.map(lambda j: j[0](j[1]), jobs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fopenmp", "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -20,9 +20,12 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <string>
 #include <type_traits>
+#include <vector>
 
 #include "../../include/mea.h"
+#include "amp_common.cuh"
 #include "heget.cuh"
 #include "kernels.h"
 
@@ -42,12 +45,6 @@ union OpWords {
   Op op;
 };
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  float bp = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
-}
-
 template <typename R>
 __device__ __forceinline__ W4<R> ld_slot(const R* slots, int s, int L, int t) {
   const R* b = slots + (size_t)s * 8 * L + t;
@@ -66,55 +63,6 @@ __device__ __forceinline__ void st_slot(R* slots, int s, int L, int t, const W4<
   for (int k = 0; k < 4; ++k) {
     b[(2 * k) * L] = w.c[k].r;
     b[(2 * k + 1) * L] = w.c[k].i;
-  }
-}
-
-// FP64 preparation of one leg or one mask row of one event.
-template <typename R>
-__device__ void prep_item(const DevProgram& P, const double* mom, int k, R* tab) {
-  const int n_ext = P.n_ext;
-  if (k < n_ext) {
-    const double* p = mom + 4 * k;
-    R* o = tab + 8 * k;
-    int type = P.leg_info[4 * k];
-    double px = p[1], py = p[2], pz = p[3];
-    double kt2 = px * px + py * py;
-    double kk = sqrt(kt2 + pz * pz);
-    if (type == 0) {
-      double kt = sqrt(kt2);
-      double ct, st, cp, sp;
-      if (kt > 0.0) { ct = pz / kk; st = kt / kk; cp = px / kt; sp = py / kt; }
-      else { ct = pz < 0.0 ? -1.0 : 1.0; st = 0.0; cp = 1.0; sp = 0.0; }
-      o[0] = (R)(ct * cp); o[1] = (R)(ct * sp); o[2] = (R)(-st);
-      o[3] = (R)(-sp); o[4] = (R)(cp); o[5] = (R)0;
-      o[6] = (R)0; o[7] = (R)0;
-    } else {
-      // chi_+ = (a, b) with a = sqrt((|p|+pz)/(2|p|)), b = (px + i py)/sqrt(2|p|(|p|+pz));
-      // |p| + pz evaluated without cancellation for pz < 0.
-      double apz = (pz >= 0.0) ? kk + pz : kt2 / (kk - pz);
-      double a, br, bi;
-      if (apz > 0.0) {
-        double nrm = 1.0 / sqrt(2.0 * kk * apz);
-        a = apz * nrm; br = px * nrm; bi = py * nrm;
-      } else {  // exactly along -z: chi_+ = (0, 1)
-        a = 0.0; br = 1.0; bi = 0.0;
-      }
-      o[0] = (R)sqrt(2.0 * p[0]); o[1] = (R)a; o[2] = (R)br; o[3] = (R)bi;
-      o[4] = o[5] = o[6] = o[7] = (R)0;
-    }
-  } else {
-    int row = k - n_ext;
-    uint32_t msk = P.masks[row];
-    double q[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int l = 0; l < n_ext; ++l)
-      if (msk >> l & 1u) {
-        double s = P.leg_info[4 * l + 2] ? -1.0 : 1.0;  // flowing-out momentum
-        for (int mu = 0; mu < 4; ++mu) q[mu] += s * mom[4 * l + mu];
-      }
-    R* o = tab + 8 * n_ext + 5 * row;
-    double q2 = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3];
-    for (int mu = 0; mu < 4; ++mu) o[mu] = (R)q[mu];
-    o[4] = (__popc(msk) > 1) ? (R)(1.0 / q2) : (R)0;
   }
 }
 
@@ -161,15 +109,7 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t ev0 = tile * E;
     // ---- phase 0: FP64 preparation
-    const int items = n_ext + P.n_masks;
-    for (int i = t; i < E * items; i += L) {
-      int e = i / items, k = i - e * items;
-      int64_t ev = ev0 + e;
-      if (ev < n) {
-        int64_t gev = listed ? (int64_t)A.event_list[ev] : ev;
-        prep_item<R>(P, A.mom + (size_t)gev * n_ext * 4, k, tab + (size_t)e * tab_stride);
-      }
-    }
+    tile_prep<R>(P, A, tab, tab_stride, ev0, n, E, t, L);
     __syncthreads();
 
     // ---- phase 1: one (event, helicity) per lane
@@ -306,6 +246,23 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
           }
         }
       }
+      if (A.jamp_out) {
+        // split colour stage: hand the colour amplitudes to the tensor-core kernel
+        if constexpr (F32) {
+          const int64_t pair = ev * H + h;
+          float* jr = A.jamp_out + (size_t)(2 * pair) * A.ldj;
+          float* ji = jr + A.ldj;
+          float jabs = 0.f;
+          for (int a = 0; a < m; ++a) {
+            const R* ja = jam + (size_t)a * JW * L + t;
+            float ar = ja[0] + ja[2 * L], ai = ja[L] + ja[3 * L];
+            jr[a] = ar;
+            ji[a] = ai;
+            jabs += fabsf(ar) + fabsf(ai);
+          }
+          A.pair_kappa[pair] = (jabs > 0.f) ? abs_mass / jabs : 0.f;
+        }
+      } else {
       // ---- colour sum: sum_ab J_a K_ab J_b^* / D
       R tot = (R)0;
       float jabs = 0.f;
@@ -330,42 +287,14 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
       val = (double)tot * P.cf_inv_den;
       if (F32) kappa = (jabs > 0.f) ? abs_mass / jabs : 0.f;
       bad = isfinite(val) ? 0 : 1;
+      }
     }
     res[t] = bad ? __longlong_as_double(0x7ff8000000000000ll) : val;
     kap[t] = kappa;
     __syncthreads();
 
     // ---- phase 2: helicity sum per event, fixed order
-    if (t < E) {
-      int64_t evr = ev0 + t;
-      if (evr < n) {
-        int64_t gev = listed ? (int64_t)A.event_list[evr] : evr;
-        double s = 0.0, wk = 0.0;
-        for (int hh = 0; hh < H; ++hh) {
-          double v = res[t * H + hh];
-          s += v;
-          wk += v * (double)kap[t * H + hh];
-          if (A.pair_out) A.pair_out[gev * H + hh] = v;
-        }
-        double me = 0.25 * s;
-        A.me2[gev] = me;
-        uint8_t fl = 0;
-        if (!isfinite(me)) fl |= MEA_FLAG_NONFINITE;
-        if (F32) {
-          // relative error indicator: FP32 unit roundoff x cancellation in J
-          double ind = (s > 0.0) ? 5.96e-8 * wk / s : 0.0;
-          if (!(ind <= (double)A.flag_threshold)) fl |= MEA_FLAG_CANCEL;
-        }
-        if (A.flags) {
-          if (A.write_flags_mode == 0) A.flags[gev] = fl;
-          else A.flags[gev] = (uint8_t)((A.flags[gev] & ~MEA_FLAG_CANCEL) | MEA_FLAG_REEVALUATED | fl);
-        }
-        if (A.flag_list && (fl & (MEA_FLAG_CANCEL | MEA_FLAG_NONFINITE))) {
-          int slot = atomicAdd(A.flag_count, 1);
-          A.flag_list[slot] = (int32_t)gev;
-        }
-      }
-    }
+    if (!A.jamp_out) tile_finish<F32>(A, t, E, H, ev0, n, listed, res, kap);
     __syncthreads();
   }
 }
@@ -381,10 +310,93 @@ size_t smem_bytes(const DevProgram& p, int threads, int E, bool jsmem, bool ssme
   return b;
 }
 
+__global__ void finish_kernel(const AmpLaunch A, int H, const double* pairval, const float* pk) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= A.n_events) return;
+  double s = 0.0, wk = 0.0;
+  for (int h = 0; h < H; ++h) {
+    double v = pairval[e * H + h];
+    s += v;
+    wk += v * (double)pk[e * H + h];
+  }
+  double me = 0.25 * s;
+  A.me2[e] = me;
+  uint8_t fl = 0;
+  if (!isfinite(me)) fl |= MEA_FLAG_NONFINITE;
+  double ind = (s > 0.0) ? 5.96e-8 * wk / s : 0.0;
+  if (!(ind <= (double)A.flag_threshold)) fl |= MEA_FLAG_CANCEL;
+  if (A.flags) A.flags[e] = fl;
+  if (A.flag_list && (fl & (MEA_FLAG_CANCEL | MEA_FLAG_NONFINITE))) {
+    int slot = atomicAdd(A.flag_count, 1);
+    A.flag_list[slot] = (int32_t)e;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_finish(const AmpLaunch& a, int H, const double* pairval, const float* pair_kappa,
+                          cudaStream_t s) {
+  if (a.n_events <= 0) return cudaSuccess;
+  int threads = 256;
+  int64_t blocks = (a.n_events + threads - 1) / threads;
+  finish_kernel<<<(unsigned)blocks, threads, 0, s>>>(a, H, pairval, pair_kappa);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) ++launch_counter();
+  return e;
+}
+
+const GenEntry* find_generated(const int* pdg, int n_ext) {
+  int n = 0;
+  const GenEntry* t = generated_table(&n);
+  std::string key;
+  for (int i = 0; i < n_ext; ++i) key += (i ? "," : "") + std::to_string(pdg[i]);
+  for (int i = 0; i < n; ++i)
+    if (key == t[i].key) return &t[i];
+  return nullptr;
+}
+
+// Straight-line kernels keep the lane state in registers: pick the tile so
+// that threads <= kGenMaxThreads with few idle lanes, then fill the SMs by
+// occupancy.
+static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms) {
+  AmpConfig best;
+  best.H = H;
+  best.jamp_in_smem = true;
+  best.slots_in_smem = true;
+  const void* k = fp64 ? p.gen->kernel_f64() : p.gen->kernel_f32();
+  const int tab_stride = 8 * p.n_ext + 5 * p.n_masks;
+  cudaFuncAttributes fa;
+  int max_threads = 256;
+  if (cudaFuncGetAttributes(&fa, k) == cudaSuccess) max_threads = std::min(max_threads, fa.maxThreadsPerBlock);
+  double best_score = -1;
+  for (int E = 1; E * H <= max_threads; ++E) {
+    int threads = ((E * H + 31) / 32) * 32;
+    if (threads > max_threads) break;
+    size_t sm = (((size_t)E * tab_stride * (fp64 ? 8 : 4) + 7) & ~size_t(7)) + (size_t)threads * 12 + 16;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, sm) != cudaSuccess) per_sm = 0;
+    if (per_sm < 1) continue;  // this tile cannot be resident: skip it
+    double util = (double)(E * H) / threads;
+    double score = std::min<double>((double)per_sm * threads, 1024.0) * util;
+    if (score > best_score + 1e-9) {
+      best_score = score;
+      best.E_cta = E; best.threads = threads; best.smem = sm; best.grid = per_sm * num_sms;
+    }
+  }
+  if (best_score < 0) {  // nothing resident at all: one warp per tile
+    best.E_cta = std::max(1, 32 / std::max(H, 1));
+    best.threads = ((best.E_cta * H + 31) / 32) * 32;
+    best.smem = (((size_t)best.E_cta * tab_stride * (fp64 ? 8 : 4) + 7) & ~size_t(7)) + (size_t)best.threads * 12 + 16;
+    best.grid = num_sms;
+  }
+  int64_t tiles = (n_events + best.E_cta - 1) / best.E_cta;
+  if (tiles < best.grid) best.grid = (int)std::max<int64_t>(tiles, 1);
+  return best;
+}
 
 AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms,
                    size_t max_smem, size_t smem_per_sm, int hint) {
+  if (p.gen && hint == 0) return plan_generated(p, fp64, H, n_events, num_sms);
   AmpConfig best;
   best.H = H;
   double best_score = -1;
@@ -430,6 +442,62 @@ AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int 
   return best;
 }
 
+std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms,
+                                         size_t max_smem, size_t smem_per_sm) {
+  std::vector<AmpConfig> out;
+  auto cap = [&](AmpConfig c) {
+    int64_t tiles = (n_events + c.E_cta - 1) / c.E_cta;
+    if (tiles < c.grid) c.grid = (int)std::max<int64_t>(tiles, 1);
+    return c;
+  };
+  if (p.gen) {
+    const void* k = fp64 ? p.gen->kernel_f64() : p.gen->kernel_f32();
+    cudaFuncAttributes fa;
+    int max_threads = 256;
+    if (cudaFuncGetAttributes(&fa, k) == cudaSuccess) max_threads = std::min(max_threads, fa.maxThreadsPerBlock);
+    const int tab_stride = 8 * p.n_ext + 5 * p.n_masks;
+    int last_threads = -1;
+    for (int E = 1; E * H <= max_threads; ++E) {
+      int threads = ((E * H + 31) / 32) * 32;
+      if (threads > max_threads) break;
+      // the largest E for each thread count (fewest idle lanes)
+      if ((E + 1) * H <= max_threads && (((E + 1) * H + 31) / 32) * 32 == threads) continue;
+      if (threads == last_threads) continue;
+      last_threads = threads;
+      AmpConfig c;
+      c.H = H; c.E_cta = E; c.threads = threads;
+      c.smem = (((size_t)E * tab_stride * (fp64 ? 8 : 4) + 7) & ~size_t(7)) + (size_t)threads * 12 + 16;
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, c.smem) != cudaSuccess || per_sm < 1)
+        continue;
+      c.grid = per_sm * num_sms;
+      out.push_back(cap(c));
+    }
+    return out;
+  }
+  const int placements[4][2] = {{1, 1}, {1, 0}, {0, 1}, {0, 0}};
+  for (auto& pl : placements) {
+    int last_threads = -1;
+    for (int E = 1; E * H <= kMaxThreads; ++E) {
+      int threads = ((E * H + 31) / 32) * 32;
+      if ((E + 1) * H <= kMaxThreads && (((E + 1) * H + 31) / 32) * 32 == threads) continue;
+      if (threads == last_threads) continue;
+      last_threads = threads;
+      size_t sm = fp64 ? smem_bytes<double>(p, threads, E, pl[0], pl[1]) : smem_bytes<float>(p, threads, E, pl[0], pl[1]);
+      if (sm > max_smem) break;
+      int per_sm = (int)std::min<size_t>(smem_per_sm / std::max<size_t>(sm, 1), 2048 / threads);
+      per_sm = std::min(per_sm, 32);
+      if (per_sm < 1) continue;
+      AmpConfig c;
+      c.H = H; c.E_cta = E; c.threads = threads; c.smem = sm;
+      c.jamp_in_smem = pl[0] != 0; c.slots_in_smem = pl[1] != 0;
+      c.grid = per_sm * num_sms;
+      out.push_back(cap(c));
+    }
+  }
+  return out;
+}
+
 size_t jamp_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig& c) {
   if (c.jamp_in_smem) return 0;
   const int JW = fp64 ? 2 : 4;
@@ -450,6 +518,12 @@ static void launch_one(const DevProgram& p, const AmpConfig& c, const AmpLaunch&
 cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const AmpLaunch& a,
                        cudaStream_t s) {
   if (c.grid <= 0) return cudaSuccess;
+  if (p.gen) {
+    p.gen->launch(fp64, p, c, a, s);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess) ++launch_counter();
+    return err;
+  }
   if (fp64) {
     if (c.jamp_in_smem && c.slots_in_smem) launch_one<double, true, true>(p, c, a, s);
     else if (c.jamp_in_smem) launch_one<double, true, false>(p, c, a, s);

@@ -2,6 +2,7 @@
 // residency of the process tables, scratch management and the evaluation
 // entry points.  No compute happens here; every step of the path runs in the
 // CUDA kernels of amp_kernel.cu and ps_kernel.cu.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -14,8 +15,10 @@
 #include <vector>
 
 #include "../../include/mea.h"
+#include "colour_gemm.h"
 #include "generator.h"
 #include "kernels.h"
+#include "process.h"
 
 namespace {
 
@@ -33,46 +36,8 @@ mea_status fail(mea_status s, const std::string& msg) {
       return fail(MEA_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-  cudaError_t ensure(size_t b) {
-    if (b <= bytes) return cudaSuccess;
-    release();
-    cudaError_t e = cudaMalloc(&p, b);
-    if (e == cudaSuccess) bytes = b;
-    return e;
-  }
-};
-
 }  // namespace
 
-struct mea_process_s {
-  mea::Program prog;
-  mea::DevProgram dev;
-  mea_options opts;
-  int device = 0;
-  int num_sms = 0;
-  size_t smem_optin = 0, smem_per_sm = 0;
-  std::vector<void*> owned;
-  std::mutex mu;
-  // scratch sets: 0 for mea_evaluate, 1 and 2 for the two host-pipeline streams
-  struct Scratch { DevBuf s32, s64, flag_list, flag_count; } scr[3];
-  // host-buffer pipeline
-  void* pin_in[2] = {nullptr, nullptr};
-  void* pin_out[2] = {nullptr, nullptr};
-  void* pin_flags[2] = {nullptr, nullptr};
-  DevBuf d_in[2], d_out[2], d_flags[2];
-  cudaStream_t st[2] = {nullptr, nullptr};
-  cudaEvent_t done[2] = {nullptr, nullptr};
-  int64_t pipe_chunk = 0;
-  bool host_only = false;
-};
 
 namespace {
 
@@ -91,12 +56,7 @@ cudaError_t upload(mea_process_s* P, const std::vector<T>& v, const T** out) {
 void destroy(mea_process_s* P) {
   if (!P) return;
   for (void* d : P->owned) cudaFree(d);
-  for (auto& x : P->scr) {
-    x.s32.release();
-    x.s64.release();
-    x.flag_list.release();
-    x.flag_count.release();
-  }
+  for (auto& x : P->scr) x.release();
   for (int i = 0; i < 2; ++i) {
     if (P->pin_in[i]) cudaFreeHost(P->pin_in[i]);
     if (P->pin_out[i]) cudaFreeHost(P->pin_out[i]);
@@ -110,7 +70,7 @@ void destroy(mea_process_s* P) {
   delete P;
 }
 
-cudaError_t place_scratch(DevBuf& buf, const mea::DevProgram& d, bool fp64, const mea::AmpConfig& c,
+cudaError_t place_scratch(mea::DevBuf& buf, const mea::DevProgram& d, bool fp64, const mea::AmpConfig& c,
                           mea::AmpLaunch& a) {
   size_t jb = (mea::jamp_scratch_bytes_needed(d, fp64, c) + 255) & ~size_t(255);
   size_t sb = mea::slot_scratch_bytes_needed(d, fp64, c);
@@ -121,14 +81,106 @@ cudaError_t place_scratch(DevBuf& buf, const mea::DevProgram& d, bool fp64, cons
   return cudaSuccess;
 }
 
-mea_status do_evaluate(mea_process_s* P, int set, const double* mom, int64_t n, mea_hel_mode hm,
+bool use_tensor_colour(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode hm) {
+  if (prec != MEA_PREC_MIXED || hm == MEA_HEL_GIVEN || P->opts.colour_mode == 1) return false;
+  if (P->opts.colour_mode == 2) return true;
+  return P->prog.n_colour >= 96;
+}
+
+// Mixed path with the colour contraction on the tensor cores, in event chunks
+// whose FP32 colour amplitudes stay below ~256 MB: amplitude kernel (writes J),
+// colour GEMM, helicity sum + flags, FP64 re-evaluation of flagged events.
+mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* mom, int64_t n, mea_hel_mode hm,
+                          double* me2, uint8_t* flags, cudaStream_t s) {
+  const mea::Program& G = P->prog;
+  const int n_ext = G.n_ext;
+  const int H = (hm == MEA_HEL_SUM_NONZERO) ? G.n_hel : (1 << n_ext);
+  const int m = G.n_colour;
+  const int ldj = ((m + 15) / 16) * 16;
+  const size_t per_event = (size_t)H * 2 * ldj * sizeof(float);
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((256u << 20) / per_event)));
+  MEA_CUDA(S.jbuf.ensure(per_event * (size_t)chunk));
+  MEA_CUDA(S.pairval.ensure(sizeof(double) * (size_t)H * chunk));
+  MEA_CUDA(S.pairk.ensure(sizeof(float) * (size_t)H * chunk));
+  MEA_CUDA(S.flag_list.ensure(sizeof(int32_t) * (size_t)chunk));
+  MEA_CUDA(S.flag_count.ensure(sizeof(int32_t)));
+  mea::DevProgram dp = P->dev;
+  dp.gen = nullptr;  // the interpreter writes the colour amplitudes
+  mea::ColourGemmArgs cg;
+  cg.m = m;
+  cg.ldj = ldj;
+  cg.nc = std::min(256, ((m + 15) / 16) * 16);
+  cg.np = ((m + cg.nc - 1) / cg.nc) * cg.nc;
+  cg.kp = ((m + 63) / 64) * 64;
+  cg.tmem_cols = 32;
+  while (cg.tmem_cols < cg.nc) cg.tmem_cols *= 2;
+  cg.b_hi = P->cf_hi;
+  cg.b_lo = P->cf_lo;
+  cg.inv_den = P->dev.cf_inv_den;
+  cg.status = P->status;
+  for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+    const int64_t cn = std::min(chunk, n - c0);
+    mea::AmpConfig c = mea::plan_amp(dp, false, H, cn, P->num_sms, P->smem_optin, P->smem_per_sm);
+    if (P->tuned[0].grid > 0 && P->tuned_H[0] == H) {  // configuration chosen by mea_autotune
+      c = P->tuned[0];
+      int64_t tiles = (cn + c.E_cta - 1) / c.E_cta;
+      if (tiles < c.grid) c.grid = (int)std::max<int64_t>(tiles, 1);
+    }
+    mea::AmpLaunch a;
+    a.mom = mom + (size_t)c0 * n_ext * 4;
+    a.n_events = cn;
+    a.hel_mode = (int)hm;
+    a.me2 = me2 + c0;
+    a.flags = flags ? flags + c0 : nullptr;
+    a.flag_threshold = (float)P->opts.flag_threshold;
+    a.jamp_out = reinterpret_cast<float*>(S.jbuf.p);
+    a.pair_kappa = reinterpret_cast<float*>(S.pairk.p);
+    a.ldj = ldj;
+    MEA_CUDA(place_scratch(S.s32, dp, false, c, a));
+    MEA_CUDA(mea::launch_amp(dp, false, c, a, s));
+    cg.J = reinterpret_cast<const float*>(S.jbuf.p);
+    cg.n_pairs = cn * H;
+    cg.pairval = reinterpret_cast<double*>(S.pairval.p);
+    MEA_CUDA(mea::launch_colour_gemm(cg, P->num_sms, s));
+    mea::AmpLaunch f = a;
+    f.jamp_out = nullptr;
+    bool reeval = P->opts.reeval_fp64 != 0;
+    if (reeval) {
+      MEA_CUDA(cudaMemsetAsync(S.flag_count.p, 0, sizeof(int32_t), s));
+      f.flag_list = reinterpret_cast<int32_t*>(S.flag_list.p);
+      f.flag_count = reinterpret_cast<int32_t*>(S.flag_count.p);
+    }
+    MEA_CUDA(mea::launch_finish(f, H, reinterpret_cast<const double*>(S.pairval.p),
+                                reinterpret_cast<const float*>(S.pairk.p), s));
+    if (reeval) {
+      mea::AmpConfig c2 = mea::plan_amp(P->dev, true, H, cn, P->num_sms, P->smem_optin, P->smem_per_sm);
+      mea::AmpLaunch b = f;
+      b.event_list = f.flag_list;
+      b.list_count = f.flag_count;
+      b.flag_list = nullptr;
+      b.flag_count = nullptr;
+      b.write_flags_mode = 1;
+      MEA_CUDA(place_scratch(S.s64, P->dev, true, c2, b));
+      MEA_CUDA(mea::launch_amp(P->dev, true, c2, b, s));
+    }
+  }
+  return MEA_OK;
+}
+
+mea_status do_evaluate(mea_process_s* P, mea::EvalScratch& S, const double* mom, int64_t n, mea_hel_mode hm,
                        const int8_t* hel, mea_prec_mode prec, double* me2, uint8_t* flags,
                        cudaStream_t s) {
+  if (use_tensor_colour(P, prec, hm)) return do_evaluate_tc(P, S, mom, n, hm, me2, flags, s);
   const mea::Program& G = P->prog;
   int H = (hm == MEA_HEL_SUM_NONZERO) ? G.n_hel : (hm == MEA_HEL_SUM_ALL ? (1 << G.n_ext) : 1);
   bool fp64 = prec == MEA_PREC_FP64;
-  mea_process_s::Scratch& S = P->scr[set];
   mea::AmpConfig c = mea::plan_amp(P->dev, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
+  const int ti = fp64 ? 1 : 0;
+  if (P->tuned[ti].grid > 0 && P->tuned_H[ti] == H) {  // configuration chosen by mea_autotune
+    c = P->tuned[ti];
+    int64_t tiles = (n + c.E_cta - 1) / c.E_cta;
+    if (tiles < c.grid) c.grid = (int)std::max<int64_t>(tiles, 1);
+  }
   mea::AmpLaunch a;
   a.mom = mom;
   a.n_events = n;
@@ -163,6 +215,36 @@ mea_status do_evaluate(mea_process_s* P, int set, const double* mom, int64_t n, 
 }
 
 }  // namespace
+
+namespace mea {
+mea_status set_error(mea_status s, const std::string& msg) { return fail(s, msg); }
+mea_status evaluate_with(mea_process_s* P, EvalScratch& S, const double* mom, int64_t n, mea_hel_mode hm,
+                         const int8_t* hel, mea_prec_mode prec, double* me2, uint8_t* flags, cudaStream_t s) {
+  return do_evaluate(P, S, mom, n, hm, hel, prec, me2, flags, s);
+}
+
+size_t scratch_estimate(mea_process_s* P, int64_t n, mea_prec_mode prec) {
+  const Program& G = P->prog;
+  const int H = G.n_hel;
+  const bool fp64 = prec == MEA_PREC_FP64;
+  auto work = [&](const DevProgram& d, bool f64, int64_t ne) {
+    AmpConfig c = plan_amp(d, f64, H, ne, P->num_sms, P->smem_optin, P->smem_per_sm);
+    return jamp_scratch_bytes_needed(d, f64, c) + slot_scratch_bytes_needed(d, f64, c) + 512;
+  };
+  if (use_tensor_colour(P, prec, MEA_HEL_SUM_NONZERO)) {
+    const int ldj = ((G.n_colour + 15) / 16) * 16;
+    const size_t per_event = (size_t)H * 2 * ldj * sizeof(float);
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((256u << 20) / per_event)));
+    DevProgram dp = P->dev;
+    dp.gen = nullptr;
+    return per_event * (size_t)chunk + (size_t)H * chunk * 12 + (size_t)chunk * 4 + work(dp, false, chunk) +
+           work(P->dev, true, chunk);
+  }
+  size_t b = work(P->dev, fp64, n);
+  if (!fp64 && P->opts.reeval_fp64) b += (size_t)n * 4 + 256 + work(P->dev, true, n);
+  return b;
+}
+}  // namespace mea
 
 extern "C" {
 
@@ -248,6 +330,29 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
   D.n_hel = G.n_hel;
   D.hel_all = dhall;
   D.g = std::sqrt(4.0 * M_PI * P->opts.alpha_s);
+  D.gen = (P->opts.colour_mode == 2) ? nullptr : mea::find_generated(pdg, n_ext);
+  {
+    std::vector<__half> hi(G.cf_num.size()), lo(G.cf_num.size());
+    bool exact = true;
+    for (size_t i = 0; i < G.cf_num.size(); ++i) {
+      hi[i] = __float2half_rn((float)G.cf_num[i]);
+      double r = (double)G.cf_num[i] - (double)__half2float(hi[i]);
+      lo[i] = __float2half_rn((float)r);
+      if (r != 0.0) exact = false;
+    }
+    const __half* dh = nullptr;
+    const __half* dl = nullptr;
+    std::vector<int> st(1, 0);
+    const int* dst = nullptr;
+    if ((e = upload(P, hi, &dh)) != cudaSuccess || (!exact && (e = upload(P, lo, &dl)) != cudaSuccess) ||
+        (e = upload(P, st, &dst)) != cudaSuccess) {
+      destroy(P);
+      return fail(MEA_E_CUDA, std::string("mea_create_process: ") + cudaGetErrorString(e));
+    }
+    P->cf_hi = dh;
+    P->cf_lo = exact ? nullptr : dl;
+    P->status = const_cast<int*>(dst);
+  }
   *out = P;
   return MEA_OK;
 }
@@ -304,6 +409,21 @@ mea_status mea_helicities(mea_process_t P, int8_t* hel, int cap, int* n_hel) {
   return MEA_OK;
 }
 
+mea_status mea_check_status(mea_process_t P, void* stream) {
+  if (!P) return fail(MEA_E_ARG, "mea_check_status: null process");
+  if (P->host_only) return MEA_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  MEA_CUDA(cudaStreamSynchronize(s));
+  int v = 0;
+  MEA_CUDA(cudaMemcpy(&v, P->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) {
+    int z = 0;
+    MEA_CUDA(cudaMemcpy(P->status, &z, sizeof(int), cudaMemcpyHostToDevice));
+    return fail(MEA_E_TIMEOUT, "mea_check_status: a bounded wait in the tensor-core colour kernel expired");
+  }
+  return MEA_OK;
+}
+
 mea_status mea_destroy_process(mea_process_t P) {
   if (!P) return fail(MEA_E_ARG, "mea_destroy_process: null handle");
   if (!P->host_only) cudaDeviceSynchronize();
@@ -323,7 +443,7 @@ mea_status mea_evaluate(mea_process_t P, const double* mom, int64_t n, mea_hel_m
   if (hm == MEA_HEL_GIVEN && !hel) return fail(MEA_E_ARG, "mea_evaluate: MEA_HEL_GIVEN needs hel_dev");
   if (prec != MEA_PREC_FP64 && prec != MEA_PREC_MIXED) return fail(MEA_E_ARG, "mea_evaluate: bad precision");
   std::lock_guard<std::mutex> lk(P->mu);
-  return do_evaluate(P, 0, mom, n, hm, hel, prec, me2, flags, reinterpret_cast<cudaStream_t>(stream));
+  return do_evaluate(P, P->scr[0], mom, n, hm, hel, prec, me2, flags, reinterpret_cast<cudaStream_t>(stream));
 }
 
 mea_status mea_evaluate_host(mea_process_t P, const double* mom_h, int64_t n, mea_prec_mode prec,
@@ -373,7 +493,7 @@ mea_status mea_evaluate_host(mea_process_t P, const double* mom_h, int64_t n, me
     std::memcpy(P->pin_in[b], mom_h + (size_t)c0 * n_ext * 4, sizeof(double) * 4 * n_ext * cn);
     MEA_CUDA(cudaMemcpyAsync(P->d_in[b].p, P->pin_in[b], sizeof(double) * 4 * n_ext * cn,
                              cudaMemcpyHostToDevice, P->st[b]));
-    s = do_evaluate(P, 1 + b, reinterpret_cast<const double*>(P->d_in[b].p), cn, MEA_HEL_SUM_NONZERO, nullptr, prec,
+    s = do_evaluate(P, P->scr[1 + b], reinterpret_cast<const double*>(P->d_in[b].p), cn, MEA_HEL_SUM_NONZERO, nullptr, prec,
                     reinterpret_cast<double*>(P->d_out[b].p), reinterpret_cast<uint8_t*>(P->d_flags[b].p), P->st[b]);
     if (s != MEA_OK) return s;
     MEA_CUDA(cudaMemcpyAsync(P->pin_out[b], P->d_out[b].p, sizeof(double) * cn, cudaMemcpyDeviceToHost, P->st[b]));

@@ -1,0 +1,229 @@
+// Autotuner and batched launch (C ABI, declared in include/mea.h).
+//
+// mea_autotune times every candidate tile shape / shared-memory placement of
+// a process's amplitude kernel on a sample and keeps the fastest.
+// mea_batch_* evaluate several subprocesses of very uneven cost with one
+// CUDA-graph launch: the graph holds one evaluation per item, each on its own
+// branch so that independent subprocesses fill the GPU together; it is
+// captured once and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "process.h"
+
+#define MEA_CK(call)                                                                          \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return mea::set_error(MEA_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct mea_batch_s {
+  std::vector<mea_batch_item> items;
+  mea_prec_mode prec = MEA_PREC_MIXED;
+  std::vector<mea::EvalScratch> scratch;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaStream_t origin = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int kernel_nodes = 0;
+};
+
+namespace {
+
+void destroy_batch(mea_batch_s* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  for (auto e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  for (auto& s : b->scratch) s.release();
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+mea_status mea_autotune(mea_process_t P, const double* mom, int64_t n, mea_prec_mode prec, double* me2,
+                        mea_tune_result* out) {
+  if (!P || !mom || !me2 || n <= 0) return mea::set_error(MEA_E_ARG, "mea_autotune: bad arguments");
+  if (P->host_only) return mea::set_error(MEA_E_UNSUPPORTED, "mea_autotune: host-only process handle");
+  if (prec != MEA_PREC_FP64 && prec != MEA_PREC_MIXED) return mea::set_error(MEA_E_ARG, "mea_autotune: bad precision");
+  std::lock_guard<std::mutex> lk(P->mu);
+  const bool fp64 = prec == MEA_PREC_FP64;
+  const int ti = fp64 ? 1 : 0;
+  const int H = P->prog.n_hel;
+  mea::DevProgram dp = P->dev;
+  const bool tc = !fp64 && P->opts.colour_mode != 1 && (P->opts.colour_mode == 2 || P->prog.n_colour >= 96);
+  if (tc) dp.gen = nullptr;  // the tensor-core colour path runs the interpreter
+  std::vector<mea::AmpConfig> cands =
+      mea::candidate_configs(dp, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
+  mea::AmpConfig def = mea::plan_amp(dp, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
+  cands.insert(cands.begin(), def);
+  cudaStream_t s;
+  MEA_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  MEA_CK(cudaEventCreate(&e0));
+  MEA_CK(cudaEventCreate(&e1));
+  mea::EvalScratch S;
+  double best = 1e30, def_ms = 0;
+  int best_i = 0;
+  mea_status st = MEA_OK;
+  for (size_t i = 0; i < cands.size() && st == MEA_OK; ++i) {
+    const mea::AmpConfig& c = cands[i];
+    mea::AmpLaunch a;
+    a.mom = mom;
+    a.n_events = n;
+    a.me2 = me2;
+    a.flag_threshold = (float)P->opts.flag_threshold;
+    size_t jb = (mea::jamp_scratch_bytes_needed(dp, fp64, c) + 255) & ~size_t(255);
+    size_t sb = mea::slot_scratch_bytes_needed(dp, fp64, c);
+    mea::DevBuf& buf = fp64 ? S.s64 : S.s32;
+    if (buf.ensure(jb + sb + 256) != cudaSuccess) continue;  // too large: skip the candidate
+    a.jamp_scratch = reinterpret_cast<float*>(buf.p);
+    a.slot_scratch = reinterpret_cast<float*>(reinterpret_cast<char*>(buf.p) + jb);
+    double t_best = 1e30;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, s);
+      cudaError_t le = mea::launch_amp(dp, fp64, c, a, s);
+      cudaEventRecord(e1, s);
+      if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { t_best = 1e30; cudaGetLastError(); break; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t_best = std::min<double>(t_best, ms);
+    }
+    if (i == 0) def_ms = t_best;
+    if (t_best < best) { best = t_best; best_i = (int)i; }
+  }
+  S.release();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (best >= 1e30) return mea::set_error(MEA_E_CUDA, "mea_autotune: no candidate ran");
+  mea::AmpConfig c = cands[best_i];
+  // keep the per-SM residency; the grid is re-capped per call
+  c.grid = std::max(c.grid, P->num_sms);
+  if (best_i != 0) {
+    // store the full-size grid of this shape
+    std::vector<mea::AmpConfig> full =
+        mea::candidate_configs(dp, fp64, H, (int64_t)1 << 40, P->num_sms, P->smem_optin, P->smem_per_sm);
+    for (auto& f : full)
+      if (f.E_cta == c.E_cta && f.threads == c.threads && f.jamp_in_smem == c.jamp_in_smem &&
+          f.slots_in_smem == c.slots_in_smem)
+        c.grid = f.grid;
+    P->tuned[ti] = c;
+    P->tuned_H[ti] = H;
+  } else {
+    P->tuned[ti] = mea::AmpConfig();  // the heuristic default won: keep using it
+    P->tuned_H[ti] = 0;
+  }
+  if (out) {
+    out->threads = c.threads;
+    out->events_per_cta = c.E_cta;
+    out->grid = c.grid;
+    out->colour_amps_in_shared = c.jamp_in_smem ? 1 : 0;
+    out->slots_in_shared = c.slots_in_smem ? 1 : 0;
+    out->candidates = (int)cands.size();
+    out->best_ms = best;
+    out->default_ms = def_ms;
+  }
+  return MEA_OK;
+}
+
+mea_status mea_batch_create(const mea_batch_item* items, int n_items, mea_prec_mode prec, mea_batch_t* out) {
+  if (!items || n_items <= 0 || !out) return mea::set_error(MEA_E_ARG, "mea_batch_create: bad arguments");
+  if (prec != MEA_PREC_FP64 && prec != MEA_PREC_MIXED) return mea::set_error(MEA_E_ARG, "mea_batch_create: bad precision");
+  for (int i = 0; i < n_items; ++i) {
+    const mea_batch_item& it = items[i];
+    if (!it.proc || it.proc->host_only || it.n_events < 0 || (it.n_events > 0 && (!it.momenta_dev || !it.me2_dev)))
+      return mea::set_error(MEA_E_ARG, "mea_batch_create: bad item " + std::to_string(i));
+  }
+  *out = nullptr;
+  mea_batch_s* b = new mea_batch_s();
+  b->items.assign(items, items + n_items);
+  b->prec = prec;
+  b->scratch.resize(n_items);
+  auto bail = [&](mea_status st) {
+    destroy_batch(b);
+    return st;
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < n_items && e == cudaSuccess; ++i) {
+    cudaStream_t s;
+    cudaEvent_t j;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) { b->streams.push_back(s); e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming); }
+    if (e == cudaSuccess) b->joins.push_back(j);
+  }
+  if (e != cudaSuccess) return bail(mea::set_error(MEA_E_CUDA, std::string("mea_batch_create: ") + cudaGetErrorString(e)));
+  // eager pass: sizes every scratch set and loads every kernel
+  for (int i = 0; i < n_items; ++i) {
+    const mea_batch_item& it = b->items[i];
+    if (it.n_events == 0) continue;
+    std::lock_guard<std::mutex> lk(it.proc->mu);
+    mea_status st = mea::evaluate_with(it.proc, b->scratch[i], it.momenta_dev, it.n_events, MEA_HEL_SUM_NONZERO,
+                                       nullptr, prec, it.me2_dev, it.flags_dev, b->streams[i]);
+    if (st != MEA_OK) return bail(st);
+  }
+  for (auto s : b->streams)
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return bail(mea::set_error(MEA_E_CUDA, std::string("mea_batch_create: ") + cudaGetErrorString(e)));
+  // capture: fork from the origin stream, one branch per item, join back
+  uint64_t k0 = mea::launch_counter();
+  e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return bail(mea::set_error(MEA_E_CUDA, std::string("mea_batch_create: ") + cudaGetErrorString(e)));
+  mea_status cst = MEA_OK;
+  cudaEventRecord(b->fork, b->origin);
+  for (int i = 0; i < n_items && cst == MEA_OK; ++i) {
+    const mea_batch_item& it = b->items[i];
+    cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+    if (it.n_events > 0) {
+      std::lock_guard<std::mutex> lk(it.proc->mu);
+      cst = mea::evaluate_with(it.proc, b->scratch[i], it.momenta_dev, it.n_events, MEA_HEL_SUM_NONZERO, nullptr,
+                               prec, it.me2_dev, it.flags_dev, b->streams[i]);
+    }
+    cudaEventRecord(b->joins[i], b->streams[i]);
+    cudaStreamWaitEvent(b->origin, b->joins[i], 0);
+  }
+  e = cudaStreamEndCapture(b->origin, &b->graph);
+  if (cst != MEA_OK) return bail(cst);
+  if (e != cudaSuccess) return bail(mea::set_error(MEA_E_CUDA, std::string("mea_batch_create: capture: ") + cudaGetErrorString(e)));
+  b->kernel_nodes = (int)(mea::launch_counter() - k0);
+  mea::launch_counter() = k0;  // captured launches run only when the graph is launched
+  e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) return bail(mea::set_error(MEA_E_CUDA, std::string("mea_batch_create: instantiate: ") + cudaGetErrorString(e)));
+  *out = b;
+  return MEA_OK;
+}
+
+mea_status mea_batch_launch(mea_batch_t b, void* stream) {
+  if (!b || !b->exec) return mea::set_error(MEA_E_ARG, "mea_batch_launch: null batch");
+  MEA_CK(cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)));
+  mea::launch_counter() += (uint64_t)b->kernel_nodes;
+  return MEA_OK;
+}
+
+mea_status mea_batch_info(mea_batch_t b, int* n_kernel_nodes) {
+  if (!b || !n_kernel_nodes) return mea::set_error(MEA_E_ARG, "mea_batch_info: null argument");
+  *n_kernel_nodes = b->kernel_nodes;
+  return MEA_OK;
+}
+
+mea_status mea_batch_destroy(mea_batch_t b) {
+  if (!b) return mea::set_error(MEA_E_ARG, "mea_batch_destroy: null batch");
+  cudaStreamSynchronize(b->origin);
+  destroy_batch(b);
+  return MEA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+// Straight-line CUDA emitter: turns a process program into a per-process
+// kernel whose wavefunctions and colour amplitudes live in registers.
+//
+// The emitted body is the same program the interpreter runs (same ops, same
+// order, same device functions from heget.cuh), written out with one SSA
+// variable per op and the colour matrix as literal constants, so that nvcc
+// allocates registers and schedules across ops.  It is used for the small
+// processes (n_ext <= 5) whose live state fits in registers; larger processes
+// stay on the table-driven interpreter.
+//
+// Usage (build step): mea_codegen <out.cu> <pdg,pdg,...> [<pdg,...> ...]
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <sstream>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "generator.h"
+
+namespace {
+
+std::string key_of(const std::vector<int>& pdg) {
+  std::string k;
+  for (size_t i = 0; i < pdg.size(); ++i) k += (i ? "," : "") + std::to_string(pdg[i]);
+  return k;
+}
+
+std::string ident_of(const std::vector<int>& pdg) {
+  std::string k = "p";
+  for (int c : pdg) k += (c < 0 ? "_m" + std::to_string(-c) : "_" + std::to_string(c));
+  return k;
+}
+
+std::string lit(double v) {
+  char b[64];
+  std::snprintf(b, sizeof b, "%.17g", v);
+  std::string s(b);
+  if (s.find('.') == std::string::npos && s.find('e') == std::string::npos) s += ".0";
+  return "R(" + s + ")";
+}
+
+void emit_body(std::ostringstream& o, const mea::Program& P, const std::string& id) {
+  using namespace mea;
+  const int m = P.n_colour;
+  o << "template <typename R>\nstruct Body_" << id << " {\n";
+  o << "  static constexpr int kColour = " << m << ";\n";
+  o << "  __device__ __forceinline__ static void run(const R* __restrict__ et, const R* __restrict__ mt,\n"
+       "                                             uint32_t lam, R g, R gg, double inv_den, double& val,\n"
+       "                                             float& kappa) {\n";
+  o << "    cx<R> J[" << m << "];\n    cx<R> Jl[" << m << "];\n";
+  o << "#pragma unroll\n    for (int a = 0; a < " << m << "; ++a) { J[a] = mk<R>(R(0), R(0)); Jl[a] = J[a]; }\n";
+  o << "    float mass = 0.f;\n";
+  std::vector<int> slot_op(P.n_slots + 1, -1);
+  for (size_t i = 0; i < P.ops.size(); ++i) {
+    const Op& op = P.ops[i];
+    auto in = [&](int k) { return "w" + std::to_string(slot_op[op.in[k]]); };
+    auto mrow = [&](int r) { return "mt + " + std::to_string(5 * r); };
+    auto minv = [&](int r) { return "mt[" + std::to_string(5 * r + 4) + "]"; };
+    std::string w = "w" + std::to_string(i);
+    switch (op.type) {
+      case OP_EXT: {
+        int l = op.leg;
+        std::string lam = "((lam >> " + std::to_string(l) + ") & 1u ? 1 : -1)";
+        if (P.leg_type[l] == 0) {
+          o << "    const W4<R> " << w << " = ext_gluon<R>(et + " << 8 * l << ", et + " << 8 * l + 3 << ", "
+            << lam << ", " << (P.incoming[l] ? "false" : "true") << ");\n";
+        } else {
+          int kind = P.leg_type[l] == 1 ? (P.incoming[l] ? 0 : 1) : (P.incoming[l] ? 3 : 2);
+          o << "    const W4<R> " << w << " = ext_spinor<R>(et[" << 8 * l << "], et[" << 8 * l + 1 << "], mk<R>(et["
+            << 8 * l + 2 << "], et[" << 8 * l + 3 << "]), " << lam << ", " << kind << ");\n";
+        }
+        break;
+      }
+      case OP_JVV:
+        o << "    const W4<R> " << w << " = jvv<R>(" << in(0) << ", " << in(1) << ", " << mrow(op.min[0]) << ", "
+          << mrow(op.min[1]) << ", " << minv(op.mout) << ", g);\n";
+        break;
+      case OP_JGGG:
+        o << "    const W4<R> " << w << " = jggg<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", "
+          << minv(op.mout) << ", gg);\n";
+        break;
+      case OP_FVI:
+        o << "    const W4<R> " << w << " = fvi<R>(" << in(0) << ", " << in(1) << ", " << mrow(op.mout) << ", "
+          << minv(op.mout) << ", g);\n";
+        break;
+      case OP_FVO:
+        o << "    const W4<R> " << w << " = fvo<R>(" << in(0) << ", " << in(1) << ", " << mrow(op.mout) << ", "
+          << minv(op.mout) << ", g);\n";
+        break;
+      case OP_JIO:
+        o << "    const W4<R> " << w << " = jio<R>(" << in(0) << ", " << in(1) << ", " << minv(op.mout) << ", g);\n";
+        break;
+      case OP_AVVV:
+      case OP_AGGGG:
+      case OP_AIOV: {
+        o << "    {\n      const cx<R> a = ";
+        if (op.type == OP_AVVV)
+          o << "vvv_amp<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", " << mrow(op.min[0]) << ", "
+            << mrow(op.min[1]) << ", " << mrow(op.min[2]) << ", g);\n";
+        else if (op.type == OP_AGGGG)
+          o << "gggg_amp<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", " << in(3) << ", gg);\n";
+        else
+          o << "iov_amp<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", g);\n";
+        for (uint32_t k = 0; k < op.col_count; ++k) {
+          const ColEntry& c = P.col[op.col_begin + k];
+          o << "      jacc<R>(J[" << c.alpha << "], Jl[" << c.alpha << "], mass, R(" << (int)c.re << "), R("
+            << (int)c.im << "), a);\n";
+        }
+        o << "    }\n";
+        break;
+      }
+      default:
+        throw std::runtime_error("codegen: unknown op");
+    }
+    if (op.type <= OP_JIO) slot_op[op.out] = (int)i;
+  }
+  // colour quadratic form with the integer colour matrix (symmetric)
+  o << "    cx<R> F[" << m << "];\n    float jabs = 0.f;\n";
+  o << "#pragma unroll\n    for (int a = 0; a < " << m << "; ++a) { F[a] = jfin<R>(J[a], Jl[a]); jabs += "
+       "(float)(fabs(F[a].r) + fabs(F[a].i)); }\n";
+  o << "    R tot = R(0);\n";
+  for (int a = 0; a < m; ++a) {
+    std::ostringstream z;
+    bool any = false;
+    for (int b = a; b < m; ++b) {
+      int64_t k = P.cf_num[(size_t)a * m + b];
+      if (!k) continue;
+      double c = (b == a) ? (double)k : 2.0 * (double)k;
+      z << "      z += " << lit(c) << " * (F[" << a << "].r * F[" << b << "].r + F[" << a << "].i * F[" << b
+        << "].i);\n";
+      any = true;
+    }
+    if (any) o << "    {\n      R z = R(0);\n" << z.str() << "      tot += z;\n    }\n";
+  }
+  o << "    val = (double)tot * inv_den;\n";
+  o << "    kappa = (jabs > 0.f) ? mass / jabs : 0.f;\n";
+  o << "  }\n};\n\n";
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  if (argc < 3) {
+    std::fprintf(stderr, "usage: %s out.cu pdg,pdg,... [...]\n", argv[0]);
+    return 2;
+  }
+  std::ostringstream o;
+  o << "// Generated by mea_codegen from the process generator; do not edit.\n"
+       "#include \"gen_kernel.cuh\"\n\nnamespace mea {\nnamespace {\n\n";
+  std::vector<std::pair<std::string, std::string>> entries;
+  for (int i = 2; i < argc; ++i) {
+    std::vector<int> pdg;
+    std::string s = argv[i];
+    size_t pos = 0;
+    while (pos < s.size()) {
+      size_t e = s.find(',', pos);
+      if (e == std::string::npos) e = s.size();
+      pdg.push_back(std::atoi(s.substr(pos, e - pos).c_str()));
+      pos = e + 1;
+    }
+    mea::Program P = mea::build_program(pdg);
+    std::string id = ident_of(pdg);
+    emit_body(o, P, id);
+    entries.push_back({key_of(pdg), id});
+  }
+  o << "}  // namespace\n\n";
+  o << "const GenEntry* generated_table(int* n) {\n  static const GenEntry t[] = {\n";
+  for (auto& e : entries)
+    o << "    {\"" << e.first << "\", &gen_launch<Body_" << e.second << "<float>, Body_" << e.second
+      << "<double>>, &gen_kernel_ptr<Body_" << e.second << "<float>, float>, &gen_kernel_ptr<Body_" << e.second
+      << "<double>, double>},\n";
+  o << "  };\n  *n = " << entries.size() << ";\n  return t;\n}\n\n}  // namespace mea\n";
+  FILE* f = std::fopen(argv[1], "w");
+  if (!f) return 1;
+  std::string txt = o.str();
+  std::fwrite(txt.data(), 1, txt.size(), f);
+  std::fclose(f);
+  return 0;
+}

@@ -1,0 +1,113 @@
+// Kernel template for the straight-line per-process bodies that codegen.cpp
+// emits.  Same tile structure as the interpreter (amp_kernel.cu): FP64
+// preparation of the per-event tables in shared memory, one lane per
+// (event, helicity) running the process body with all wavefunctions and
+// colour amplitudes in registers, fixed-order helicity sum.  Only the
+// per-event tables and the lane results use shared memory.
+#pragma once
+#include <type_traits>
+
+#include "amp_common.cuh"
+
+namespace mea {
+namespace {
+
+constexpr int kGenMaxThreads = 256;
+
+// J += (cr + i ci) a, two-sum compensated in FP32 (lo collects the rounding
+// errors); mass accumulates sum |c a| for the cancellation indicator.
+template <typename R>
+__device__ __forceinline__ void jacc(cx<R>& hi, cx<R>& lo, float& mass, R cr, R ci, cx<R> a) {
+  R xr = cr * a.r - ci * a.i;
+  R xi = cr * a.i + ci * a.r;
+  if constexpr (std::is_same<R, float>::value) {
+    float s, e;
+    two_sum(hi.r, xr, s, e);
+    hi.r = s;
+    lo.r += e;
+    two_sum(hi.i, xi, s, e);
+    hi.i = s;
+    lo.i += e;
+    mass += fabsf(xr) + fabsf(xi);
+  } else {
+    hi.r += xr;
+    hi.i += xi;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ cx<R> jfin(cx<R> hi, cx<R> lo) {
+  if constexpr (std::is_same<R, float>::value) return cx<R>{hi.r + lo.r, hi.i + lo.i};
+  return hi;
+}
+
+template <typename R, typename Body>
+__global__ void __launch_bounds__(kGenMaxThreads) gen_kernel(const DevProgram P, const AmpLaunch A,
+                                                             const AmpConfig C) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr bool F32 = std::is_same<R, float>::value;
+  const int L = blockDim.x;
+  const int t = threadIdx.x;
+  const int n_ext = P.n_ext, H = C.H, E = C.E_cta;
+  const int tab_stride = 8 * n_ext + 5 * P.n_masks;
+  R* tab = reinterpret_cast<R*>(smem);
+  size_t off = ((size_t)E * tab_stride * sizeof(R) + 7) & ~size_t(7);
+  double* res = reinterpret_cast<double*>(smem + off);
+  off += (size_t)L * sizeof(double);
+  float* kap = reinterpret_cast<float*>(smem + off);
+
+  const bool listed = A.event_list != nullptr;
+  const int64_t n = listed ? (int64_t)(*A.list_count) : A.n_events;
+  const int64_t n_tiles = (n + E - 1) / E;
+  const R g = (R)P.g;
+  const R gg = (R)(P.g * P.g);
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t ev0 = tile * E;
+    tile_prep<R>(P, A, tab, tab_stride, ev0, n, E, t, L);
+    __syncthreads();
+    const int e = t / H, h = t - (t / H) * H;
+    const int64_t ev = ev0 + e;
+    const bool active = (t < E * H) && (ev < n);
+    double val = 0.0;
+    float kappa = 0.f;
+    if (active) {
+      const int64_t gev = listed ? (int64_t)A.event_list[ev] : ev;
+      uint32_t lam = 0;
+      for (int l = 0; l < n_ext; ++l) {
+        int8_t v;
+        if (A.hel_mode == 0) v = P.hel[h * n_ext + l];
+        else if (A.hel_mode == 1) v = P.hel_all[h * n_ext + l];
+        else v = A.hel_given[gev * n_ext + l];
+        if (v > 0) lam |= 1u << l;
+      }
+      const R* et = tab + (size_t)e * tab_stride;
+      Body::run(et, et + 8 * n_ext, lam, g, gg, P.cf_inv_den, val, kappa);
+      if (!isfinite(val)) val = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    res[t] = val;
+    kap[t] = kappa;
+    __syncthreads();
+    tile_finish<F32>(A, t, E, H, ev0, n, listed, res, kap);
+    __syncthreads();
+  }
+}
+
+template <typename BodyF, typename BodyD>
+void gen_launch(bool fp64, const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
+  if (fp64) {
+    cudaFuncSetAttribute(gen_kernel<double, BodyD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    gen_kernel<double, BodyD><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
+  } else {
+    cudaFuncSetAttribute(gen_kernel<float, BodyF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    gen_kernel<float, BodyF><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
+  }
+}
+
+template <typename Body, typename R>
+const void* gen_kernel_ptr() {
+  return reinterpret_cast<const void*>(gen_kernel<R, Body>);
+}
+
+}  // namespace
+}  // namespace mea

@@ -1,11 +1,27 @@
 // Host-side declarations of the CUDA kernels' launch helpers.
 #pragma once
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "generator.h"
 
 namespace mea {
+
+struct DevProgram;
+struct AmpConfig;
+struct AmpLaunch;
+
+// A straight-line per-process kernel emitted by codegen.cpp at build time.
+struct GenEntry {
+  const char* key;  // PDG codes joined by commas
+  void (*launch)(bool fp64, const DevProgram&, const AmpConfig&, const AmpLaunch&, cudaStream_t);
+  const void* (*kernel_f32)();
+  const void* (*kernel_f64)();
+};
+const GenEntry* generated_table(int* n);
+const GenEntry* find_generated(const int* pdg, int n_ext);
 
 // Device copy of a process program (all pointers are device memory).
 struct DevProgram {
@@ -25,6 +41,7 @@ struct DevProgram {
   int n_hel = 0;
   const int8_t* hel_all = nullptr;    // [2^n_ext][n_ext]
   double g = 0;                       // g_s
+  const GenEntry* gen = nullptr;      // straight-line kernel of this process, if emitted
 };
 
 struct AmpLaunch {
@@ -41,6 +58,9 @@ struct AmpLaunch {
   int32_t* flag_list = nullptr;       // mixed path: indices of flagged events are appended here
   int32_t* flag_count = nullptr;
   double* pair_out = nullptr;         // optional [event][H] per-helicity values (tests)
+  float* jamp_out = nullptr;          // split colour stage: write J rows [2*pair][ldj] (FP32) and
+  float* pair_kappa = nullptr;        //   the per-pair indicator instead of the colour sum
+  int ldj = 0;
   float* jamp_scratch = nullptr;      // global colour-amplitude accumulators when not in SMEM
   float* slot_scratch = nullptr;      // global wavefunction slots when not in SMEM
 };
@@ -59,11 +79,19 @@ struct AmpConfig {
 AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms,
                    size_t max_smem_per_block, size_t smem_per_sm, int events_per_tile_hint = 0);
 
+// Every distinct tile shape / placement worth timing (autotuner).
+std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms,
+                                         size_t max_smem, size_t smem_per_sm);
+
 size_t jamp_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig& c);
 size_t slot_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig& c);
 
 cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const AmpLaunch& a,
                        cudaStream_t s);
+
+// Helicity sum + flags for the split colour stage: me2 = 1/4 sum_h pairval.
+cudaError_t launch_finish(const AmpLaunch& a, int H, const double* pairval, const float* pair_kappa,
+                          cudaStream_t s);
 
 // Phase-space generator kernel (input generator).
 struct PsConfigDev {

@@ -1,0 +1,85 @@
+// Internal definitions shared by the C ABI translation units (api.cu,
+// batch.cu, server.cu): the process handle and the evaluation driver.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mea.h"
+#include "generator.h"
+#include "kernels.h"
+
+namespace mea {
+
+// Growable device buffer (cudaMalloc on growth only).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t b) {
+    if (b <= bytes) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e == cudaSuccess) bytes = b;
+    return e;
+  }
+};
+
+
+// Scratch of one in-flight evaluation.  Evaluations that may overlap on the
+// GPU (different streams, graph branches, server slots) use distinct sets.
+struct EvalScratch {
+  DevBuf s32, s64, flag_list, flag_count, jbuf, pairval, pairk;
+  void release() {
+    s32.release(); s64.release(); flag_list.release(); flag_count.release();
+    jbuf.release(); pairval.release(); pairk.release();
+  }
+};
+
+mea_status set_error(mea_status s, const std::string& msg);
+
+}  // namespace mea
+
+struct mea_process_s {
+  mea::Program prog;
+  mea::DevProgram dev;
+  mea_options opts;
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0, smem_per_sm = 0;
+  std::vector<void*> owned;
+  std::mutex mu;
+  // scratch sets: 0 for mea_evaluate, 1 and 2 for the two host-pipeline streams
+  mea::EvalScratch scr[3];
+  // configurations chosen by mea_autotune, per precision (0 mixed, 1 FP64), or grid 0
+  mea::AmpConfig tuned[2];
+  int tuned_H[2] = {0, 0};
+  // tensor-core colour stage: fp16(K) and K - fp16(K) (null when exact), status word
+  const __half* cf_hi = nullptr;
+  const __half* cf_lo = nullptr;
+  int* status = nullptr;
+  // host-buffer pipeline
+  void* pin_in[2] = {nullptr, nullptr};
+  void* pin_out[2] = {nullptr, nullptr};
+  void* pin_flags[2] = {nullptr, nullptr};
+  mea::DevBuf d_in[2], d_out[2], d_flags[2];
+  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  int64_t pipe_chunk = 0;
+  bool host_only = false;
+};
+
+namespace mea {
+// Enqueue one evaluation on stream s using scratch set S (see api.cu).
+mea_status evaluate_with(mea_process_s* P, EvalScratch& S, const double* mom, int64_t n, mea_hel_mode hm,
+                         const int8_t* hel, mea_prec_mode prec, double* me2, uint8_t* flags, cudaStream_t s);
+// Device scratch bytes an evaluation of n events would hold (admission control).
+size_t scratch_estimate(mea_process_s* P, int64_t n, mea_prec_mode prec);
+}  // namespace mea

@@ -47,6 +47,23 @@ class ProcessInfo(ctypes.Structure):
                 ("flops_per_hel", ctypes.c_double), ("colour_flops_per_hel", ctypes.c_double)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("events_per_cta", ctypes.c_int), ("grid", ctypes.c_int),
+                ("colour_amps_in_shared", ctypes.c_int), ("slots_in_shared", ctypes.c_int),
+                ("candidates", ctypes.c_int), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("proc", ctypes.c_void_p), ("momenta_dev", ctypes.c_void_p), ("n_events", ctypes.c_int64),
+                ("me2_dev", ctypes.c_void_p), ("flags_dev", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("events_completed", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("busy_seconds", ctypes.c_double), ("reserved_bytes", ctypes.c_size_t)]
+
+
 class PsConfig(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("n_final", ctypes.c_int), ("rs_lo", ctypes.c_double),
                 ("rs_hi", ctypes.c_double), ("pt_min", ctypes.c_double), ("eta_max", ctypes.c_double),
@@ -71,15 +88,29 @@ def load(path: str | None = None):
             lib.mea_colour_matrix.argtypes = [vp, vp, vp]
             lib.mea_helicities.argtypes = [vp, vp, i32, vp]
             lib.mea_destroy_process.argtypes = [vp]
+            lib.mea_check_status.argtypes = [vp, vp]
             lib.mea_evaluate.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp, vp]
             lib.mea_evaluate_host.argtypes = [vp, vp, i64, i32, vp, vp]
             lib.mea_evaluate_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp]
             lib.mea_generate_phase_space.argtypes = [vp, ctypes.c_uint64, i64, vp, vp, vp]
+            lib.mea_autotune.argtypes = [vp, vp, i64, i32, vp, vp]
+            lib.mea_batch_create.argtypes = [vp, i32, i32, vp]
+            lib.mea_batch_launch.argtypes = [vp, vp]
+            lib.mea_batch_info.argtypes = [vp, vp]
+            lib.mea_batch_destroy.argtypes = [vp]
+            lib.mea_server_create.argtypes = [ctypes.c_size_t, i32, i64, vp]
+            lib.mea_server_submit.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp]
+            lib.mea_server_wait.argtypes = [vp, ctypes.c_uint64, i32, vp]
+            lib.mea_server_stats.argtypes = [vp, vp]
+            lib.mea_server_destroy.argtypes = [vp]
             lib.mea_last_error.restype = ctypes.c_char_p
             lib.mea_kernel_launch_count.restype = ctypes.c_uint64
             for name in ("mea_create_process", "mea_create_process_host_only", "mea_process_info",
                          "mea_colour_matrix", "mea_helicities", "mea_destroy_process", "mea_evaluate",
-                         "mea_evaluate_host", "mea_evaluate_noalloc", "mea_generate_phase_space"):
+                         "mea_evaluate_host", "mea_evaluate_noalloc", "mea_generate_phase_space",
+                         "mea_check_status", "mea_autotune", "mea_batch_create", "mea_batch_launch",
+                         "mea_batch_info", "mea_batch_destroy", "mea_server_create", "mea_server_submit",
+                         "mea_server_wait", "mea_server_stats", "mea_server_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -174,6 +205,19 @@ class Process:
         _check(load().mea_evaluate(self._h, _ptr(momenta), n_events, hel_mode, _ptr(hel), precision,
                                    _ptr(me2), _ptr(flags), _stream(stream)))
 
+    def autotune(self, momenta, scratch_me2, n_sample=None, precision=PREC_MIXED):
+        """Time the candidate tile shapes on a device sample and keep the fastest."""
+        if n_sample is None:
+            n_sample = int(momenta.shape[0])
+        r = TuneResult()
+        _check(load().mea_autotune(self._h, _ptr(momenta), n_sample, precision, _ptr(scratch_me2),
+                                   ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
+    def check_status(self, stream=None):
+        """Synchronise and raise MeaError(MEA_E_TIMEOUT) if a bounded device wait expired."""
+        _check(load().mea_check_status(self._h, _stream(stream)))
+
     def evaluate_noalloc(self, momenta, me2, n_events=None, precision=PREC_MIXED, flags=None, stream=None):
         """mea_evaluate_noalloc: same result as evaluate() with the helicity sum,
         using only the library's fixed device scratch array (no allocation)."""
@@ -198,3 +242,86 @@ def generate_phase_space(n_final, n, momenta, first_event=0, seed=0x09095257, rs
     cfg = PsConfig(seed, n_final, rs_lo, rs_hi, pt_min, eta_max, dr_min)
     _check(load().mea_generate_phase_space(ctypes.byref(cfg), first_event, n, _ptr(momenta),
                                            _ptr(attempts), _stream(stream)))
+
+
+class Batch:
+    """Several subprocesses evaluated by one CUDA-graph launch.
+
+    items: list of (Process, momenta_dev, me2_dev, flags_dev or None) with
+    device tensors; the graph is captured at construction and replayed by
+    launch()."""
+
+    def __init__(self, items, precision=PREC_MIXED):
+        lib = load()
+        self._keep = items
+        arr = (BatchItem * len(items))()
+        for i, (proc, mom, me2, flags) in enumerate(items):
+            arr[i] = BatchItem(proc._h.value, _ptr(mom).value, int(mom.shape[0]), _ptr(me2).value,
+                               _ptr(flags).value if flags is not None else None)
+        h = ctypes.c_void_p()
+        _check(lib.mea_batch_create(arr, len(items), precision, ctypes.byref(h)))
+        self._h = h
+        n = ctypes.c_int()
+        _check(lib.mea_batch_info(self._h, ctypes.byref(n)))
+        self.kernel_nodes = n.value
+
+    def launch(self, stream=None):
+        _check(load().mea_batch_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().mea_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (mea_server_*): requests of any
+    process are split into chunks dispatched round robin to n_slots streams,
+    admitted by a scratch-memory budget."""
+
+    def __init__(self, mem_budget_bytes=4 << 30, n_slots=4, chunk_events=1 << 14):
+        h = ctypes.c_void_p()
+        _check(load().mea_server_create(mem_budget_bytes, n_slots, chunk_events, ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, proc, momenta, me2, flags=None, precision=PREC_MIXED, n_events=None):
+        if n_events is None:
+            n_events = int(momenta.shape[0])
+        rid = ctypes.c_uint64()
+        _check(load().mea_server_submit(self._h, proc._h, _ptr(momenta), n_events, precision, _ptr(me2),
+                                        _ptr(flags), ctypes.byref(rid)))
+        self._keep[rid.value] = (proc, momenta, me2, flags)
+        return rid.value
+
+    def wait(self, req_id, timeout_ms=-1):
+        """Returns the request latency in ms; raises MeaError (e.g. MEA_E_TIMEOUT)."""
+        lat = ctypes.c_double()
+        rc = load().mea_server_wait(self._h, req_id, timeout_ms, ctypes.byref(lat))
+        if rc != -5:
+            self._keep.pop(req_id, None)
+        _check(rc)
+        return lat.value
+
+    def stats(self):
+        st = ServerStats()
+        _check(load().mea_server_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().mea_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,129 @@
+"""Batched CUDA-graph launch, autotuner and the continuous-batching server.
+
+Every per-event result is the same alone, inside a batch, after tuning, and
+in the served mix (bitwise: each event runs the same arithmetic whatever tile,
+chunk or neighbours it lands with)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SEED = 0x09095257 + 4
+
+
+def _mea():
+    from paper_0909_5257_gb300 import mea
+    return mea
+
+
+def _events(nf, n, lo, hi, first=0):
+    mea = _mea()
+    m = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
+    mea.generate_phase_space(nf, n, m, first_event=first, seed=SEED, rs_lo=lo, rs_hi=hi)
+    return m
+
+
+def _alone(P, mom, prec):
+    out = torch.empty(mom.shape[0], dtype=torch.float64, device="cuda")
+    P.evaluate(mom, out, precision=prec)
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_graph_matches_individual_evaluations(prec):
+    mea = _mea()
+    rng = np.random.default_rng(7)
+    spec = [([21] * 5, 3, 200.0, 2000.0, 3000), ([2, -2, 21, 21, 21, 21], 4, 300.0, 3000.0, 1500),
+            ([2, 2, 2, 2, 21, 21, 21], 5, 500.0, 5000.0, 300), ([21] * 6, 4, 300.0, 3000.0, 200)]
+    items, refs = [], []
+    for pdg, nf, lo, hi, n in spec:
+        n = int(n * rng.uniform(0.5, 1.5))  # uneven, seeded
+        P = mea.Process(pdg)
+        mom = _events(nf, n, lo, hi)
+        out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        fl = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        items.append((P, mom, out, fl))
+        refs.append(_alone(P, mom, prec))
+    B = mea.Batch(items, precision=prec)
+    assert B.kernel_nodes >= len(items)
+    for it in items:
+        it[2].fill_(float("nan"))
+    B.launch()
+    torch.cuda.synchronize()
+    for (P, mom, out, fl), ref in zip(items, refs):
+        assert torch.equal(out, ref)
+    B.launch()
+    torch.cuda.synchronize()
+    for (P, mom, out, fl), ref in zip(items, refs):
+        assert torch.equal(out, ref)
+    B.close()
+
+
+@pytest.mark.parametrize("pdg,nf,lo,hi", [([21] * 5, 3, 200.0, 2000.0), ([2, -2, 21, 21, 21, 21], 4, 300.0, 3000.0)])
+def test_autotune_keeps_results(pdg, nf, lo, hi):
+    mea = _mea()
+    P = mea.Process(pdg)
+    mom = _events(nf, 4096, lo, hi)
+    ref = _alone(P, mom, mea.PREC_MIXED)
+    scratch = torch.empty(2048, dtype=torch.float64, device="cuda")
+    r = P.autotune(mom[:2048], scratch, precision=mea.PREC_MIXED)
+    assert r["candidates"] >= 1 and r["best_ms"] > 0 and r["best_ms"] <= r["default_ms"] * 1.0001
+    got = _alone(P, mom, mea.PREC_MIXED)
+    assert torch.equal(got, ref)
+
+
+def test_server_results_identical_alone_and_in_mix():
+    """Poisson-ordered requests of three subprocesses with log-uniform sizes run
+    through the server (4 slots, chunks of 2^12 events); every result equals
+    the same request evaluated alone."""
+    mea = _mea()
+    rng = np.random.default_rng(11)
+    procs = [(mea.Process([2, 2, 2, 2, 21, 21, 21]), 5, 500.0, 5000.0),
+             (mea.Process([2, -2, 21, 21, 21, 21]), 4, 300.0, 3000.0),
+             (mea.Process([21] * 5), 3, 200.0, 2000.0)]
+    srv = mea.Server(mem_budget_bytes=8 << 30, n_slots=4, chunk_events=1 << 12)
+    reqs = []
+    first = 0
+    for k in range(12):
+        pi = int(rng.choice(3, p=[0.2, 0.4, 0.4]))
+        P, nf, lo, hi = procs[pi]
+        n = int(np.exp(rng.uniform(np.log(2 ** 8), np.log(2 ** 13))))
+        mom = _events(nf, n, lo, hi, first=first)
+        first += n
+        out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        prec = mea.PREC_MIXED if k % 3 else mea.PREC_FP64
+        torch.cuda.synchronize()
+        rid = srv.submit(P, mom, out, precision=prec)
+        reqs.append((rid, P, mom, out, prec))
+    lats = [srv.wait(rid, timeout_ms=120000) for rid, *_ in reqs]
+    assert all(l >= 0 for l in lats)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["rejected"] == 0
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    for rid, P, mom, out, prec in reqs:
+        assert torch.equal(out, _alone(P, mom, prec))
+    srv.close()
+
+
+def test_server_admission_rejects_and_times_out_without_hanging():
+    mea = _mea()
+    P = mea.Process([21] * 6)
+    mom = _events(4, 4096, 300.0, 3000.0)
+    out = torch.empty(4096, dtype=torch.float64, device="cuda")
+    small = mea.Server(mem_budget_bytes=1 << 10, n_slots=2, chunk_events=1 << 10)
+    with pytest.raises(mea.MeaError) as e:
+        small.submit(P, mom, out)
+    assert e.value.status == -6  # MEA_E_REJECTED
+    small.close()
+    srv = mea.Server(mem_budget_bytes=8 << 30, n_slots=1, chunk_events=256)
+    rid = srv.submit(P, mom, out, precision=mea.PREC_FP64)
+    with pytest.raises(mea.MeaError) as e:
+        srv.wait(rid, timeout_ms=0)
+    assert e.value.status == -5  # MEA_E_TIMEOUT, request still running
+    srv.wait(rid, timeout_ms=120000)
+    assert torch.equal(out, _alone(P, mom, mea.PREC_FP64))
+    with pytest.raises(mea.MeaError):
+        srv.wait(12345, timeout_ms=10)
+    srv.close()

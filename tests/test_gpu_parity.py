@@ -235,3 +235,32 @@ def test_full_size_sampled(name, nf, lo, hi):
     assert np.median(r32) <= 1e-6 and r32.max() <= 1e-4
     # every event: mixed within 1e-4 of the FP64 GPU path
     assert np.max(np.abs(g32 / g64 - 1.0)) <= 1e-4
+
+
+@pytest.mark.parametrize("name", ["gg>gg", "uu~>gg", "gg>ggg", "uu~>ggg", "uu>uug", "uu>uugg", "uu~>gggg"])
+def test_tensor_core_colour_stage_forced(name):
+    """Mixed path with the colour contraction forced onto the tcgen05 GEMM
+    (colour_mode 2) for small colour bases, against the oracle."""
+    _, pdg, _, _ = _case(name)
+    mom, ref = _data(name)
+    got, flags = _run(pdg, mom, _mea().PREC_MIXED, colour_mode=2)
+    _proc(pdg, colour_mode=2).check_status()
+    rel = np.abs(got / ref - 1.0)
+    assert np.all(np.isfinite(got))
+    assert np.median(rel) <= 1e-6, f"{name}: median rel {np.median(rel):.3e}"
+    assert rel.max() <= 1e-4, f"{name}: max rel {rel.max():.3e}"
+
+
+@pytest.mark.parametrize("name", ["gg>gggg", "uu>uuggg", "uu~>ggggg", "gg>ggggg"])
+def test_tensor_core_colour_stage_default_for_large_bases(name):
+    """Colour bases of 120 and more take the tensor-core stage by default; the
+    CUDA-core stage (colour_mode 1) on the same inputs agrees within the mixed
+    tolerance."""
+    _, pdg, _, _ = _case(name)
+    mom, ref = _data(name)
+    tc, _ = _run(pdg, mom, _mea().PREC_MIXED)
+    _proc(pdg).check_status()
+    cc, _ = _run(pdg, mom, _mea().PREC_MIXED, colour_mode=1)
+    assert np.max(np.abs(tc / ref - 1.0)) <= 1e-4
+    assert np.max(np.abs(cc / ref - 1.0)) <= 1e-4
+    assert np.max(np.abs(tc / cc - 1.0)) <= 1e-4
