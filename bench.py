@@ -193,13 +193,153 @@ def cpu_baseline(subs, seed_off, budget_s=12.0):
             "sample": "; ".join(parts)}
 
 
+BATCH_SPEC = [  # (name, pdg, n_final, sqrt(s) range, configured events)
+    ("gg>ggg", [21, 21, 21, 21, 21], 3, 200.0, 2000.0, 1 << 18),
+    ("uu~>gggg", [2, -2, 21, 21, 21, 21], 4, 300.0, 3000.0, 1 << 20),
+    ("uu>uuggg", [2, 2, 2, 2, 21, 21, 21], 5, 300.0, 3000.0, 1 << 19),
+    ("gg>gggg", [21] * 6, 4, 300.0, 3000.0, 1 << 17),
+]
+
+
+def run_batch(args):
+    """Batched mixed launch: four subprocesses of very uneven cost, counts
+    perturbed by a seeded draw, autotuned per process, evaluated by one
+    CUDA-graph launch per step (mea_batch_*); mixed vs FP64 graph."""
+    import torch
+    from paper_0909_5257_gb300 import mea
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(SEED_BASE + 3)
+    procs, moms, n_ev = [], [], []
+    for name, pdg, nf, lo, hi, n in BATCH_SPEC:
+        n = max(64, int(n * args.scale * rng.uniform(0.75, 1.25)))
+        P = mea.Process(pdg)
+        m = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
+        mea.generate_phase_space(nf, n, m, seed=SEED_BASE + 3, rs_lo=lo, rs_hi=hi)
+        procs.append(P); moms.append(m); n_ev.append(n)
+    tune = {}
+    for (name, *_), P, m in zip(BATCH_SPEC, procs, moms):
+        k = min(m.shape[0], 1 << 14)
+        scratch = torch.empty(k, dtype=torch.float64, device="cuda")
+        tune[name] = P.autotune(m[:k], scratch, precision=mea.PREC_MIXED)
+    res = {}
+    for prec, pname in ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64")):
+        outs = [torch.empty(n, dtype=torch.float64, device="cuda") for n in n_ev]
+        flags = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in n_ev]
+        B = mea.Batch(list(zip(procs, moms, outs, flags)), precision=prec)
+        steps = args.steps if pname == "mixed" else max(1, min(args.steps, 2))
+        for _ in range(max(1, args.warmup if pname == "mixed" else 1)):
+            B.launch()
+        torch.cuda.synchronize()
+        l0 = mea.kernel_launch_count()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(steps):
+            B.launch()
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / steps
+        res[pname] = {"events_per_s": sum(n_ev) / (ms * 1e-3), "ms_per_launch": ms, "steps": steps,
+                      "graph_kernel_nodes": B.kernel_nodes, "kernels_launched": mea.kernel_launch_count() - l0}
+        res[pname + "_out"] = [o.clone() for o in outs]
+        B.close()
+    errs = {}
+    for i, (name, *_) in enumerate(BATCH_SPEC):
+        rel = (res["mixed_out"][i] / res["fp64_out"][i] - 1.0).abs()
+        errs[name] = {"events": n_ev[i], "mixed_vs_fp64_rel_err_median": float(rel.median()),
+                      "mixed_vs_fp64_rel_err_max": float(rel.max()), "autotune": tune[name]}
+    out = {"metric": METRIC, "value": res["mixed"]["events_per_s"], "unit": "events/s", "n_gpus": 1,
+           "steps": res["mixed"]["steps"], "warmup": args.warmup, "ms_per_step": res["mixed"]["ms_per_launch"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 amplitudes + tcgen05 f16-split colour sum; f64 re-evaluation", "data": "synthetic",
+           "config": {"workload": "batched mixed launch (one CUDA graph): " +
+                      ", ".join(f"{b[0]} {n}" for b, n in zip(BATCH_SPEC, n_ev)),
+                      "scale": args.scale},
+           "fp64": {k: v for k, v in res["fp64"].items()}, "mixed": {k: v for k, v in res["mixed"].items()},
+           "per_subprocess": errs, "gpu_launches": res["mixed"]["kernels_launched"]}
+    print(json.dumps(out), flush=True)
+
+
+SERVE_MIX = [("gg>ggggg", [21] * 7, 5, 0.4), ("uu~>ggggg", [2, -2, 21, 21, 21, 21, 21], 5, 0.4),
+             ("uu>uuggg", [2, 2, 2, 2, 21, 21, 21], 5, 0.2)]
+
+
+def run_serve(args):
+    """Serving: Poisson arrivals, request sizes log-uniform in
+    [2^10, 2^18] x scale events, mix 40/40/20 % of gg>ggggg, uu~>ggggg,
+    uu>uuggg, sqrt(s) in [500 GeV, 5 TeV]; offered load a fraction of the
+    measured capacity; p50/p99 latency and throughput for the mixed and the
+    FP64 path."""
+    import torch
+    from paper_0909_5257_gb300 import mea
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(SEED_BASE + 4)
+    procs = {name: mea.Process(pdg) for name, pdg, _, _ in SERVE_MIX}
+    n_req = max(8, args.steps * 4)
+    lo_n, hi_n = (1 << 10) * args.scale, (1 << 18) * args.scale
+    reqs = []
+    first = 0
+    for k in range(n_req):
+        name, pdg, nf, _ = SERVE_MIX[int(rng.choice(3, p=[w for *_, w in SERVE_MIX]))]
+        n = max(16, int(np.exp(rng.uniform(np.log(lo_n), np.log(hi_n)))))
+        m = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
+        mea.generate_phase_space(nf, n, m, first_event=first, seed=SEED_BASE + 4, rs_lo=500.0, rs_hi=5000.0)
+        first += n
+        reqs.append((name, m, n))
+    torch.cuda.synchronize()
+    results = {}
+    for prec, pname in ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64")):
+        # capacity: back-to-back submission
+        srv = mea.Server(mem_budget_bytes=16 << 30, n_slots=4, chunk_events=1 << 12)
+        outs = [torch.empty(n, dtype=torch.float64, device="cuda") for _, _, n in reqs]
+        t0 = time.perf_counter()
+        ids = [srv.submit(procs[nm], m, o, precision=prec) for (nm, m, n), o in zip(reqs, outs)]
+        for i in ids:
+            srv.wait(i, timeout_ms=600000)
+        cap_s = time.perf_counter() - t0
+        total = sum(n for _, _, n in reqs)
+        srv.close()
+        capacity = total / cap_s
+        # Poisson arrivals at 0.8 x capacity
+        mean_gap = (total / len(reqs)) / (0.8 * capacity)
+        gaps = rng.exponential(mean_gap, size=len(reqs))
+        srv = mea.Server(mem_budget_bytes=16 << 30, n_slots=4, chunk_events=1 << 12)
+        t0 = time.perf_counter()
+        ids = []
+        tnext = t0
+        for (nm, m, n), o, g in zip(reqs, outs, gaps):
+            tnext += g
+            while time.perf_counter() < tnext:
+                time.sleep(min(0.001, max(0.0, tnext - time.perf_counter())))
+            ids.append(srv.submit(procs[nm], m, o, precision=prec))
+        for i in ids:
+            srv.wait(i, timeout_ms=600000)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        results[pname] = {"capacity_events_per_s": capacity, "offered_load": 0.8, "events_per_s": total / wall,
+                          "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                          "requests": len(reqs), "events": total}
+    out = {"metric": METRIC, "value": results["mixed"]["events_per_s"], "unit": "events/s", "n_gpus": 1,
+           "steps": n_req, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 amplitudes + tcgen05 f16-split colour sum; f64 re-evaluation",
+           "data": "synthetic",
+           "config": {"workload": "serving: Poisson arrivals at 0.8 x capacity, sizes log-uniform "
+                                  f"[{int(lo_n)}, {int(hi_n)}], mix 40/40/20 gg>ggggg/uu~>ggggg/uu>uuggg",
+                      "scale": args.scale, "slots": 4, "chunk_events": 4096},
+           "p50_ms": results["mixed"]["p50_ms"], "p99_ms": results["mixed"]["p99_ms"],
+           "mixed": results["mixed"], "fp64": results["fp64"]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3jet", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="3jet", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="batch/serve: multiply the configured event counts (bounded runs)")
     ap.add_argument("--ref-events", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -207,6 +347,12 @@ def main():
 
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
 
     import torch

@@ -102,13 +102,15 @@ typedef struct {
   int n_currents;         /* off-shell currents in the shared current graph */
   int n_ops;              /* operations in the per-(event,helicity) program */
   int n_slots;            /* wavefunction slots the program needs at once */
-  int colour_denominator_log2; /* unused (0) */
+  int n_colour_amplitudes;  /* colour amplitudes the kernels accumulate: n_colour,
+                              or n_colour/2 for pure-gluon processes (reflection
+                              identity J_rev(a) = (-1)^n J_a, folded colour matrix) */
   int64_t cf_denominator; /* N = K / cf_denominator with K integer */
   int64_t cf_max_abs_numerator; /* max |K| */
   double flops_per_hel;   /* algorithmic FLOPs of the amplitude stage per
                              (event, helicity): wavefunctions, vertices,
                              currents and colour-amplitude accumulation */
-  double colour_flops_per_hel; /* 4 m^2: FLOPs of the colour quadratic form */
+  double colour_flops_per_hel; /* 4 n_colour_amplitudes^2: FLOPs of the colour quadratic form */
 } mea_process_info_t;
 
 /* ---- process handles ---------------------------------------------------- */

@@ -84,7 +84,7 @@ cudaError_t place_scratch(mea::DevBuf& buf, const mea::DevProgram& d, bool fp64,
 bool use_tensor_colour(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode hm) {
   if (prec != MEA_PREC_MIXED || hm == MEA_HEL_GIVEN || P->opts.colour_mode == 1) return false;
   if (P->opts.colour_mode == 2) return true;
-  return P->prog.n_colour >= 96;
+  return P->prog.n_jamp >= 96;
 }
 
 // Mixed path with the colour contraction on the tensor cores, in event chunks
@@ -95,7 +95,7 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
   const mea::Program& G = P->prog;
   const int n_ext = G.n_ext;
   const int H = (hm == MEA_HEL_SUM_NONZERO) ? G.n_hel : (1 << n_ext);
-  const int m = G.n_colour;
+  const int m = G.n_jamp;
   const int ldj = ((m + 15) / 16) * 16;
   const size_t per_event = (size_t)H * 2 * ldj * sizeof(float);
   const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((256u << 20) / per_event)));
@@ -232,7 +232,7 @@ size_t scratch_estimate(mea_process_s* P, int64_t n, mea_prec_mode prec) {
     return jamp_scratch_bytes_needed(d, f64, c) + slot_scratch_bytes_needed(d, f64, c) + 512;
   };
   if (use_tensor_colour(P, prec, MEA_HEL_SUM_NONZERO)) {
-    const int ldj = ((G.n_colour + 15) / 16) * 16;
+    const int ldj = ((G.n_jamp + 15) / 16) * 16;
     const size_t per_event = (size_t)H * 2 * ldj * sizeof(float);
     const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((256u << 20) / per_event)));
     DevProgram dp = P->dev;
@@ -293,11 +293,11 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
     leg[4 * l + 1] = (int8_t)kind;
     leg[4 * l + 2] = (int8_t)G.incoming[l];
   }
-  std::vector<float> cff(G.cf_num.size());
-  std::vector<double> cfd(G.cf_num.size());
-  for (size_t i = 0; i < G.cf_num.size(); ++i) {
-    cff[i] = (float)G.cf_num[i];
-    cfd[i] = (double)G.cf_num[i];
+  std::vector<float> cff(G.cf_jamp.size());
+  std::vector<double> cfd(G.cf_jamp.size());
+  for (size_t i = 0; i < G.cf_jamp.size(); ++i) {
+    cff[i] = (float)G.cf_jamp[i];
+    cfd[i] = (double)G.cf_jamp[i];
   }
   mea::DevProgram& D = P->dev;
   const mea::Op* dops;
@@ -322,7 +322,7 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
   D.leg_info = dleg;
   D.n_ext = n_ext;
   D.n_slots = G.n_slots;
-  D.n_colour = G.n_colour;
+  D.n_colour = G.n_jamp;  // colour amplitudes accumulated (folded for gluons)
   D.cf_f = dcff;
   D.cf_d = dcfd;
   D.cf_inv_den = 1.0 / (double)G.cf_den;
@@ -332,11 +332,11 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
   D.g = std::sqrt(4.0 * M_PI * P->opts.alpha_s);
   D.gen = (P->opts.colour_mode == 2) ? nullptr : mea::find_generated(pdg, n_ext);
   {
-    std::vector<__half> hi(G.cf_num.size()), lo(G.cf_num.size());
+    std::vector<__half> hi(G.cf_jamp.size()), lo(G.cf_jamp.size());
     bool exact = true;
-    for (size_t i = 0; i < G.cf_num.size(); ++i) {
-      hi[i] = __float2half_rn((float)G.cf_num[i]);
-      double r = (double)G.cf_num[i] - (double)__half2float(hi[i]);
+    for (size_t i = 0; i < G.cf_jamp.size(); ++i) {
+      hi[i] = __float2half_rn((float)G.cf_jamp[i]);
+      double r = (double)G.cf_jamp[i] - (double)__half2float(hi[i]);
       lo[i] = __float2half_rn((float)r);
       if (r != 0.0) exact = false;
     }
@@ -387,8 +387,9 @@ mea_status mea_process_info(mea_process_t P, mea_process_info_t* info) {
   info->n_slots = G.n_slots;
   info->cf_denominator = G.cf_den;
   info->cf_max_abs_numerator = G.cf_max_abs;
+  info->n_colour_amplitudes = G.n_jamp;
   info->flops_per_hel = G.flops_per_hel;
-  info->colour_flops_per_hel = 4.0 * (double)G.n_colour * (double)G.n_colour;
+  info->colour_flops_per_hel = 4.0 * (double)G.n_jamp * (double)G.n_jamp;
   return MEA_OK;
 }
 

@@ -63,7 +63,7 @@ mea_status mea_autotune(mea_process_t P, const double* mom, int64_t n, mea_prec_
   const int ti = fp64 ? 1 : 0;
   const int H = P->prog.n_hel;
   mea::DevProgram dp = P->dev;
-  const bool tc = !fp64 && P->opts.colour_mode != 1 && (P->opts.colour_mode == 2 || P->prog.n_colour >= 96);
+  const bool tc = !fp64 && P->opts.colour_mode != 1 && (P->opts.colour_mode == 2 || P->prog.n_jamp >= 96);
   if (tc) dp.gen = nullptr;  // the tensor-core colour path runs the interpreter
   std::vector<mea::AmpConfig> cands =
       mea::candidate_configs(dp, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);

@@ -43,7 +43,7 @@ std::string lit(double v) {
 
 void emit_body(std::ostringstream& o, const mea::Program& P, const std::string& id) {
   using namespace mea;
-  const int m = P.n_colour;
+  const int m = P.n_jamp;  // colour amplitudes accumulated (folded for gluons)
   o << "template <typename R>\nstruct Body_" << id << " {\n";
   o << "  static constexpr int kColour = " << m << ";\n";
   o << "  __device__ __forceinline__ static void run(const R* __restrict__ et, const R* __restrict__ mt,\n"
@@ -125,7 +125,7 @@ void emit_body(std::ostringstream& o, const mea::Program& P, const std::string& 
     std::ostringstream z;
     bool any = false;
     for (int b = a; b < m; ++b) {
-      int64_t k = P.cf_num[(size_t)a * m + b];
+      int64_t k = P.cf_jamp[(size_t)a * m + b];
       if (!k) continue;
       double c = (b == a) ? (double)k : 2.0 * (double)k;
       z << "      z += " << lit(c) << " * (F[" << a << "].r * F[" << b << "].r + F[" << a << "].i * F[" << b

@@ -9,10 +9,13 @@
 //     into three FP16 parts (33 significant bits together, more than FP32's 24);
 //   * K is an integer matrix; it is split K = K_hi + K_lo with K_hi = fp16(K)
 //     (exact when |K| <= 2048, then K_lo = 0 and those products are skipped);
-//   * Z = (J_hi + J_mid + J_lo) K_hi + (J_hi + J_mid) K_lo, FP32 accumulation;
-//   * the epilogue reads Z from tensor memory (tcgen05.ld) and forms
-//     sum_a J_a Z_a per row in FP64 against the unscaled FP32 J, then undoes
-//     the scale.
+//   * Z = (J_hi + J_mid + J_lo) K_hi + (J_hi + J_mid) K_lo with FP32
+//     accumulation in tensor memory, restarted for every 64-wide K chunk: the
+//     tensor core's FP32 accumulation is biased over long sums (measured: a
+//     systematic 2e-6 relative shift of |M|^2 at m = 720 when one accumulator
+//     spans all of K), so each chunk's partial Z is read out (tcgen05.ld) and
+//     sum_a J_a Z_a is accumulated across chunks in FP64 against the unscaled
+//     FP32 J, after which the row scale is undone.
 // Operands are staged in shared memory in the canonical no-swizzle K-major
 // layout (8-row x 16-byte core matrices).  Every wait is bounded: on expiry
 // the kernel records an error in *status, drains its own MMAs with a bounded
@@ -165,8 +168,8 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
     double acc_row = 0.0;  // this thread's row: sum_a J_a Z_a (scaled)
     for (int n0 = 0; n0 < g.np; n0 += NC) {
       for (int k0 = 0; k0 < g.kp; k0 += kKC) {
-        __syncthreads();  // previous MMAs have completed (waited below) before overwriting
-        // A tiles: row = t's share; 128 rows x KC columns, 128 threads
+        __syncthreads();  // previous MMAs and epilogue reads are done before overwriting
+        // A tiles: 128 rows x KC columns, three FP16 parts of the scaled J
         for (int idx = t; idx < kM * kKC; idx += kThreads) {
           int row = idx / kKC, k = idx - (idx / kKC) * kKC;
           int64_t r = row0 + row;
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
             uint64_t dal = make_desc(smem_u32(a_lo) + koff, lbo, sbo_a);
             uint64_t dbh = make_desc(smem_u32(b_hi) + koff, lbo, sbo_b);
             uint64_t dbl = make_desc(smem_u32(b_lo) + koff, lbo, sbo_b);
-            uint32_t first = (k0 == 0 && ks == 0) ? 0u : 1u;
+            uint32_t first = (ks == 0) ? 0u : 1u;  // fresh accumulator for every K chunk
             // smallest terms first
             mma_f16(tmem, dal, dbh, idesc, first);
             if (use_blo) {
@@ -229,23 +232,23 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
         }
         phase ^= 1u;
         tc_fence_after();
-      }
-      // epilogue for columns n0 .. n0+NC: this thread owns TMEM lane t
-      if (!*abort_flag) {
-        const int64_t r = row0 + t;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        for (int c0 = 0; c0 < NC; c0 += 16) {
-          float z[16];
-          tmem_ld16(tmem + lane_base + (uint32_t)c0, z);
-          if (r < n_rows) {
-            const float* jr = g.J + r * ldj + n0 + c0;
+        // epilogue of this K chunk: this thread owns TMEM lane t (its row)
+        if (!*abort_flag) {
+          const int64_t r = row0 + t;
+          const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+          for (int c0 = 0; c0 < NC && n0 + c0 < m; c0 += 16) {
+            float z[16];
+            tmem_ld16(tmem + lane_base + (uint32_t)c0, z);
+            if (r < n_rows) {
+              const float* jr = g.J + r * ldj + n0 + c0;
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (n0 + c0 + i < m) acc_row += (double)jr[i] * (double)z[i];
+              for (int i = 0; i < 16; ++i)
+                if (n0 + c0 + i < m) acc_row += (double)jr[i] * (double)z[i];
+            }
           }
         }
+        tc_fence_before();
       }
-      tc_fence_before();
       __syncthreads();
       tc_fence_after();
     }

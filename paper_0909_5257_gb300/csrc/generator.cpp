@@ -707,6 +707,81 @@ void colour_matrix(Builder& B, Program& P) {
   }
 }
 
+// ------------------------------------------------------ reflection folding
+// Pure-gluon colour amplitudes obey J_rev(a) = (-1)^n J_a (reversing a trace
+// Tr(T^r T^w1 ... T^wk) gives Tr(T^r T^wk ... T^w1) and every f^{abc} changes
+// sign under the reversal of its trace expansion).  When every diagram's
+// coefficients satisfy it exactly, keep the canonical half of the orderings
+// (word < reversed word) and fold the colour matrix.
+void fold_reflection(Builder& B, Program& P) {
+  const int m = B.n_colour;
+  P.n_jamp = m;
+  P.cf_jamp = P.cf_num;
+  if (B.fam != FAM_GLUON || m < 2) {
+    P.cf_jamp_max_abs = P.cf_max_abs;
+    return;
+  }
+  std::vector<int> rev(m, -1);
+  for (auto& kv : B.gluon_index) {
+    Word r = kv.first;
+    std::reverse(r.begin(), r.end());
+    rev[kv.second] = B.gluon_index.at(r);
+  }
+  const int sgn = (B.n % 2 == 0) ? 1 : -1;
+  for (const Op& op : P.ops) {
+    if (op.type < OP_AVVV) continue;
+    std::map<int, std::pair<int, int>> c;
+    for (uint32_t k = 0; k < op.col_count; ++k) {
+      const ColEntry& e = P.col[op.col_begin + k];
+      c[e.alpha] = {e.re, e.im};
+    }
+    for (auto& kv : c) {
+      auto it = c.find(rev[kv.first]);
+      if (it == c.end() || it->second.first != sgn * kv.second.first || it->second.second != sgn * kv.second.second) {
+        P.cf_jamp_max_abs = P.cf_max_abs;
+        return;  // identity does not hold term by term: keep the full basis
+      }
+    }
+  }
+  // canonical = word lexicographically smaller than its reverse
+  std::vector<int> canon_of(m, -1);
+  std::vector<int> canon;
+  for (auto& kv : B.gluon_index) {
+    Word r = kv.first;
+    std::reverse(r.begin(), r.end());
+    if (kv.first < r) {
+      canon_of[kv.second] = (int)canon.size();
+      canon.push_back(kv.second);
+    }
+  }
+  const int h = (int)canon.size();
+  // remap colour entries, dropping the reflected ones
+  std::vector<ColEntry> col;
+  for (Op& op : P.ops) {
+    if (op.type < OP_AVVV) continue;
+    uint32_t b = (uint32_t)col.size();
+    for (uint32_t k = 0; k < op.col_count; ++k) {
+      ColEntry e = P.col[op.col_begin + k];
+      if (canon_of[e.alpha] < 0) continue;
+      e.alpha = (uint16_t)canon_of[e.alpha];
+      col.push_back(e);
+    }
+    op.col_begin = b;
+    op.col_count = (uint32_t)col.size() - b;
+  }
+  P.col = col;
+  P.n_jamp = h;
+  P.cf_jamp.assign((size_t)h * h, 0);
+  P.cf_jamp_max_abs = 0;
+  for (int a = 0; a < h; ++a)
+    for (int b = 0; b < h; ++b) {
+      int ia = canon[a], ib = canon[b];
+      int64_t v = 2 * (P.cf_num[(size_t)ia * m + ib] + sgn * P.cf_num[(size_t)ia * m + rev[ib]]);
+      P.cf_jamp[(size_t)a * h + b] = v;
+      P.cf_jamp_max_abs = std::max<int64_t>(P.cf_jamp_max_abs, v < 0 ? -v : v);
+    }
+}
+
 // ------------------------------------------------------ helicity rules
 // Massless tree amplitudes: helicity is conserved along every quark line
 // (in the all-outgoing convention its two ends have opposite helicity); pure
@@ -897,9 +972,15 @@ Program build_program(const std::vector<int>& pdg) {
     throw std::runtime_error("generator: program too large");
   P.n_slots = n_slots;
   P.n_currents = n_cur;
-  P.flops_per_hel = flops;
+  P.flops_per_hel = flops;  // recounted after the colour folding below
 
   colour_matrix(B, P);
+  fold_reflection(B, P);
+  {
+    double f = 0;
+    for (const Op& op : P.ops) f += op_flops(op.type) + ((op.type >= OP_AVVV) ? 4.0 * op.col_count : 0.0);
+    P.flops_per_hel = f;
+  }
 
   // helicities
   for (int h = 0; h < (1 << n); ++h) {

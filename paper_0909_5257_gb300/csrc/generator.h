@@ -68,11 +68,19 @@ struct Program {
   int n_slots = 0;
   int n_diagrams = 0;
   int n_currents = 0;
-  int n_colour = 0;
+  int n_colour = 0;                   // colour basis size (Table 1)
   int n_a = 1, n_b = 1;
-  std::vector<int64_t> cf_num;        // [m*m]
+  std::vector<int64_t> cf_num;        // [m*m] exact colour matrix K of the basis, N = K / cf_den
   int64_t cf_den = 1;
   int64_t cf_max_abs = 0;
+  // Colour amplitudes the kernels accumulate.  For pure-gluon processes the
+  // reflection identity J_rev(a) = (-1)^n J_a (checked on every diagram's
+  // coefficients) halves them: only canonical orderings are kept and the
+  // colour matrix is folded, K'_ab = 2 (K_ab + (-1)^n K_a,rev(b)).  Otherwise
+  // n_jamp = n_colour and cf_jamp = cf_num.
+  int n_jamp = 0;
+  std::vector<int64_t> cf_jamp;       // [n_jamp * n_jamp], same denominator cf_den
+  int64_t cf_jamp_max_abs = 0;
   std::vector<int8_t> hel;            // [n_hel][n_ext], physical helicities
   int n_hel = 0;
   std::vector<int8_t> hel_all;        // [2^n_ext][n_ext]

@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
 class ProcessInfo(ctypes.Structure):
     _fields_ = [("n_ext", ctypes.c_int), ("n_diagrams", ctypes.c_int), ("n_colour", ctypes.c_int),
                 ("n_hel_nonzero", ctypes.c_int), ("n_currents", ctypes.c_int), ("n_ops", ctypes.c_int),
-                ("n_slots", ctypes.c_int), ("colour_denominator_log2", ctypes.c_int),
+                ("n_slots", ctypes.c_int), ("n_colour_amplitudes", ctypes.c_int),
                 ("cf_denominator", ctypes.c_int64), ("cf_max_abs_numerator", ctypes.c_int64),
                 ("flops_per_hel", ctypes.c_double), ("colour_flops_per_hel", ctypes.c_double)]
 
