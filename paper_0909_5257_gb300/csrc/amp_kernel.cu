@@ -66,9 +66,10 @@ __device__ __forceinline__ void st_slot(R* slots, int s, int L, int t, const W4<
   }
 }
 
-template <typename R, bool JSMEM, bool SSMEM>
+template <typename R, bool JSMEM, bool SSMEM, bool AOUT>
 __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, const AmpLaunch A,
                                                    const AmpConfig C) {
+  static_assert(!AOUT || std::is_same<R, float>::value, "amplitude output is an FP32 path");
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr bool F32 = std::is_same<R, float>::value;
   constexpr int JW = F32 ? 4 : 2;  // FP32: hi re, hi im, lo re, lo im
@@ -131,8 +132,14 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
       }
       const R* et = tab + (size_t)e * tab_stride;
       const R* mt = et + 8 * n_ext;
-      for (int a = 0; a < m * JW; ++a) jam[(size_t)a * L + t] = (R)0;
+      if (!AOUT)
+        for (int a = 0; a < m * JW; ++a) jam[(size_t)a * L + t] = (R)0;
       float abs_mass = 0.f;  // sum of |c A| over all colour entries (FP32 indicator)
+      // amplitude output: diagram ordinal, row maxima of |Re A|, |Im A|, finiteness
+      const int64_t pair = ev * H + h;
+      int d_amp = 0;
+      float mx_re = 0.f, mx_im = 0.f;
+      bool finite_amps = true;
 
       for (int i = 0; i < P.n_ops; ++i) {
         OpWords w;
@@ -222,7 +229,17 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
           default:
             break;
         }
-        if (is_amp) {
+        if (AOUT && is_amp) {
+          // hand the diagram amplitude to the tensor-core colour-amplitude stage
+          float2* dst = reinterpret_cast<float2*>(A.amp_out + (size_t)d_amp * A.lda + 2 * pair);
+          *dst = make_float2((float)amp.r, (float)amp.i);
+          const float ar = fabsf((float)amp.r), ai = fabsf((float)amp.i);
+          finite_amps = finite_amps && isfinite(ar) && isfinite(ai);
+          mx_re = fmaxf(mx_re, ar);
+          mx_im = fmaxf(mx_im, ai);
+          abs_mass += __ldg(P.amp_w + d_amp) * (ar + ai);
+          ++d_amp;
+        } else if (is_amp) {
           const ColEntry* ce = P.col + op.col_begin;
           for (uint32_t k = 0; k < op.col_count; ++k) {
             ColEntry c = ce[k];
@@ -246,7 +263,12 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
           }
         }
       }
-      if (A.jamp_out) {
+      if (AOUT) {
+        const float nan = __int_as_float(0x7fc00000);
+        A.amp_rowmax[2 * pair] = finite_amps ? mx_re : nan;
+        A.amp_rowmax[2 * pair + 1] = finite_amps ? mx_im : nan;
+        A.pair_kappa[pair] = abs_mass;  // divided by sum |J| after the colour-amplitude stage
+      } else if (A.jamp_out) {
         // split colour stage: hand the colour amplitudes to the tensor-core kernel
         if constexpr (F32) {
           const int64_t pair = ev * H + h;
@@ -294,7 +316,7 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
     __syncthreads();
 
     // ---- phase 2: helicity sum per event, fixed order
-    if (!A.jamp_out) tile_finish<F32>(A, t, E, H, ev0, n, listed, res, kap);
+    if (!A.jamp_out && !AOUT) tile_finish<F32>(A, t, E, H, ev0, n, listed, res, kap);
     __syncthreads();
   }
 }
@@ -310,14 +332,25 @@ size_t smem_bytes(const DevProgram& p, int threads, int E, bool jsmem, bool ssme
   return b;
 }
 
-__global__ void finish_kernel(const AmpLaunch A, int H, const double* pairval, const float* pk) {
+// pk: per-pair indicator; with jabs (sum |J| of each column split, [n_splits][n_pairs])
+// pk holds sum |c A| and the indicator is pk / sum_splits jabs.
+__global__ void finish_kernel(const AmpLaunch A, int H, const double* pairval, const float* pk,
+                              const float* jabs, int n_splits) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= A.n_events) return;
+  const int64_t n_pairs = A.n_events * H;
   double s = 0.0, wk = 0.0;
   for (int h = 0; h < H; ++h) {
-    double v = pairval[e * H + h];
+    const int64_t p = e * H + h;
+    double v = pairval[p];
+    float k = pk[p];
+    if (jabs) {
+      float ja = 0.f;
+      for (int q = 0; q < n_splits; ++q) ja += jabs[(size_t)q * n_pairs + p];
+      k = (ja > 0.f) ? k / ja : 0.f;
+    }
     s += v;
-    wk += v * (double)pk[e * H + h];
+    wk += v * (double)k;
   }
   double me = 0.25 * s;
   A.me2[e] = me;
@@ -335,11 +368,11 @@ __global__ void finish_kernel(const AmpLaunch A, int H, const double* pairval, c
 }  // namespace
 
 cudaError_t launch_finish(const AmpLaunch& a, int H, const double* pairval, const float* pair_kappa,
-                          cudaStream_t s) {
+                          cudaStream_t s, const float* jabs, int n_splits) {
   if (a.n_events <= 0) return cudaSuccess;
   int threads = 256;
   int64_t blocks = (a.n_events + threads - 1) / threads;
-  finish_kernel<<<(unsigned)blocks, threads, 0, s>>>(a, H, pairval, pair_kappa);
+  finish_kernel<<<(unsigned)blocks, threads, 0, s>>>(a, H, pairval, pair_kappa, jabs, n_splits);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) ++launch_counter();
   return e;
@@ -400,12 +433,15 @@ AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int 
   AmpConfig best;
   best.H = H;
   double best_score = -1;
-  // preference: everything in shared memory; then the wavefunction slots in
-  // global memory (L1-cached) and the colour amplitudes, which every diagram
-  // updates ~2^(n-3) times, in shared memory; then the reverse; then both global
+  // Every placement is scored by the lanes it keeps resident per SM (latency
+  // hiding) times the fraction of busy lanes: everything in shared memory
+  // counts up to 512 lanes per SM, placements that go through L1/L2 up to 256.
+  // A shared-memory placement that leaves only a few lanes per SM loses to a
+  // global one with many (measured: gg>gggg 2.6x, uu~>gggg 2.5x faster).
   const int placements[4][2] = {{1, 1}, {1, 0}, {0, 1}, {0, 0}};
-  for (int pl = 0; pl < 4 && best_score <= 0; ++pl) {
+  for (int pl = 0; pl < 4; ++pl) {
     bool jsm = placements[pl][0] != 0, ssm = placements[pl][1] != 0;
+    if (p.n_colour == 0 && !jsm) continue;  // no colour accumulators: one placement axis
     for (int E = 1; E * H <= kMaxThreads; ++E) {
       if (hint > 0 && E != hint) continue;
       int threads = ((E * H + 31) / 32) * 32;
@@ -477,6 +513,7 @@ std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, 
   }
   const int placements[4][2] = {{1, 1}, {1, 0}, {0, 1}, {0, 0}};
   for (auto& pl : placements) {
+    if (p.n_colour == 0 && !pl[0]) continue;  // no colour accumulators: one placement axis
     int last_threads = -1;
     for (int E = 1; E * H <= kMaxThreads; ++E) {
       int threads = ((E * H + 31) / 32) * 32;
@@ -509,22 +546,23 @@ size_t slot_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig
   return (size_t)c.grid * p.n_slots * 8 * c.threads * (fp64 ? sizeof(double) : sizeof(float));
 }
 
-template <typename R, bool J, bool S>
+template <typename R, bool J, bool S, bool O = false>
 static void launch_one(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
-  cudaFuncSetAttribute(amp_kernel<R, J, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-  amp_kernel<R, J, S><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
+  cudaFuncSetAttribute(amp_kernel<R, J, S, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  amp_kernel<R, J, S, O><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
 }
 
 cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const AmpLaunch& a,
                        cudaStream_t s) {
   if (c.grid <= 0) return cudaSuccess;
-  if (p.gen) {
+  if (a.amp_out) {
+    // diagram amplitudes out (no colour accumulators): FP32 interpreter only
+    if (fp64 || p.n_colour != 0) return cudaErrorInvalidValue;
+    if (c.slots_in_smem) launch_one<float, true, true, true>(p, c, a, s);
+    else launch_one<float, true, false, true>(p, c, a, s);
+  } else if (p.gen) {
     p.gen->launch(fp64, p, c, a, s);
-    cudaError_t err = cudaGetLastError();
-    if (err == cudaSuccess) ++launch_counter();
-    return err;
-  }
-  if (fp64) {
+  } else if (fp64) {
     if (c.jamp_in_smem && c.slots_in_smem) launch_one<double, true, true>(p, c, a, s);
     else if (c.jamp_in_smem) launch_one<double, true, false>(p, c, a, s);
     else if (c.slots_in_smem) launch_one<double, false, true>(p, c, a, s);

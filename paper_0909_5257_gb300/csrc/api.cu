@@ -16,6 +16,7 @@
 
 #include "../../include/mea.h"
 #include "colour_gemm.h"
+#include "jamp_gemm.h"
 #include "generator.h"
 #include "kernels.h"
 #include "process.h"
@@ -81,31 +82,75 @@ cudaError_t place_scratch(mea::DevBuf& buf, const mea::DevProgram& d, bool fp64,
   return cudaSuccess;
 }
 
+// Mixed path with both colour stages on the tensor cores: the interpreter
+// writes every diagram amplitude (no colour accumulators), the colour
+// amplitudes are formed as an exact integer contraction (jamp_gemm.cu), the
+// colour sum as a split-precision contraction (colour_gemm.cu).  Used for
+// processes without a straight-line kernel, or on request (colour_mode 2).
 bool use_tensor_colour(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode hm) {
   if (prec != MEA_PREC_MIXED || hm == MEA_HEL_GIVEN || P->opts.colour_mode == 1) return false;
+  if (!P->jmap.ok) return false;
   if (P->opts.colour_mode == 2) return true;
-  return P->prog.n_jamp >= 96;
+  return P->dev.gen == nullptr;
 }
 
-// Mixed path with the colour contraction on the tensor cores, in event chunks
-// whose FP32 colour amplitudes stay below ~256 MB: amplitude kernel (writes J),
-// colour GEMM, helicity sum + flags, FP64 re-evaluation of flagged events.
+// Events per chunk of the tensor-core path: the diagram amplitudes of a chunk
+// (8 bytes per diagram and pair) stay below kAmpBudget.
+constexpr size_t kAmpBudget = size_t(3) << 30;
+
+int64_t tc_chunk_events(const mea_process_s* P, int H, int64_t n) {
+  const size_t per_event = (size_t)H * 2 * (size_t)P->jmap.kd * sizeof(float);
+  return std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)(kAmpBudget / std::max<size_t>(per_event, 1))));
+}
+
+// Launch configuration of the amplitude-output interpreter for H lanes per event.
+mea::AmpConfig tc_amp_config(const mea_process_s* P, const mea::DevProgram& dp, int H, int64_t cn) {
+  mea::AmpConfig c = mea::plan_amp(dp, false, H, cn, P->num_sms, P->smem_optin, P->smem_per_sm);
+  if (P->tuned[0].grid > 0 && P->tuned_H[0] == H) {  // configuration chosen by mea_autotune
+    c = P->tuned[0];
+    int64_t tiles = (cn + c.E_cta - 1) / c.E_cta;
+    if (tiles < c.grid) c.grid = (int)std::max<int64_t>(tiles, 1);
+  }
+  return c;
+}
+
 mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* mom, int64_t n, mea_hel_mode hm,
                           double* me2, uint8_t* flags, cudaStream_t s) {
   const mea::Program& G = P->prog;
+  const mea::JampMap& JM = P->jmap;
   const int n_ext = G.n_ext;
   const int H = (hm == MEA_HEL_SUM_NONZERO) ? G.n_hel : (1 << n_ext);
   const int m = G.n_jamp;
   const int ldj = ((m + 15) / 16) * 16;
-  const size_t per_event = (size_t)H * 2 * ldj * sizeof(float);
-  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((256u << 20) / per_event)));
-  MEA_CUDA(S.jbuf.ensure(per_event * (size_t)chunk));
+  const int64_t chunk = tc_chunk_events(P, H, n);
+  const int64_t lda = ((2 * chunk * H + 127) / 128) * 128;
+  MEA_CUDA(S.abuf.ensure(sizeof(float) * (size_t)JM.kd * (size_t)lda));
+  MEA_CUDA(S.rowmax.ensure(sizeof(float) * 2 * (size_t)H * chunk));
+  MEA_CUDA(S.jabs.ensure(sizeof(float) * (size_t)JM.n_splits * (size_t)H * chunk));
+  MEA_CUDA(S.jbuf.ensure(sizeof(float) * 2 * (size_t)ldj * (size_t)H * chunk));
   MEA_CUDA(S.pairval.ensure(sizeof(double) * (size_t)H * chunk));
   MEA_CUDA(S.pairk.ensure(sizeof(float) * (size_t)H * chunk));
   MEA_CUDA(S.flag_list.ensure(sizeof(int32_t) * (size_t)chunk));
   MEA_CUDA(S.flag_count.ensure(sizeof(int32_t)));
   mea::DevProgram dp = P->dev;
-  dp.gen = nullptr;  // the interpreter writes the colour amplitudes
+  dp.gen = nullptr;   // the interpreter writes the diagram amplitudes
+  dp.n_colour = 0;    // and holds no colour accumulators
+  mea::JampGemmArgs jg;
+  jg.A = reinterpret_cast<const float*>(S.abuf.p);
+  jg.lda = lda;
+  jg.rowmax = reinterpret_cast<const float*>(S.rowmax.p);
+  jg.kd = JM.kd;
+  jg.kpad = JM.kpad;
+  jg.m = m;
+  jg.nc = JM.nc;
+  jg.n_splits = JM.n_splits;
+  jg.q = JM.q;
+  jg.cfac = JM.cfac;
+  jg.tiles = P->jmap_tiles;
+  jg.J = reinterpret_cast<float*>(S.jbuf.p);
+  jg.ldj = ldj;
+  jg.jabs = reinterpret_cast<float*>(S.jabs.p);
+  jg.status = P->status;
   mea::ColourGemmArgs cg;
   cg.m = m;
   cg.ldj = ldj;
@@ -118,14 +163,11 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
   cg.b_lo = P->cf_lo;
   cg.inv_den = P->dev.cf_inv_den;
   cg.status = P->status;
+  cg.J = reinterpret_cast<const float*>(S.jbuf.p);
+  cg.pairval = reinterpret_cast<double*>(S.pairval.p);
   for (int64_t c0 = 0; c0 < n; c0 += chunk) {
     const int64_t cn = std::min(chunk, n - c0);
-    mea::AmpConfig c = mea::plan_amp(dp, false, H, cn, P->num_sms, P->smem_optin, P->smem_per_sm);
-    if (P->tuned[0].grid > 0 && P->tuned_H[0] == H) {  // configuration chosen by mea_autotune
-      c = P->tuned[0];
-      int64_t tiles = (cn + c.E_cta - 1) / c.E_cta;
-      if (tiles < c.grid) c.grid = (int)std::max<int64_t>(tiles, 1);
-    }
+    mea::AmpConfig c = tc_amp_config(P, dp, H, cn);
     mea::AmpLaunch a;
     a.mom = mom + (size_t)c0 * n_ext * 4;
     a.n_events = cn;
@@ -133,17 +175,18 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
     a.me2 = me2 + c0;
     a.flags = flags ? flags + c0 : nullptr;
     a.flag_threshold = (float)P->opts.flag_threshold;
-    a.jamp_out = reinterpret_cast<float*>(S.jbuf.p);
+    a.amp_out = reinterpret_cast<float*>(S.abuf.p);
+    a.lda = lda;
+    a.amp_rowmax = reinterpret_cast<float*>(S.rowmax.p);
     a.pair_kappa = reinterpret_cast<float*>(S.pairk.p);
-    a.ldj = ldj;
     MEA_CUDA(place_scratch(S.s32, dp, false, c, a));
     MEA_CUDA(mea::launch_amp(dp, false, c, a, s));
-    cg.J = reinterpret_cast<const float*>(S.jbuf.p);
+    jg.n_pairs = cn * H;
+    MEA_CUDA(mea::launch_jamp_gemm(jg, P->num_sms, s));
     cg.n_pairs = cn * H;
-    cg.pairval = reinterpret_cast<double*>(S.pairval.p);
     MEA_CUDA(mea::launch_colour_gemm(cg, P->num_sms, s));
     mea::AmpLaunch f = a;
-    f.jamp_out = nullptr;
+    f.amp_out = nullptr;
     bool reeval = P->opts.reeval_fp64 != 0;
     if (reeval) {
       MEA_CUDA(cudaMemsetAsync(S.flag_count.p, 0, sizeof(int32_t), s));
@@ -151,7 +194,8 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
       f.flag_count = reinterpret_cast<int32_t*>(S.flag_count.p);
     }
     MEA_CUDA(mea::launch_finish(f, H, reinterpret_cast<const double*>(S.pairval.p),
-                                reinterpret_cast<const float*>(S.pairk.p), s));
+                                reinterpret_cast<const float*>(S.pairk.p), s,
+                                reinterpret_cast<const float*>(S.jabs.p), JM.n_splits));
     if (reeval) {
       mea::AmpConfig c2 = mea::plan_amp(P->dev, true, H, cn, P->num_sms, P->smem_optin, P->smem_per_sm);
       mea::AmpLaunch b = f;
@@ -218,6 +262,9 @@ mea_status do_evaluate(mea_process_s* P, mea::EvalScratch& S, const double* mom,
 
 namespace mea {
 mea_status set_error(mea_status s, const std::string& msg) { return fail(s, msg); }
+bool uses_tensor_path(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode hm) {
+  return use_tensor_colour(P, prec, hm);
+}
 mea_status evaluate_with(mea_process_s* P, EvalScratch& S, const double* mom, int64_t n, mea_hel_mode hm,
                          const int8_t* hel, mea_prec_mode prec, double* me2, uint8_t* flags, cudaStream_t s) {
   return do_evaluate(P, S, mom, n, hm, hel, prec, me2, flags, s);
@@ -233,12 +280,14 @@ size_t scratch_estimate(mea_process_s* P, int64_t n, mea_prec_mode prec) {
   };
   if (use_tensor_colour(P, prec, MEA_HEL_SUM_NONZERO)) {
     const int ldj = ((G.n_jamp + 15) / 16) * 16;
-    const size_t per_event = (size_t)H * 2 * ldj * sizeof(float);
-    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((256u << 20) / per_event)));
+    const int64_t chunk = tc_chunk_events(P, H, n);
+    const int64_t lda = ((2 * chunk * H + 127) / 128) * 128;
     DevProgram dp = P->dev;
     dp.gen = nullptr;
-    return per_event * (size_t)chunk + (size_t)H * chunk * 12 + (size_t)chunk * 4 + work(dp, false, chunk) +
-           work(P->dev, true, chunk);
+    dp.n_colour = 0;
+    return sizeof(float) * (size_t)P->jmap.kd * (size_t)lda + sizeof(float) * (size_t)H * chunk * (3 + P->jmap.n_splits) +
+           sizeof(float) * 2 * (size_t)ldj * (size_t)H * chunk + sizeof(double) * (size_t)H * chunk +
+           (size_t)chunk * 4 + 4096 + work(dp, false, chunk) + work(P->dev, true, chunk);
   }
   size_t b = work(P->dev, fp64, n);
   if (!fp64 && P->opts.reeval_fp64) b += (size_t)n * 4 + 256 + work(P->dev, true, n);
@@ -352,6 +401,21 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
     P->cf_hi = dh;
     P->cf_lo = exact ? nullptr : dl;
     P->status = const_cast<int*>(dst);
+  }
+  {
+    // diagram -> colour-amplitude coefficients for the tensor-core stage
+    P->jmap = mea::build_jamp_map(G);
+    if (P->jmap.ok) {
+      const __half* dt = nullptr;
+      const float* dw = nullptr;
+      if ((e = upload(P, P->jmap.tiles, &dt)) != cudaSuccess || (e = upload(P, P->jmap.weight, &dw)) != cudaSuccess) {
+        destroy(P);
+        return fail(MEA_E_CUDA, std::string("mea_create_process: ") + cudaGetErrorString(e));
+      }
+      P->jmap_tiles = dt;
+      D.amp_w = dw;
+      std::vector<__half>().swap(P->jmap.tiles);
+    }
   }
   *out = P;
   return MEA_OK;

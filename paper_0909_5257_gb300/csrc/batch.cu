@@ -63,8 +63,23 @@ mea_status mea_autotune(mea_process_t P, const double* mom, int64_t n, mea_prec_
   const int ti = fp64 ? 1 : 0;
   const int H = P->prog.n_hel;
   mea::DevProgram dp = P->dev;
-  const bool tc = !fp64 && P->opts.colour_mode != 1 && (P->opts.colour_mode == 2 || P->prog.n_jamp >= 96);
-  if (tc) dp.gen = nullptr;  // the tensor-core colour path runs the interpreter
+  const bool tc = mea::uses_tensor_path(P, prec, MEA_HEL_SUM_NONZERO);
+  mea::DevBuf abuf, rowmax, pairk;
+  int64_t lda = 0;
+  if (tc) {
+    // the tensor-core path runs the amplitude-output interpreter: time that
+    dp.gen = nullptr;
+    dp.n_colour = 0;
+    const size_t per_event = (size_t)H * 2 * (size_t)P->jmap.kd * sizeof(float);
+    n = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((size_t(1) << 30) / std::max<size_t>(per_event, 1))));
+    lda = ((2 * n * H + 127) / 128) * 128;
+    if (abuf.ensure(sizeof(float) * (size_t)P->jmap.kd * (size_t)lda) != cudaSuccess ||
+        rowmax.ensure(sizeof(float) * 2 * (size_t)H * n) != cudaSuccess ||
+        pairk.ensure(sizeof(float) * (size_t)H * n) != cudaSuccess) {
+      abuf.release(); rowmax.release(); pairk.release();
+      return mea::set_error(MEA_E_NOMEM, "mea_autotune: no room for the amplitude sample");
+    }
+  }
   std::vector<mea::AmpConfig> cands =
       mea::candidate_configs(dp, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
   mea::AmpConfig def = mea::plan_amp(dp, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
@@ -85,6 +100,12 @@ mea_status mea_autotune(mea_process_t P, const double* mom, int64_t n, mea_prec_
     a.n_events = n;
     a.me2 = me2;
     a.flag_threshold = (float)P->opts.flag_threshold;
+    if (tc) {
+      a.amp_out = reinterpret_cast<float*>(abuf.p);
+      a.lda = lda;
+      a.amp_rowmax = reinterpret_cast<float*>(rowmax.p);
+      a.pair_kappa = reinterpret_cast<float*>(pairk.p);
+    }
     size_t jb = (mea::jamp_scratch_bytes_needed(dp, fp64, c) + 255) & ~size_t(255);
     size_t sb = mea::slot_scratch_bytes_needed(dp, fp64, c);
     mea::DevBuf& buf = fp64 ? S.s64 : S.s32;
@@ -105,6 +126,9 @@ mea_status mea_autotune(mea_process_t P, const double* mom, int64_t n, mea_prec_
     if (t_best < best) { best = t_best; best_i = (int)i; }
   }
   S.release();
+  abuf.release();
+  rowmax.release();
+  pairk.release();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamDestroy(s);

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <numeric>
 #include <sstream>
 #include <stdexcept>
 #include <string>
@@ -52,6 +53,17 @@ void emit_body(std::ostringstream& o, const mea::Program& P, const std::string& 
   o << "    cx<R> J[" << m << "];\n    cx<R> Jl[" << m << "];\n";
   o << "#pragma unroll\n    for (int a = 0; a < " << m << "; ++a) { J[a] = mk<R>(R(0), R(0)); Jl[a] = J[a]; }\n";
   o << "    float mass = 0.f;\n";
+  // Common factor of the colour coefficients: the amplitudes are accumulated
+  // with the cofactors (+-1 for every process here) and J is scaled by the
+  // factor at the end -- a power of two for the gluon processes, so the
+  // result is bitwise that of accumulating the full coefficients.
+  int cfac = 0;
+  bool cfac_real = true;
+  for (const ColEntry& c : P.col) {
+    cfac = std::gcd(cfac, std::gcd(std::abs((int)c.re), std::abs((int)c.im)));
+    if (c.im != 0) cfac_real = false;
+  }
+  if (cfac <= 0 || (cfac & (cfac - 1)) != 0) cfac = 1;  // keep the scaling exact
   std::vector<int> slot_op(P.n_slots + 1, -1);
   for (size_t i = 0; i < P.ops.size(); ++i) {
     const Op& op = P.ops[i];
@@ -103,11 +115,25 @@ void emit_body(std::ostringstream& o, const mea::Program& P, const std::string& 
           o << "gggg_amp<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", " << in(3) << ", gg);\n";
         else
           o << "iov_amp<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", g);\n";
+        int wsum = 0;  // sum over entries of |Re c| + |Im c| (cancellation indicator)
         for (uint32_t k = 0; k < op.col_count; ++k) {
           const ColEntry& c = P.col[op.col_begin + k];
-          o << "      jacc<R>(J[" << c.alpha << "], Jl[" << c.alpha << "], mass, R(" << (int)c.re << "), R("
-            << (int)c.im << "), a);\n";
+          wsum += std::abs((int)c.re) + std::abs((int)c.im);
+          if (cfac_real) {
+            const int n = (int)c.re / cfac;
+            if (n == 1 || n == -1)
+              o << "      jadd<R>(J[" << c.alpha << "], Jl[" << c.alpha << "], " << (n > 0 ? "a" : "neg<R>(a)")
+                << ");\n";
+            else
+              o << "      jadd<R>(J[" << c.alpha << "], Jl[" << c.alpha << "], mk<R>(R(" << n << ") * a.r, R(" << n
+                << ") * a.i));\n";
+          } else {
+            o << "      jadd<R>(J[" << c.alpha << "], Jl[" << c.alpha << "], mk<R>(R(" << (int)c.re << ") * a.r - R("
+              << (int)c.im << ") * a.i, R(" << (int)c.re << ") * a.i + R(" << (int)c.im << ") * a.r));\n";
+          }
         }
+        o << "      if constexpr (std::is_same<R, float>::value) mass += " << wsum
+          << ".f * (fabsf(a.r) + fabsf(a.i));\n";
         o << "    }\n";
         break;
       }
@@ -118,8 +144,9 @@ void emit_body(std::ostringstream& o, const mea::Program& P, const std::string& 
   }
   // colour quadratic form with the integer colour matrix (symmetric)
   o << "    cx<R> F[" << m << "];\n    float jabs = 0.f;\n";
-  o << "#pragma unroll\n    for (int a = 0; a < " << m << "; ++a) { F[a] = jfin<R>(J[a], Jl[a]); jabs += "
-       "(float)(fabs(F[a].r) + fabs(F[a].i)); }\n";
+  const std::string scale = (cfac_real && cfac != 1) ? " * R(" + std::to_string(cfac) + ")" : "";
+  o << "#pragma unroll\n    for (int a = 0; a < " << m << "; ++a) { F[a] = jfin<R>(J[a], Jl[a]); F[a].r = F[a].r"
+    << scale << "; F[a].i = F[a].i" << scale << "; jabs += (float)(fabs(F[a].r) + fabs(F[a].i)); }\n";
   o << "    R tot = R(0);\n";
   for (int a = 0; a < m; ++a) {
     std::ostringstream z;

@@ -28,6 +28,7 @@
 
 #include "colour_gemm.h"
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace mea {
 namespace {
@@ -35,81 +36,7 @@ namespace {
 constexpr int kThreads = 128;   // 4 warps: TMEM lanes 0..127 = tile rows
 constexpr int kM = 128;         // tile rows (64 pairs x {re, im})
 constexpr int kKC = 64;         // K elements per shared-memory stage
-constexpr uint32_t kSpinLimit = 1u << 26;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// UMMA shared-memory matrix descriptor (no swizzle, K-major canonical layout).
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor cores
-  return d;                // base offset 0, swizzle none
-}
-
-// Instruction descriptor: kind::f16, A = B = F16, D = F32, both K-major.
-__host__ __device__ constexpr uint32_t make_idesc(int m, int n) {
-  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the given phase; returns false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
-    if (mbar_try_wait(bar, phase)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Byte offset of element (row, k) in a canonical K-major no-swizzle tile whose
-// K extent is kc elements.
-__device__ __forceinline__ uint32_t canon_off(int row, int k, int kc) {
-  return (uint32_t)((row >> 3) * (kc / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
-}
+using namespace tc;
 
 __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -139,9 +66,9 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   const uint32_t tmem = *tslot;
   uint32_t phase = 0;
   int pending = -1;  // phase of a wait that expired (drained once more before freeing TMEM)
@@ -199,9 +126,9 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
           *reinterpret_cast<__half*>(b_lo + off) = lo;
         }
         fence_async_smem();
-        tc_fence_before();
+        fence_before();
         __syncthreads();
-        tc_fence_after();
+        fence_after();
         if (t == 0 && !*abort_flag) {
           const uint32_t lbo = 128, sbo_a = (kKC / 8) * 128, sbo_b = (kKC / 8) * 128;
           for (int ks = 0; ks < kKC / 16; ++ks) {
@@ -231,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
           }
         }
         phase ^= 1u;
-        tc_fence_after();
+        fence_after();
         // epilogue of this K chunk: this thread owns TMEM lane t (its row)
         if (!*abort_flag) {
           const int64_t r = row0 + t;
@@ -247,10 +174,10 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
             }
           }
         }
-        tc_fence_before();
+        fence_before();
       }
       __syncthreads();
-      tc_fence_after();
+      fence_after();
     }
     // row value = (J . Z) / scale ; pair value = (re row + im row) / D
     {
@@ -268,9 +195,9 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
   // the tensor memory they write is released
   if (pending >= 0) mbar_wait(bar, (uint32_t)pending);
   // free tensor memory (after every tcgen05.ld has completed)
-  tc_fence_before();
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)g.tmem_cols)
                  : "memory");

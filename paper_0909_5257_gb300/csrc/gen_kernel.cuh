@@ -35,6 +35,29 @@ __device__ __forceinline__ void jacc(cx<R>& hi, cx<R>& lo, float& mass, R cr, R 
   }
 }
 
+// J += a, two-sum compensated in FP32 (the coefficient is folded into a by
+// the emitter; mass is accumulated once per amplitude).
+template <typename R>
+__device__ __forceinline__ void jadd(cx<R>& hi, cx<R>& lo, cx<R> a) {
+  if constexpr (std::is_same<R, float>::value) {
+    float s, e;
+    two_sum(hi.r, a.r, s, e);
+    hi.r = s;
+    lo.r += e;
+    two_sum(hi.i, a.i, s, e);
+    hi.i = s;
+    lo.i += e;
+  } else {
+    hi.r += a.r;
+    hi.i += a.i;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ cx<R> neg(cx<R> a) {
+  return cx<R>{-a.r, -a.i};
+}
+
 template <typename R>
 __device__ __forceinline__ cx<R> jfin(cx<R> hi, cx<R> lo) {
   if constexpr (std::is_same<R, float>::value) return cx<R>{hi.r + lo.r, hi.i + lo.i};

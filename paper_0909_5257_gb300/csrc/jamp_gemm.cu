@@ -1,0 +1,310 @@
+// Colour amplitudes J_alpha = sum_d c_{alpha d} A_d (Eq. (color-amplitude))
+// as an exact integer contraction on the tensor cores.
+//
+// The amplitude kernel writes every Feynman-diagram amplitude A_d of every
+// (event, helicity) pair in FP32.  All colour coefficients of the processes
+// handled here are real, c = cfac * n with small integers n.  Per row r (the
+// real or the imaginary parts of one pair) the amplitudes are scaled by a
+// power of two, x = A * 2^(q - e_r) with 2^(e_r - 1) <= max_d |A_rd| < 2^e_r,
+// so that |x| < 2^q, and split into three integer digits
+//     x = h + m 2^-(q+1) + l 2^-2(q+1) + O(2^-(2q+3)),   |h|, |m|, |l| <= 2^q,
+// each exact in FP16 (q <= 11).  tcgen05.mma kind::f16 then forms
+// H = sum_d n_d h_d, M = sum_d n_d m_d, L = sum_d n_d l_d in three FP32
+// tensor-memory accumulators over the whole diagram sum: every product and
+// every partial sum is an integer below sum_d |n_{alpha d}| 2^q < 2^24, so the
+// accumulation is exact whatever order or internal rounding the tensor core
+// uses.  The epilogue recombines cfac * 2^(e_r - q) (H + M 2^-(q+1) +
+// L 2^-2(q+1)) in FP64 and rounds once to FP32.  The only error left is the
+// digit truncation, below 2^-(3q+3) of the row maximum: the colour amplitudes
+// come out as the correctly rounded FP32 sum of the FP32 diagram amplitudes
+// (the compensated summation of the paper's Sec. 3.2 step 3 with nothing left
+// to compensate).
+//
+// Tile: 128 rows (64 pairs) x nc colour columns, K in chunks of 64 diagrams,
+// two shared-memory stages so that the digit conversion of chunk k+1 overlaps
+// the MMAs of chunk k.  Every wait is bounded; on expiry the kernel records an
+// error in *status, drains its MMAs with one more bounded wait, frees its
+// tensor memory and returns.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <numeric>
+
+#include "jamp_gemm.h"
+#include "kernels.h"
+#include "tc_common.cuh"
+
+namespace mea {
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 256;  // 8 warps convert; warps 0..3 own TMEM lanes 0..127 in the epilogue
+constexpr int kM = 128;
+constexpr int kKC = 64;
+constexpr int kStageA = kM * kKC * 2;  // one FP16 digit plane of A
+
+__host__ __device__ constexpr size_t stage_bytes(int nc) { return (size_t)3 * kStageA + (size_t)nc * kKC * 2; }
+
+__global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  const int NC = g.nc;
+  const size_t SB = stage_bytes(NC);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SB);  // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  int* abort_flag = reinterpret_cast<int*>(tslot + 1);
+  float* rscale = reinterpret_cast<float*>(tslot + 4);  // [128] 2^(q - e_r)
+  float* rowabs = rscale + kM;                          // [128] sum |J| of the row in this split
+
+  uint32_t tmem_cols = 32;
+  while (tmem_cols < (uint32_t)(3 * NC)) tmem_cols <<= 1;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *abort_flag = 0;
+  }
+  if (warp == 0) tmem_alloc(tslot, tmem_cols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t d_h = tmem, d_m = tmem + (uint32_t)NC, d_l = tmem + (uint32_t)(2 * NC);
+
+  uint32_t phase[2] = {0u, 0u};
+  int outstanding[2] = {0, 0};  // commits on each stage's barrier not yet waited for
+  const int64_t n_rows = 2 * g.n_pairs;
+  const int64_t n_mt = (n_rows + kM - 1) / kM;
+  const int n_kc = g.kpad / kKC;
+  const uint32_t idesc = make_idesc(kM, NC);
+  const float w1 = ldexpf(1.f, g.q + 1);  // digit base
+  const double inv_w1 = 1.0 / (double)w1, inv_w2 = inv_w1 * inv_w1;
+
+  auto wait_stage = [&](int st) {
+    if (outstanding[st] == 0) return;
+    if (!*abort_flag) {
+      if (!mbar_wait(&bar[st], phase[st])) {
+        atomicExch(abort_flag, 1);
+        if (g.status) atomicExch(g.status, 1);
+        return;  // left outstanding: drained once more before TMEM is freed
+      }
+    } else {
+      return;
+    }
+    phase[st] ^= 1u;
+    outstanding[st] = 0;
+  };
+
+  for (int64_t w = blockIdx.x; w < n_mt * g.n_splits; w += gridDim.x) {
+    const int64_t mt = w / g.n_splits;
+    const int split = (int)(w - mt * g.n_splits);
+    const int64_t row0 = mt * kM;
+    const int n0 = split * NC;
+    if (t < kM) {
+      const int64_t r = row0 + t;
+      float mx = (r < n_rows) ? g.rowmax[r] : 0.f;
+      float sc;
+      if (!isfinite(mx)) {
+        sc = __int_as_float(0x7fc00000);  // a non-finite row stays non-finite (flagged later)
+      } else {
+        int e = 0;
+        if (mx > 0.f) frexpf(mx, &e);
+        sc = ldexpf(1.f, max(-120, min(120, g.q - e)));
+      }
+      rscale[t] = sc;
+      rowabs[t] = 0.f;
+    }
+    __syncthreads();
+
+    for (int kc = 0; kc < n_kc; ++kc) {
+      const int st = kc & 1;
+      wait_stage(st);  // the MMAs that read this stage two chunks ago are done
+      unsigned char* a_h = smem + st * SB;
+      unsigned char* a_m = a_h + kStageA;
+      unsigned char* a_l = a_m + kStageA;
+      unsigned char* b_t = a_l + kStageA;
+      // A digits: thread -> (row, 8 consecutive diagrams); global reads are
+      // coalesced over rows, shared stores are whole 16-byte core-matrix rows
+      {
+        const int row = t & (kM - 1);
+        const int64_t r = row0 + row;
+        const float sc = rscale[row];
+        for (int kg = t >> 7; kg < kKC / 8; kg += kThreads / kM) {
+          __align__(16) __half hv[8], mv[8], lv[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int d = kc * kKC + kg * 8 + i;
+            float x = 0.f;
+            if (r < n_rows && d < g.kd) x = g.A[(size_t)d * g.lda + r] * sc;
+            const float h = rintf(x);
+            const float r1 = (x - h) * w1;
+            const float mm = rintf(r1);
+            const float l = rintf((r1 - mm) * w1);
+            hv[i] = __float2half_rn(h);
+            mv[i] = __float2half_rn(mm);
+            lv[i] = __float2half_rn(l);
+          }
+          const uint32_t off = canon_off(row, kg * 8, kKC);
+          *reinterpret_cast<uint4*>(a_h + off) = *reinterpret_cast<const uint4*>(hv);
+          *reinterpret_cast<uint4*>(a_m + off) = *reinterpret_cast<const uint4*>(mv);
+          *reinterpret_cast<uint4*>(a_l + off) = *reinterpret_cast<const uint4*>(lv);
+        }
+      }
+      // B: the precomputed canonical tile of coefficient integers
+      {
+        const uint4* src = reinterpret_cast<const uint4*>(g.tiles + ((size_t)split * n_kc + kc) * NC * kKC);
+        uint4* dst = reinterpret_cast<uint4*>(b_t);
+        for (int i = t; i < NC * kKC / 8; i += kThreads) dst[i] = __ldg(src + i);
+      }
+      fence_async_smem();
+      fence_before();
+      __syncthreads();
+      fence_after();
+      if (!*abort_flag) {
+        if (t == 0) {
+          const uint32_t lbo = 128, sbo = (kKC / 8) * 128;
+          for (int ks = 0; ks < kKC / 16; ++ks) {
+            const uint32_t koff = (uint32_t)(ks * 2 * 128);
+            const uint64_t db = make_desc(smem_u32(b_t) + koff, lbo, sbo);
+            const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+            mma_f16(d_l, make_desc(smem_u32(a_l) + koff, lbo, sbo), db, idesc, acc);
+            mma_f16(d_m, make_desc(smem_u32(a_m) + koff, lbo, sbo), db, idesc, acc);
+            mma_f16(d_h, make_desc(smem_u32(a_h) + koff, lbo, sbo), db, idesc, acc);
+          }
+          mma_commit(&bar[st]);
+        }
+        outstanding[st] = 1;
+      }
+    }
+    // all MMAs of this tile: the last chunk's commit covers every earlier one,
+    // but each barrier's phases are consumed in order
+    if (n_kc >= 2) wait_stage((n_kc - 2) & 1);
+    wait_stage((n_kc - 1) & 1);
+    fence_after();
+    if (warp < 4 && !*abort_flag) {
+      const int64_t r = row0 + t;
+      const double back = g.cfac / (double)rscale[t];
+      const uint32_t lane = (uint32_t)(warp * 32) << 16;
+      float* jrow = g.J + (size_t)r * g.ldj;
+      float sabs = 0.f;
+      for (int c0 = 0; c0 < NC && n0 + c0 < g.m; c0 += 16) {
+        float vh[16], vm[16], vl[16];
+        tmem_ld16(d_h + lane + (uint32_t)c0, vh);
+        tmem_ld16(d_m + lane + (uint32_t)c0, vm);
+        tmem_ld16(d_l + lane + (uint32_t)c0, vl);
+        if (r < n_rows) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int a = n0 + c0 + i;
+            if (a < g.m) {
+              const float v = (float)(((double)vh[i] + (double)vm[i] * inv_w1 + (double)vl[i] * inv_w2) * back);
+              jrow[a] = v;
+              sabs += fabsf(v);
+            }
+          }
+        }
+      }
+      rowabs[t] = sabs;
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t < kM / 2 && g.jabs) {
+      const int64_t p = row0 / 2 + t;
+      if (p < g.n_pairs) g.jabs[(size_t)split * g.n_pairs + p] = rowabs[2 * t] + rowabs[2 * t + 1];
+    }
+  }
+  // an expired wait: one more bounded wait for each stage's MMAs before the
+  // tensor memory they write is released
+  for (int st = 0; st < 2; ++st)
+    if (outstanding[st]) mbar_wait(&bar[st], phase[st]);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) tmem_dealloc(tmem, tmem_cols);
+}
+
+}  // namespace
+
+JampMap build_jamp_map(const Program& p) {
+  JampMap M;
+  M.m = p.n_jamp;
+  int kd = 0;
+  int g = 0;
+  bool real = true;
+  for (const Op& op : p.ops) {
+    if (op.type < OP_AVVV) continue;
+    ++kd;
+    for (uint32_t k = 0; k < op.col_count; ++k) {
+      const ColEntry& c = p.col[op.col_begin + k];
+      if (c.im != 0) real = false;
+      g = std::gcd(g, std::abs((int)c.re));
+    }
+  }
+  M.kd = kd;
+  if (!real || kd == 0 || M.m <= 0 || g == 0) return M;
+  M.cfac = g;
+  M.nc = std::min(160, ((M.m + 15) / 16) * 16);
+  M.n_splits = (M.m + M.nc - 1) / M.nc;
+  // balance the splits: the smallest multiple of 16 that still needs n_splits
+  M.nc = std::min(M.nc, (((M.m + M.n_splits - 1) / M.n_splits) + 15) / 16 * 16);
+  M.kpad = ((kd + kKC - 1) / kKC) * kKC;
+  std::vector<int> colw(M.m, 0);
+  M.weight.assign(kd, 0.f);
+  const int n_kc = M.kpad / kKC;
+  M.tiles.assign((size_t)M.n_splits * n_kc * M.nc * kKC, __float2half(0.f));
+  int d = 0;
+  for (const Op& op : p.ops) {
+    if (op.type < OP_AVVV) continue;
+    for (uint32_t k = 0; k < op.col_count; ++k) {
+      const ColEntry& c = p.col[op.col_begin + k];
+      const int n = c.re / g;
+      const int a = c.alpha;
+      colw[a] += std::abs(n);
+      M.weight[d] += (float)std::abs((int)c.re);
+      const int split = a / M.nc, row = a - split * M.nc;
+      const int kc = d / kKC, kk = d - kc * kKC;
+      __half* tile = M.tiles.data() + ((size_t)split * n_kc + kc) * M.nc * kKC;
+      const float prev = __half2float(*reinterpret_cast<__half*>(reinterpret_cast<char*>(tile) + tc::canon_off(row, kk, kKC)));
+      *reinterpret_cast<__half*>(reinterpret_cast<char*>(tile) + tc::canon_off(row, kk, kKC)) =
+          __float2half((float)(prev + n));
+    }
+    ++d;
+  }
+  const int wmax = *std::max_element(colw.begin(), colw.end());
+  // exact accumulation: sum_d |n_{alpha d}| 2^q < 2^24 for every alpha, and 2^q <= 2048 (FP16 integers)
+  int q = 11;
+  while (q > 0 && (double)wmax * std::ldexp(1.0, q) >= 16777216.0) --q;
+  M.q = q;
+  // every tile entry must itself be a small integer (coefficients of one diagram in one colour add up)
+  for (const __half& h : M.tiles)
+    if (std::fabs(__half2float(h)) > 2048.f) return M;
+  M.ok = q >= 8;  // digit truncation below 2^-27 of the row maximum
+  return M;
+}
+
+size_t jamp_gemm_smem(int nc) { return 2 * stage_bytes(nc) + 16 + 16 + (size_t)kM * 8 + 16; }
+
+cudaError_t launch_jamp_gemm(const JampGemmArgs& a, int num_sms, cudaStream_t s) {
+  if (a.n_pairs <= 0) return cudaSuccess;
+  const size_t sm = jamp_gemm_smem(a.nc);
+  cudaError_t e = cudaFuncSetAttribute(jamp_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int64_t work = ((2 * a.n_pairs + kM - 1) / kM) * a.n_splits;
+  int tmem = 32;
+  while (tmem < 3 * a.nc) tmem *= 2;
+  int per_sm = std::max(1, std::min<int>(512 / tmem, (int)((227u << 10) / sm)));
+  const int grid = (int)std::min<int64_t>(work, (int64_t)num_sms * per_sm);
+  jamp_gemm_kernel<<<grid, kThreads, sm, s>>>(a);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) ++launch_counter();
+  return e;
+}
+
+}  // namespace mea

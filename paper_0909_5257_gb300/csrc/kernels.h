@@ -42,6 +42,7 @@ struct DevProgram {
   const int8_t* hel_all = nullptr;    // [2^n_ext][n_ext]
   double g = 0;                       // g_s
   const GenEntry* gen = nullptr;      // straight-line kernel of this process, if emitted
+  const float* amp_w = nullptr;       // [n_diagrams] sum_alpha |c_alpha d| (amplitude-output mode)
 };
 
 struct AmpLaunch {
@@ -61,6 +62,9 @@ struct AmpLaunch {
   float* jamp_out = nullptr;          // split colour stage: write J rows [2*pair][ldj] (FP32) and
   float* pair_kappa = nullptr;        //   the per-pair indicator instead of the colour sum
   int ldj = 0;
+  float* amp_out = nullptr;           // amplitude-output mode: A[d][lda], (Re, Im) of pair p at 2p, 2p+1;
+  int64_t lda = 0;                    //   pair_kappa then receives sum_d w_d |A_d| and
+  float* amp_rowmax = nullptr;        //   amp_rowmax[2p], [2p+1] the row maxima of |Re A|, |Im A|
   float* jamp_scratch = nullptr;      // global colour-amplitude accumulators when not in SMEM
   float* slot_scratch = nullptr;      // global wavefunction slots when not in SMEM
 };
@@ -90,8 +94,10 @@ cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const
                        cudaStream_t s);
 
 // Helicity sum + flags for the split colour stage: me2 = 1/4 sum_h pairval.
+// With jabs ([n_splits][n_events*H] sums of |J|), pair_kappa holds sum |c A|
+// and the per-pair indicator is pair_kappa / sum_splits jabs.
 cudaError_t launch_finish(const AmpLaunch& a, int H, const double* pairval, const float* pair_kappa,
-                          cudaStream_t s);
+                          cudaStream_t s, const float* jabs = nullptr, int n_splits = 0);
 
 // Phase-space generator kernel (input generator).
 struct PsConfigDev {

@@ -10,6 +10,7 @@
 
 #include "../../include/mea.h"
 #include "generator.h"
+#include "jamp_gemm.h"
 #include "kernels.h"
 
 namespace mea {
@@ -36,10 +37,10 @@ struct DevBuf {
 // Scratch of one in-flight evaluation.  Evaluations that may overlap on the
 // GPU (different streams, graph branches, server slots) use distinct sets.
 struct EvalScratch {
-  DevBuf s32, s64, flag_list, flag_count, jbuf, pairval, pairk;
+  DevBuf s32, s64, flag_list, flag_count, jbuf, pairval, pairk, abuf, rowmax, jabs;
   void release() {
     s32.release(); s64.release(); flag_list.release(); flag_count.release();
-    jbuf.release(); pairval.release(); pairk.release();
+    jbuf.release(); pairval.release(); pairk.release(); abuf.release(); rowmax.release(); jabs.release();
   }
 };
 
@@ -65,6 +66,9 @@ struct mea_process_s {
   const __half* cf_hi = nullptr;
   const __half* cf_lo = nullptr;
   int* status = nullptr;
+  // diagram -> colour-amplitude map for the tensor-core colour-amplitude stage
+  mea::JampMap jmap;                  // host description (tiles released after upload)
+  const __half* jmap_tiles = nullptr;  // device copy of the coefficient tiles
   // host-buffer pipeline
   void* pin_in[2] = {nullptr, nullptr};
   void* pin_out[2] = {nullptr, nullptr};
@@ -80,6 +84,9 @@ namespace mea {
 // Enqueue one evaluation on stream s using scratch set S (see api.cu).
 mea_status evaluate_with(mea_process_s* P, EvalScratch& S, const double* mom, int64_t n, mea_hel_mode hm,
                          const int8_t* hel, mea_prec_mode prec, double* me2, uint8_t* flags, cudaStream_t s);
+// True when evaluations of this precision / helicity mode run the tensor-core
+// path (amplitude-output interpreter + colour-amplitude and colour GEMMs).
+bool uses_tensor_path(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode hm);
 // Device scratch bytes an evaluation of n events would hold (admission control).
 size_t scratch_estimate(mea_process_s* P, int64_t n, mea_prec_mode prec);
 }  // namespace mea

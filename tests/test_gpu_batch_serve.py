@@ -83,7 +83,7 @@ def test_server_results_identical_alone_and_in_mix():
     procs = [(mea.Process([2, 2, 2, 2, 21, 21, 21]), 5, 500.0, 5000.0),
              (mea.Process([2, -2, 21, 21, 21, 21]), 4, 300.0, 3000.0),
              (mea.Process([21] * 5), 3, 200.0, 2000.0)]
-    srv = mea.Server(mem_budget_bytes=8 << 30, n_slots=4, chunk_events=1 << 12)
+    srv = mea.Server(mem_budget_bytes=32 << 30, n_slots=4, chunk_events=1 << 12)
     reqs = []
     first = 0
     for k in range(12):

@@ -251,11 +251,12 @@ def test_tensor_core_colour_stage_forced(name):
     assert rel.max() <= 1e-4, f"{name}: max rel {rel.max():.3e}"
 
 
-@pytest.mark.parametrize("name", ["gg>gggg", "uu>uuggg", "uu~>ggggg", "gg>ggggg"])
+@pytest.mark.parametrize("name", ["gg>gggg", "uu~>gggg", "uu>uuggg", "uu~>ggggg", "gg>ggggg"])
 def test_tensor_core_colour_stage_default_for_large_bases(name):
-    """Colour bases of 120 and more take the tensor-core stage by default; the
-    CUDA-core stage (colour_mode 1) on the same inputs agrees within the mixed
-    tolerance."""
+    """Processes without a straight-line kernel take the tensor-core stages by
+    default (diagram amplitudes out, colour amplitudes and colour sum on
+    tcgen05); the CUDA-core stage (colour_mode 1, two-sum colour amplitudes)
+    on the same inputs agrees within the mixed tolerance."""
     _, pdg, _, _ = _case(name)
     mom, ref = _data(name)
     tc, _ = _run(pdg, mom, _mea().PREC_MIXED)
@@ -264,3 +265,25 @@ def test_tensor_core_colour_stage_default_for_large_bases(name):
     assert np.max(np.abs(tc / ref - 1.0)) <= 1e-4
     assert np.max(np.abs(cc / ref - 1.0)) <= 1e-4
     assert np.max(np.abs(tc / cc - 1.0)) <= 1e-4
+
+
+@pytest.mark.parametrize("pdg,nf,lo,hi,n", [([21] * 7, 5, 500.0, 5000.0, 1001),
+                                            ([2, -2, 21, 21, 21, 21, 21], 5, 500.0, 5000.0, 4999)])
+def test_tensor_path_several_chunks_against_fp64(pdg, nf, lo, hi, n):
+    """The tensor-core path splits large requests into event chunks (diagram
+    amplitudes of a chunk below a few GB): gg>5g at 1001 events and uu~>5g at
+    4999 events span several chunks with a ragged last one.  Every event
+    agrees with the GPU FP64 path (itself pinned to the oracle at 1e-12)."""
+    mea = _mea()
+    P = _proc(pdg)
+    d_mom = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
+    mea.generate_phase_space(nf, n, d_mom, seed=ps.SEED_BASE + 211, rs_lo=lo, rs_hi=hi)
+    mixed = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    fp64 = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    P.evaluate(d_mom, mixed, precision=mea.PREC_MIXED)
+    P.evaluate(d_mom, fp64, precision=mea.PREC_FP64)
+    P.check_status()
+    rel = (mixed / fp64 - 1.0).abs().cpu().numpy()
+    assert np.all(np.isfinite(rel))
+    assert np.median(rel) <= 1e-6, np.median(rel)
+    assert rel.max() <= 1e-4, rel.max()
