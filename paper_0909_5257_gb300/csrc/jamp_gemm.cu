@@ -47,6 +47,7 @@ constexpr int kThreads = 256;  // 8 warps convert; warps 0..3 own TMEM lanes 0..
 constexpr int kM = 128;
 constexpr int kKC = 64;
 constexpr int kStageA = kM * kKC * 2;  // one FP16 digit plane of A
+constexpr int kMaxNC = 128;            // 3 accumulators of nc columns in 512 TMEM columns; 4 tile vectors per thread
 
 __host__ __device__ constexpr size_t stage_bytes(int nc) { return (size_t)3 * kStageA + (size_t)nc * kKC * 2; }
 
@@ -122,6 +123,33 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
     }
     __syncthreads();
 
+    // Register prefetch: each thread holds its 4 x 8 amplitudes and 4 tile
+    // vectors of the next chunk, issued right after the current chunk is
+    // converted so that the loads overlap the MMAs and the barrier.
+    const int row = t & (kM - 1);
+    const int64_t r = row0 + row;
+    const bool row_ok = r < n_rows;
+    float pa[kKC / 8 / (kThreads / kM)][8];
+    uint4 pb[4];
+    const int nb = NC * kKC / 8;  // 16-byte vectors per coefficient tile
+    auto prefetch = [&](int kc) {
+#pragma unroll
+      for (int j = 0; j < kKC / 8 / (kThreads / kM); ++j) {
+        const int kg = (t >> 7) + j * (kThreads / kM);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int d = kc * kKC + kg * 8 + i;
+          pa[j][i] = (row_ok && d < g.kd) ? __ldg(g.A + (size_t)d * g.lda + r) : 0.f;
+        }
+      }
+      const uint4* src = reinterpret_cast<const uint4*>(g.tiles + ((size_t)split * n_kc + kc) * NC * kKC);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = t + j * kThreads;
+        if (i < nb) pb[j] = __ldg(src + i);
+      }
+    };
+    prefetch(0);
     for (int kc = 0; kc < n_kc; ++kc) {
       const int st = kc & 1;
       wait_stage(st);  // the MMAs that read this stage two chunks ago are done
@@ -132,16 +160,14 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
       // A digits: thread -> (row, 8 consecutive diagrams); global reads are
       // coalesced over rows, shared stores are whole 16-byte core-matrix rows
       {
-        const int row = t & (kM - 1);
-        const int64_t r = row0 + row;
         const float sc = rscale[row];
-        for (int kg = t >> 7; kg < kKC / 8; kg += kThreads / kM) {
+#pragma unroll
+        for (int j = 0; j < kKC / 8 / (kThreads / kM); ++j) {
+          const int kg = (t >> 7) + j * (kThreads / kM);
           __align__(16) __half hv[8], mv[8], lv[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const int d = kc * kKC + kg * 8 + i;
-            float x = 0.f;
-            if (r < n_rows && d < g.kd) x = g.A[(size_t)d * g.lda + r] * sc;
+            const float x = pa[j][i] * sc;
             const float h = rintf(x);
             const float r1 = (x - h) * w1;
             const float mm = rintf(r1);
@@ -158,10 +184,14 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
       }
       // B: the precomputed canonical tile of coefficient integers
       {
-        const uint4* src = reinterpret_cast<const uint4*>(g.tiles + ((size_t)split * n_kc + kc) * NC * kKC);
         uint4* dst = reinterpret_cast<uint4*>(b_t);
-        for (int i = t; i < NC * kKC / 8; i += kThreads) dst[i] = __ldg(src + i);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int i = t + j * kThreads;
+          if (i < nb) dst[i] = pb[j];
+        }
       }
+      if (kc + 1 < n_kc) prefetch(kc + 1);
       fence_async_smem();
       fence_before();
       __syncthreads();
@@ -250,7 +280,7 @@ JampMap build_jamp_map(const Program& p) {
   M.kd = kd;
   if (!real || kd == 0 || M.m <= 0 || g == 0) return M;
   M.cfac = g;
-  M.nc = std::min(160, ((M.m + 15) / 16) * 16);
+  M.nc = std::min(kMaxNC, ((M.m + 15) / 16) * 16);
   M.n_splits = (M.m + M.nc - 1) / M.nc;
   // balance the splits: the smallest multiple of 16 that still needs n_splits
   M.nc = std::min(M.nc, (((M.m + M.n_splits - 1) / M.n_splits) + 15) / 16 * 16);
@@ -293,6 +323,7 @@ size_t jamp_gemm_smem(int nc) { return 2 * stage_bytes(nc) + 16 + 16 + (size_t)k
 
 cudaError_t launch_jamp_gemm(const JampGemmArgs& a, int num_sms, cudaStream_t s) {
   if (a.n_pairs <= 0) return cudaSuccess;
+  if (a.nc < 16 || a.nc > kMaxNC || a.nc % 16 != 0 || a.kpad % kKC != 0) return cudaErrorInvalidValue;
   const size_t sm = jamp_gemm_smem(a.nc);
   cudaError_t e = cudaFuncSetAttribute(jamp_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
