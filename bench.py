@@ -422,14 +422,18 @@ def main():
     sampler.start()
     ms_mixed, per_mixed, launches = timed(mea.PREC_MIXED, args.steps)
     clocks = sampler.stop()
+    # the clones run on torch's stream: finish them before the FP64 pass
+    # overwrites the outputs on the evaluation stream
     mixed_out = [o.clone() for o in outs]
     mixed_flags = [f.clone() for f in flags]
+    torch.cuda.synchronize()
 
     fp64 = None
     if not args.no_fp64:
         ms64, per64, _ = timed(mea.PREC_FP64, args.steps)
         fp64 = {"value": ws * n * len(procs) / (ms64 * 1e-3), "unit": "events/s", "ms_per_step": ms64}
     fp64_out = [o.clone() for o in outs]
+    torch.cuda.synchronize()
 
     per_sub = {}
     for i, (name, pdg, nf, lo, hi) in enumerate(subs):
@@ -466,7 +470,9 @@ def main():
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,
-                "kernel": f"amp_kernel<float> ({subs[dom][0]}, incl. FP64 re-evaluation launch)",
+                "kernel": (f"gen_kernel<float> straight-line body ({subs[dom][0]})" if len(subs[dom][1]) <= 5
+                           else f"amp_kernel<float> + jamp/colour GEMMs ({subs[dom][0]})") +
+                          ", per-launch CUDA events incl. the FP64 re-evaluation launch",
                 "peak_note": f"derived: {n_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x {MAX_SM_MHZ:.0f} MHz"}
 
     # end to end through the host-buffer entry point

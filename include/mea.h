@@ -86,12 +86,20 @@ typedef struct {
                             flagged in MEA_PREC_MIXED; <= 0 -> 1e-5 */
   int reeval_fp64;       /* 1: re-evaluate flagged events in FP64 (default) */
   int colour_mode;       /* 0 auto, 1 CUDA-core colour sum, 2 tensor-core GEMM */
+  int64_t chunk_events;  /* tensor-core path: events per chunk (bounds its device
+                            scratch, ~8 bytes per diagram per helicity per event);
+                            <= 0 -> automatic (enough lanes to fill the GPU) */
 } mea_options;
 
 /* Per-event flag bits written to flags_dev. */
 #define MEA_FLAG_REEVALUATED 0x01u  /* result comes from the FP64 re-evaluation */
 #define MEA_FLAG_NONFINITE   0x02u  /* a non-finite value was met */
 #define MEA_FLAG_CANCEL      0x04u  /* error indicator above flag_threshold */
+#define MEA_FLAG_QGUARD      0x08u  /* a propagator invariant |q^2| is below 1e-10 of the
+                                       squared energy flowing through it (near-singular
+                                       kinematics; re-evaluated in FP64 on the mixed path) */
+#define MEA_FLAG_MOMENTUM    0x10u  /* momentum conservation violated by more than
+                                       1e-9 sqrt(s) in some component (input check) */
 
 typedef struct {
   int n_ext;              /* external partons */

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
   const int L = blockDim.x;
   const int t = threadIdx.x;
   const int n_ext = P.n_ext, m = P.n_colour, H = C.H, E = C.E_cta;
-  const int tab_stride = 8 * n_ext + 5 * P.n_masks;
+  const int tab_stride = event_table_stride(n_ext, P.n_masks);
 
   size_t off = 0;
   R* slots;
@@ -99,6 +99,8 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
   double* res = reinterpret_cast<double*>(smem + off);
   off += (size_t)L * sizeof(double);
   float* kap = reinterpret_cast<float*>(smem + off);
+  unsigned int* evflag = reinterpret_cast<unsigned int*>(kap + L);  // [E] input-check bits
+  for (int i = t; i < E; i += L) evflag[i] = 0u;
 
   const bool listed = A.event_list != nullptr;
   const int64_t n = listed ? (int64_t)(*A.list_count) : A.n_events;
@@ -110,7 +112,8 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t ev0 = tile * E;
     // ---- phase 0: FP64 preparation
-    tile_prep<R>(P, A, tab, tab_stride, ev0, n, E, t, L);
+    __syncthreads();  // evflag cleared (first tile) / released by the previous finish
+    tile_prep<R>(P, A, tab, tab_stride, ev0, n, E, t, L, evflag);
     __syncthreads();
 
     // ---- phase 1: one (event, helicity) per lane
@@ -268,22 +271,6 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
         A.amp_rowmax[2 * pair] = finite_amps ? mx_re : nan;
         A.amp_rowmax[2 * pair + 1] = finite_amps ? mx_im : nan;
         A.pair_kappa[pair] = abs_mass;  // divided by sum |J| after the colour-amplitude stage
-      } else if (A.jamp_out) {
-        // split colour stage: hand the colour amplitudes to the tensor-core kernel
-        if constexpr (F32) {
-          const int64_t pair = ev * H + h;
-          float* jr = A.jamp_out + (size_t)(2 * pair) * A.ldj;
-          float* ji = jr + A.ldj;
-          float jabs = 0.f;
-          for (int a = 0; a < m; ++a) {
-            const R* ja = jam + (size_t)a * JW * L + t;
-            float ar = ja[0] + ja[2 * L], ai = ja[L] + ja[3 * L];
-            jr[a] = ar;
-            ji[a] = ai;
-            jabs += fabsf(ar) + fabsf(ai);
-          }
-          A.pair_kappa[pair] = (jabs > 0.f) ? abs_mass / jabs : 0.f;
-        }
       } else {
       // ---- colour sum: sum_ab J_a K_ab J_b^* / D
       R tot = (R)0;
@@ -316,7 +303,13 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
     __syncthreads();
 
     // ---- phase 2: helicity sum per event, fixed order
-    if (!A.jamp_out && !AOUT) tile_finish<F32>(A, t, E, H, ev0, n, listed, res, kap);
+    if (!AOUT) {
+      tile_finish<F32>(A, t, E, H, ev0, n, listed, res, kap, evflag);
+    } else if (t < E) {
+      // the helicity sum runs after the colour stages: hand over the input checks
+      if (ev0 + t < n) A.ev_flags[ev0 + t] = (uint8_t)evflag[t];
+      evflag[t] = 0u;
+    }
     __syncthreads();
   }
 }
@@ -326,9 +319,9 @@ size_t smem_bytes(const DevProgram& p, int threads, int E, bool jsmem, bool ssme
   const int JW = std::is_same<R, float>::value ? 4 : 2;
   size_t b = ssmem ? (size_t)p.n_slots * 8 * threads * sizeof(R) : 0;
   if (jsmem) b += (size_t)p.n_colour * JW * threads * sizeof(R);
-  b += (size_t)E * (8 * p.n_ext + 5 * p.n_masks) * sizeof(R);
+  b += (size_t)E * event_table_stride(p.n_ext, p.n_masks) * sizeof(R);
   b = (b + 7) & ~size_t(7);
-  b += (size_t)threads * (sizeof(double) + sizeof(float)) + 16;
+  b += (size_t)threads * (sizeof(double) + sizeof(float) + sizeof(unsigned int)) + 16;
   return b;
 }
 
@@ -354,12 +347,12 @@ __global__ void finish_kernel(const AmpLaunch A, int H, const double* pairval, c
   }
   double me = 0.25 * s;
   A.me2[e] = me;
-  uint8_t fl = 0;
+  uint8_t fl = A.ev_flags ? A.ev_flags[e] : (uint8_t)0;
   if (!isfinite(me)) fl |= MEA_FLAG_NONFINITE;
   double ind = (s > 0.0) ? 5.96e-8 * wk / s : 0.0;
   if (!(ind <= (double)A.flag_threshold)) fl |= MEA_FLAG_CANCEL;
   if (A.flags) A.flags[e] = fl;
-  if (A.flag_list && (fl & (MEA_FLAG_CANCEL | MEA_FLAG_NONFINITE))) {
+  if (A.flag_list && (fl & (MEA_FLAG_CANCEL | MEA_FLAG_NONFINITE | MEA_FLAG_QGUARD))) {
     int slot = atomicAdd(A.flag_count, 1);
     A.flag_list[slot] = (int32_t)e;
   }
@@ -397,7 +390,7 @@ static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n
   best.jamp_in_smem = true;
   best.slots_in_smem = true;
   const void* k = fp64 ? p.gen->kernel_f64() : p.gen->kernel_f32();
-  const int tab_stride = 8 * p.n_ext + 5 * p.n_masks;
+  const int tab_stride = event_table_stride(p.n_ext, p.n_masks);
   cudaFuncAttributes fa;
   int max_threads = 256;
   if (cudaFuncGetAttributes(&fa, k) == cudaSuccess) max_threads = std::min(max_threads, fa.maxThreadsPerBlock);
@@ -405,7 +398,7 @@ static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n
   for (int E = 1; E * H <= max_threads; ++E) {
     int threads = ((E * H + 31) / 32) * 32;
     if (threads > max_threads) break;
-    size_t sm = (((size_t)E * tab_stride * (fp64 ? 8 : 4) + 7) & ~size_t(7)) + (size_t)threads * 12 + 16;
+    size_t sm = (((size_t)E * tab_stride * (fp64 ? 8 : 4) + 7) & ~size_t(7)) + (size_t)threads * 16 + 16;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, sm) != cudaSuccess) per_sm = 0;
     if (per_sm < 1) continue;  // this tile cannot be resident: skip it
@@ -419,7 +412,7 @@ static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n
   if (best_score < 0) {  // nothing resident at all: one warp per tile
     best.E_cta = std::max(1, 32 / std::max(H, 1));
     best.threads = ((best.E_cta * H + 31) / 32) * 32;
-    best.smem = (((size_t)best.E_cta * tab_stride * (fp64 ? 8 : 4) + 7) & ~size_t(7)) + (size_t)best.threads * 12 + 16;
+    best.smem = (((size_t)best.E_cta * tab_stride * (fp64 ? 8 : 4) + 7) & ~size_t(7)) + (size_t)best.threads * 16 + 16;
     best.grid = num_sms;
   }
   int64_t tiles = (n_events + best.E_cta - 1) / best.E_cta;
@@ -491,7 +484,7 @@ std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, 
     cudaFuncAttributes fa;
     int max_threads = 256;
     if (cudaFuncGetAttributes(&fa, k) == cudaSuccess) max_threads = std::min(max_threads, fa.maxThreadsPerBlock);
-    const int tab_stride = 8 * p.n_ext + 5 * p.n_masks;
+    const int tab_stride = event_table_stride(p.n_ext, p.n_masks);
     int last_threads = -1;
     for (int E = 1; E * H <= max_threads; ++E) {
       int threads = ((E * H + 31) / 32) * 32;
@@ -502,7 +495,7 @@ std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, 
       last_threads = threads;
       AmpConfig c;
       c.H = H; c.E_cta = E; c.threads = threads;
-      c.smem = (((size_t)E * tab_stride * (fp64 ? 8 : 4) + 7) & ~size_t(7)) + (size_t)threads * 12 + 16;
+      c.smem = (((size_t)E * tab_stride * (fp64 ? 8 : 4) + 7) & ~size_t(7)) + (size_t)threads * 16 + 16;
       int per_sm = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, c.smem) != cudaSuccess || per_sm < 1)
         continue;

@@ -94,13 +94,21 @@ bool use_tensor_colour(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode 
   return P->dev.gen == nullptr;
 }
 
-// Events per chunk of the tensor-core path: the diagram amplitudes of a chunk
-// (8 bytes per diagram and pair) stay below kAmpBudget.
-constexpr size_t kAmpBudget = size_t(3) << 30;
+// Events per chunk of the tensor-core path.  A chunk should hold enough
+// (event, helicity) lanes to fill every SM with the amplitude kernel
+// (kLanesPerSm), with its diagram amplitudes (8 bytes per diagram and pair)
+// between kAmpMin and kAmpMax bytes.
+constexpr size_t kAmpMin = size_t(1) << 30;
+constexpr size_t kAmpMax = size_t(10) << 30;
+constexpr int64_t kLanesPerSm = 2048;
 
 int64_t tc_chunk_events(const mea_process_s* P, int H, int64_t n) {
-  const size_t per_event = (size_t)H * 2 * (size_t)P->jmap.kd * sizeof(float);
-  return std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)(kAmpBudget / std::max<size_t>(per_event, 1))));
+  if (P->opts.chunk_events > 0) return std::max<int64_t>(1, std::min<int64_t>(n, P->opts.chunk_events));
+  const size_t per_pair = 2 * (size_t)P->jmap.kd * sizeof(float);
+  size_t bytes = (size_t)P->num_sms * kLanesPerSm * per_pair;
+  bytes = std::min(kAmpMax, std::max(kAmpMin, bytes));
+  const size_t per_event = (size_t)H * per_pair;
+  return std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)(bytes / std::max<size_t>(per_event, 1))));
 }
 
 // Launch configuration of the amplitude-output interpreter for H lanes per event.
@@ -132,6 +140,7 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
   MEA_CUDA(S.pairk.ensure(sizeof(float) * (size_t)H * chunk));
   MEA_CUDA(S.flag_list.ensure(sizeof(int32_t) * (size_t)chunk));
   MEA_CUDA(S.flag_count.ensure(sizeof(int32_t)));
+  MEA_CUDA(S.evf.ensure((size_t)chunk));
   mea::DevProgram dp = P->dev;
   dp.gen = nullptr;   // the interpreter writes the diagram amplitudes
   dp.n_colour = 0;    // and holds no colour accumulators
@@ -179,6 +188,7 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
     a.lda = lda;
     a.amp_rowmax = reinterpret_cast<float*>(S.rowmax.p);
     a.pair_kappa = reinterpret_cast<float*>(S.pairk.p);
+    a.ev_flags = reinterpret_cast<uint8_t*>(S.evf.p);
     MEA_CUDA(place_scratch(S.s32, dp, false, c, a));
     MEA_CUDA(mea::launch_amp(dp, false, c, a, s));
     jg.n_pairs = cn * H;
@@ -287,7 +297,7 @@ size_t scratch_estimate(mea_process_s* P, int64_t n, mea_prec_mode prec) {
     dp.n_colour = 0;
     return sizeof(float) * (size_t)P->jmap.kd * (size_t)lda + sizeof(float) * (size_t)H * chunk * (3 + P->jmap.n_splits) +
            sizeof(float) * 2 * (size_t)ldj * (size_t)H * chunk + sizeof(double) * (size_t)H * chunk +
-           (size_t)chunk * 4 + 4096 + work(dp, false, chunk) + work(P->dev, true, chunk);
+           (size_t)chunk * 5 + 4096 + work(dp, false, chunk) + work(P->dev, true, chunk);
   }
   size_t b = work(P->dev, fp64, n);
   if (!fp64 && P->opts.reeval_fp64) b += (size_t)n * 4 + 256 + work(P->dev, true, n);
@@ -310,11 +320,13 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
   P->opts.flag_threshold = 1e-5;
   P->opts.reeval_fp64 = 1;
   P->opts.colour_mode = 0;
+  P->opts.chunk_events = 0;
   if (opts) {
     if (opts->alpha_s > 0) P->opts.alpha_s = opts->alpha_s;
     if (opts->flag_threshold > 0) P->opts.flag_threshold = opts->flag_threshold;
     P->opts.reeval_fp64 = opts->reeval_fp64;
     P->opts.colour_mode = opts->colour_mode;
+    P->opts.chunk_events = opts->chunk_events;
   }
   try {
     P->prog = mea::build_program(std::vector<int>(pdg, pdg + n_ext));

@@ -64,7 +64,7 @@ mea_status mea_autotune(mea_process_t P, const double* mom, int64_t n, mea_prec_
   const int H = P->prog.n_hel;
   mea::DevProgram dp = P->dev;
   const bool tc = mea::uses_tensor_path(P, prec, MEA_HEL_SUM_NONZERO);
-  mea::DevBuf abuf, rowmax, pairk;
+  mea::DevBuf abuf, rowmax, pairk, evf;
   int64_t lda = 0;
   if (tc) {
     // the tensor-core path runs the amplitude-output interpreter: time that
@@ -75,8 +75,8 @@ mea_status mea_autotune(mea_process_t P, const double* mom, int64_t n, mea_prec_
     lda = ((2 * n * H + 127) / 128) * 128;
     if (abuf.ensure(sizeof(float) * (size_t)P->jmap.kd * (size_t)lda) != cudaSuccess ||
         rowmax.ensure(sizeof(float) * 2 * (size_t)H * n) != cudaSuccess ||
-        pairk.ensure(sizeof(float) * (size_t)H * n) != cudaSuccess) {
-      abuf.release(); rowmax.release(); pairk.release();
+        pairk.ensure(sizeof(float) * (size_t)H * n) != cudaSuccess || evf.ensure((size_t)n) != cudaSuccess) {
+      abuf.release(); rowmax.release(); pairk.release(); evf.release();
       return mea::set_error(MEA_E_NOMEM, "mea_autotune: no room for the amplitude sample");
     }
   }
@@ -105,6 +105,7 @@ mea_status mea_autotune(mea_process_t P, const double* mom, int64_t n, mea_prec_
       a.lda = lda;
       a.amp_rowmax = reinterpret_cast<float*>(rowmax.p);
       a.pair_kappa = reinterpret_cast<float*>(pairk.p);
+      a.ev_flags = reinterpret_cast<uint8_t*>(evf.p);
     }
     size_t jb = (mea::jamp_scratch_bytes_needed(dp, fp64, c) + 255) & ~size_t(255);
     size_t sb = mea::slot_scratch_bytes_needed(dp, fp64, c);
@@ -129,6 +130,7 @@ mea_status mea_autotune(mea_process_t P, const double* mom, int64_t n, mea_prec_
   abuf.release();
   rowmax.release();
   pairk.release();
+  evf.release();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamDestroy(s);

@@ -14,8 +14,10 @@
 //     tensor core's FP32 accumulation is biased over long sums (measured: a
 //     systematic 2e-6 relative shift of |M|^2 at m = 720 when one accumulator
 //     spans all of K), so each chunk's partial Z is read out (tcgen05.ld) and
-//     sum_a J_a Z_a is accumulated across chunks in FP64 against the unscaled
-//     FP32 J, after which the row scale is undone.
+//     sum_a J_a Z_a is accumulated across chunks against the unscaled FP32 J
+//     with the compensated dot product Dot2 in FP32 (twice the working
+//     precision; the FP64 pipe of this part is 64 times slower), after which
+//     the row scale is undone.
 // Operands are staged in shared memory in the canonical no-swizzle K-major
 // layout (8-row x 16-byte core matrices).  Every wait is bounded: on expiry
 // the kernel records an error in *status, drains its own MMAs with a bounded
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
       if (mx > 0.f && isfinite(mx)) { frexpf(mx, &e); }
       rscale[t] = ldexpf(1.f, max(-120, min(120, 14 - e)));
     }
-    double acc_row = 0.0;  // this thread's row: sum_a J_a Z_a (scaled)
+    float acc_hi = 0.f, acc_lo = 0.f;  // this thread's row: sum_a J_a Z_a (scaled), compensated
     for (int n0 = 0; n0 < g.np; n0 += NC) {
       for (int k0 = 0; k0 < g.kp; k0 += kKC) {
         __syncthreads();  // previous MMAs and epilogue reads are done before overwriting
@@ -170,7 +172,17 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
               const float* jr = g.J + r * ldj + n0 + c0;
 #pragma unroll
               for (int i = 0; i < 16; ++i)
-                if (n0 + c0 + i < m) acc_row += (double)jr[i] * (double)z[i];
+                if (n0 + c0 + i < m) {
+                  // Dot2 (Ogita, Rump, Oishi 2005): exact product error by FMA,
+                  // two-sum of the running value, errors collected in acc_lo
+                  const float p = __fmul_rn(jr[i], z[i]);
+                  const float pe = fmaf(jr[i], z[i], -p);
+                  const float s = __fadd_rn(acc_hi, p);
+                  const float bb = __fsub_rn(s, acc_hi);
+                  const float se = __fadd_rn(__fsub_rn(acc_hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+                  acc_hi = s;
+                  acc_lo = __fadd_rn(acc_lo, __fadd_rn(se, pe));
+                }
             }
           }
         }
@@ -182,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
     // row value = (J . Z) / scale ; pair value = (re row + im row) / D
     {
       double* rowval = rowbuf;
-      rowval[t] = acc_row / (double)rscale[t];
+      rowval[t] = ((double)acc_hi + (double)acc_lo) / (double)rscale[t];
       __syncthreads();
       if (t < kM / 2) {
         int64_t p = tile * (kM / 2) + t;

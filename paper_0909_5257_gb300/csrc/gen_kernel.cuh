@@ -72,12 +72,14 @@ __global__ void __launch_bounds__(kGenMaxThreads) gen_kernel(const DevProgram P,
   const int L = blockDim.x;
   const int t = threadIdx.x;
   const int n_ext = P.n_ext, H = C.H, E = C.E_cta;
-  const int tab_stride = 8 * n_ext + 5 * P.n_masks;
+  const int tab_stride = event_table_stride(n_ext, P.n_masks);
   R* tab = reinterpret_cast<R*>(smem);
   size_t off = ((size_t)E * tab_stride * sizeof(R) + 7) & ~size_t(7);
   double* res = reinterpret_cast<double*>(smem + off);
   off += (size_t)L * sizeof(double);
   float* kap = reinterpret_cast<float*>(smem + off);
+  unsigned int* evflag = reinterpret_cast<unsigned int*>(kap + L);  // [E] input-check bits
+  for (int i = t; i < E; i += L) evflag[i] = 0u;
 
   const bool listed = A.event_list != nullptr;
   const int64_t n = listed ? (int64_t)(*A.list_count) : A.n_events;
@@ -87,7 +89,8 @@ __global__ void __launch_bounds__(kGenMaxThreads) gen_kernel(const DevProgram P,
 
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t ev0 = tile * E;
-    tile_prep<R>(P, A, tab, tab_stride, ev0, n, E, t, L);
+    __syncthreads();  // evflag cleared (first tile) / released by the previous finish
+    tile_prep<R>(P, A, tab, tab_stride, ev0, n, E, t, L, evflag);
     __syncthreads();
     const int e = t / H, h = t - (t / H) * H;
     const int64_t ev = ev0 + e;
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(kGenMaxThreads) gen_kernel(const DevProgram P,
     res[t] = val;
     kap[t] = kappa;
     __syncthreads();
-    tile_finish<F32>(A, t, E, H, ev0, n, listed, res, kap);
+    tile_finish<F32>(A, t, E, H, ev0, n, listed, res, kap, evflag);
     __syncthreads();
   }
 }

@@ -14,11 +14,11 @@
 // every partial sum is an integer below sum_d |n_{alpha d}| 2^q < 2^24, so the
 // accumulation is exact whatever order or internal rounding the tensor core
 // uses.  The epilogue recombines cfac * 2^(e_r - q) (H + M 2^-(q+1) +
-// L 2^-2(q+1)) in FP64 and rounds once to FP32.  The only error left is the
-// digit truncation, below 2^-(3q+3) of the row maximum: the colour amplitudes
-// come out as the correctly rounded FP32 sum of the FP32 diagram amplitudes
-// (the compensated summation of the paper's Sec. 3.2 step 3 with nothing left
-// to compensate).
+// L 2^-2(q+1)) with two FP32 FMAs (within an ulp of the exact value).  The
+// only other error is the digit truncation, below 2^-(3q+3) of the row
+// maximum: the colour amplitudes come out as the FP32-rounded exact sum of the
+// FP32 diagram amplitudes (the compensated summation of the paper's Sec. 3.2
+// step 3 with nothing left to compensate).
 //
 // Tile: 128 rows (64 pairs) x nc colour columns, K in chunks of 64 diagrams,
 // two shared-memory stages so that the digit conversion of chunk k+1 overlaps
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
   const int n_kc = g.kpad / kKC;
   const uint32_t idesc = make_idesc(kM, NC);
   const float w1 = ldexpf(1.f, g.q + 1);  // digit base
-  const double inv_w1 = 1.0 / (double)w1, inv_w2 = inv_w1 * inv_w1;
+  const float inv_w1 = 1.f / w1, inv_w2 = inv_w1 * inv_w1;  // powers of two
 
   auto wait_stage = [&](int st) {
     if (outstanding[st] == 0) return;
@@ -167,11 +167,11 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
           __align__(16) __half hv[8], mv[8], lv[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const float x = pa[j][i] * sc;
+            const float x = __fmul_rn(pa[j][i], sc);
             const float h = rintf(x);
-            const float r1 = (x - h) * w1;
+            const float r1 = __fmul_rn(__fsub_rn(x, h), w1);
             const float mm = rintf(r1);
-            const float l = rintf((r1 - mm) * w1);
+            const float l = rintf(__fmul_rn(__fsub_rn(r1, mm), w1));
             hv[i] = __float2half_rn(h);
             mv[i] = __float2half_rn(mm);
             lv[i] = __float2half_rn(l);
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
     fence_after();
     if (warp < 4 && !*abort_flag) {
       const int64_t r = row0 + t;
-      const double back = g.cfac / (double)rscale[t];
+      const float back = (float)g.cfac / rscale[t];  // cfac (1 or 2) times a power of two
       const uint32_t lane = (uint32_t)(warp * 32) << 16;
       float* jrow = g.J + (size_t)r * g.ldj;
       float sabs = 0.f;
@@ -233,7 +233,9 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
           for (int i = 0; i < 16; ++i) {
             const int a = n0 + c0 + i;
             if (a < g.m) {
-              const float v = (float)(((double)vh[i] + (double)vm[i] * inv_w1 + (double)vl[i] * inv_w2) * back);
+              // h + m/2^(q+1) + l/2^2(q+1): the inner FMA is exact up to one rounding and the
+              // l term lies below the last digit of m, so v is within an ulp of the exact sum
+              const float v = fmaf(vl[i], inv_w2, fmaf(vm[i], inv_w1, vh[i])) * back;
               jrow[a] = v;
               sabs += fabsf(v);
             }

@@ -59,9 +59,9 @@ struct AmpLaunch {
   int32_t* flag_list = nullptr;       // mixed path: indices of flagged events are appended here
   int32_t* flag_count = nullptr;
   double* pair_out = nullptr;         // optional [event][H] per-helicity values (tests)
-  float* jamp_out = nullptr;          // split colour stage: write J rows [2*pair][ldj] (FP32) and
-  float* pair_kappa = nullptr;        //   the per-pair indicator instead of the colour sum
-  int ldj = 0;
+  float* pair_kappa = nullptr;        // per-pair indicator (see amp_out)
+  uint8_t* ev_flags = nullptr;        // amplitude-output mode: per-event input-check bits out;
+                                      //   finish_kernel ORs them into the flags
   float* amp_out = nullptr;           // amplitude-output mode: A[d][lda], (Re, Im) of pair p at 2p, 2p+1;
   int64_t lda = 0;                    //   pair_kappa then receives sum_d w_d |A_d| and
   float* amp_rowmax = nullptr;        //   amp_rowmax[2p], [2p+1] the row maxima of |Re A|, |Im A|

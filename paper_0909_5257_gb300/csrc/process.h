@@ -37,10 +37,11 @@ struct DevBuf {
 // Scratch of one in-flight evaluation.  Evaluations that may overlap on the
 // GPU (different streams, graph branches, server slots) use distinct sets.
 struct EvalScratch {
-  DevBuf s32, s64, flag_list, flag_count, jbuf, pairval, pairk, abuf, rowmax, jabs;
+  DevBuf s32, s64, flag_list, flag_count, jbuf, pairval, pairk, abuf, rowmax, jabs, evf;
   void release() {
     s32.release(); s64.release(); flag_list.release(); flag_count.release();
     jbuf.release(); pairval.release(); pairk.release(); abuf.release(); rowmax.release(); jabs.release();
+    evf.release();
   }
 };
 

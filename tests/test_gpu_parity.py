@@ -28,6 +28,14 @@ CASES = [
     ("uu>uuggg", [2, 2, 2, 2, 21, 21, 21], (500.0, 5000.0), 37),
     ("uu~>ggggg", [2, -2] + [21] * 5, (500.0, 5000.0), 23),
     ("gg>ggggg", [21] * 7, (500.0, 5000.0), 5),
+    # crossings and other flavours through the same generator (no emitted
+    # kernels: these run the interpreter / tensor-core path)
+    ("ug>ug", [2, 21, 2, 21], (200.0, 2000.0), 2051),
+    ("gu>ugg", [21, 2, 2, 21, 21], (200.0, 2000.0), 1037),
+    ("ud>udg", [2, 1, 2, 1, 21], (200.0, 2000.0), 1037),
+    ("uu~>dd~g", [2, -2, 1, -1, 21], (200.0, 2000.0), 1037),
+    ("uu~>uu~g", [2, -2, 2, -2, 21], (200.0, 2000.0), 1037),
+    ("d~d~>d~d~g", [-1, -1, -1, -1, 21], (200.0, 2000.0), 1037),
 ]
 
 _ref_cache = {}
@@ -267,15 +275,17 @@ def test_tensor_core_colour_stage_default_for_large_bases(name):
     assert np.max(np.abs(tc / cc - 1.0)) <= 1e-4
 
 
-@pytest.mark.parametrize("pdg,nf,lo,hi,n", [([21] * 7, 5, 500.0, 5000.0, 1001),
-                                            ([2, -2, 21, 21, 21, 21, 21], 5, 500.0, 5000.0, 4999)])
-def test_tensor_path_several_chunks_against_fp64(pdg, nf, lo, hi, n):
-    """The tensor-core path splits large requests into event chunks (diagram
-    amplitudes of a chunk below a few GB): gg>5g at 1001 events and uu~>5g at
-    4999 events span several chunks with a ragged last one.  Every event
-    agrees with the GPU FP64 path (itself pinned to the oracle at 1e-12)."""
+@pytest.mark.parametrize("pdg,nf,lo,hi,n,chunk", [([21] * 7, 5, 500.0, 5000.0, 1001, 400),
+                                                  ([2, -2, 21, 21, 21, 21, 21], 5, 500.0, 5000.0, 4999, 2000),
+                                                  ([21] * 6, 4, 300.0, 3000.0, 20011, 0)])
+def test_tensor_path_several_chunks_against_fp64(pdg, nf, lo, hi, n, chunk):
+    """The tensor-core path splits large requests into event chunks that bound
+    its scratch: gg>5g at 1001 events in chunks of 400 and uu~>5g at 4999 in
+    chunks of 2000 (ragged last chunks), gg>4g at 20011 events with the
+    automatic chunk size.  Every event agrees with the GPU FP64 path (itself
+    pinned to the oracle at 1e-12)."""
     mea = _mea()
-    P = _proc(pdg)
+    P = _proc(pdg, chunk_events=chunk)
     d_mom = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
     mea.generate_phase_space(nf, n, d_mom, seed=ps.SEED_BASE + 211, rs_lo=lo, rs_hi=hi)
     mixed = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
@@ -287,3 +297,56 @@ def test_tensor_path_several_chunks_against_fp64(pdg, nf, lo, hi, n):
     assert np.all(np.isfinite(rel))
     assert np.median(rel) <= 1e-6, np.median(rel)
     assert rel.max() <= 1e-4, rel.max()
+
+
+def _collinear_event(n_final, delta, rs_scale=1000.0):
+    """A massless event with final partons 0 and 1 at an angle delta (their
+    invariant ~ a b delta^2), the others spread out, the last one balancing
+    the spatial momentum; the incoming pair along z carries the total energy."""
+    rng = np.random.default_rng(5)
+    fin = []
+    a, b = 0.3 * rs_scale, 0.2 * rs_scale
+    n1 = np.array([np.sin(0.7), 0.0, np.cos(0.7)])
+    n2 = np.array([np.sin(0.7 + delta), 0.0, np.cos(0.7 + delta)])
+    fin.append(np.concatenate([[a], a * n1]))
+    fin.append(np.concatenate([[b], b * n2]))
+    for k in range(n_final - 3):
+        th, ph = rng.uniform(1.0, 2.0), rng.uniform(0, 2 * np.pi)
+        e = rs_scale * rng.uniform(0.1, 0.3)
+        fin.append(np.array([e, e * np.sin(th) * np.cos(ph), e * np.sin(th) * np.sin(ph), e * np.cos(th)]))
+    tot = np.sum(fin, axis=0)
+    last = -tot[1:]
+    fin.append(np.concatenate([[np.linalg.norm(last)], last]))
+    rs = sum(f[0] for f in fin)
+    pin = [np.array([rs / 2, 0, 0, rs / 2]), np.array([rs / 2, 0, 0, -rs / 2])]
+    return np.array(pin + fin)
+
+
+@pytest.mark.parametrize("pdg", [[21] * 5, [21] * 6])
+def test_input_check_flags(pdg):
+    """MEA_FLAG_MOMENTUM marks an event whose momenta do not balance (1e-6
+    sqrt(s) added to one component); MEA_FLAG_QGUARD marks an event with two
+    final partons 1e-7 rad apart (invariant ~1e-15 of the energy squared):
+    on the mixed path it is re-evaluated in FP64 and agrees with the FP64 path;
+    ordinary events carry neither bit.  Straight-line kernel (gg>ggg) and
+    tensor-core path (gg>gggg)."""
+    mea = _mea()
+    nf = len(pdg) - 2
+    good = ps.generate(ps.PhaseSpaceConfig(nf, rs_lo=300.0, rs_hi=3000.0, seed=ps.SEED_BASE + 307), 64)
+    mom = good.copy()
+    rs = np.sqrt((mom[5, 0, 0] + mom[5, 1, 0]) ** 2 - (mom[5, 0, 3] + mom[5, 1, 3]) ** 2)
+    mom[5, 2, 1] += 1e-6 * rs
+    mom[9] = _collinear_event(nf, 1e-7)
+    out = {}
+    for prec in (mea.PREC_MIXED, mea.PREC_FP64):
+        got, fl = _run(pdg, mom, prec)
+        out[prec] = (got, fl)
+        assert fl[5] & 0x10 and not fl[5] & 0x08
+        assert fl[9] & 0x08 and not fl[9] & 0x10
+        others = np.delete(fl, [5, 9])
+        assert not np.any(others & 0x18)
+    gm, fm = out[mea.PREC_MIXED]
+    g64, _ = out[mea.PREC_FP64]
+    assert fm[9] & 0x01  # re-evaluated in FP64
+    assert np.isfinite(g64[9]) and g64[9] > 0
+    assert gm[9] == g64[9]
