@@ -343,6 +343,7 @@ def main():
     ap.add_argument("--ref-events", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -387,6 +388,15 @@ def main():
         outs.append(torch.empty(n, dtype=torch.float64, device="cuda"))
         flags.append(torch.empty(n, dtype=torch.uint8, device="cuda"))
     torch.cuda.synchronize()
+    # one-time tile / register-variant choice per subprocess and precision
+    # (mea_autotune on a 2^16-event sample), outside the timed region
+    tuned = {}
+    if not args.no_autotune:
+        for (name, *_), P, m, o in zip(subs, procs, moms, outs):
+            k = min(n, 1 << 16)
+            tuned[name] = {pn: P.autotune(m[:k], o[:k], precision=pr)
+                           for pr, pn in ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64"))}
+        torch.cuda.synchronize()
 
     def step(prec, ev_pairs=None):
         for i, P in enumerate(procs):
@@ -511,7 +521,9 @@ def main():
         "dtype": "f32 amplitudes (two-sum colour amplitudes) + f64 prep/re-evaluation",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload], "events_per_subprocess_per_gpu": n,
-                   "l2": "inputs larger than L2 (no flush)", "alpha_s": 0.118},
+                   "l2": "inputs larger than L2 (no flush)", "alpha_s": 0.118,
+                   "autotuned": {k: {pn: {kk: v[pn][kk] for kk in ("threads", "events_per_cta", "register_cap")}
+                                     for pn in v} for k, v in tuned.items()}},
         "per_subprocess": per_sub,
         "fp64": fp64,
         "roofline": roofline,

@@ -89,6 +89,10 @@ typedef struct {
   int64_t chunk_events;  /* tensor-core path: events per chunk (bounds its device
                             scratch, ~8 bytes per diagram per helicity per event);
                             <= 0 -> automatic (enough lanes to fill the GPU) */
+  int auto_tune;         /* 1 (default): the first mea_evaluate of >= 65536 events per
+                            precision with MEA_HEL_SUM_NONZERO, outside stream capture,
+                            synchronises its stream and runs mea_autotune on those
+                            events (me2 as scratch) before evaluating; 0: off */
 } mea_options;
 
 /* Per-event flag bits written to flags_dev. */
@@ -189,6 +193,8 @@ typedef struct {
   int candidates;        /* configurations timed */
   double best_ms;        /* time of the chosen configuration on the sample */
   double default_ms;     /* time of the heuristic default on the sample */
+  int register_cap;      /* straight-line kernels: registers per thread of the
+                            chosen variant (128 or 85); 0 for the interpreter */
 } mea_tune_result;
 
 mea_status mea_autotune(mea_process_t proc, const double *momenta_dev, int64_t n_sample,

@@ -221,9 +221,30 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
   return MEA_OK;
 }
 
+// Tuning on first use: the first evaluation of at least kAutoTuneMin events
+// with the non-zero helicity sum (outside stream capture) waits for its
+// stream, times the candidate tiles on its first kAutoTuneMin events with me2
+// as scratch (mea_autotune), and then evaluates with the chosen tile.  The
+// choice never changes a result: per-event arithmetic does not depend on it.
+constexpr int64_t kAutoTuneMin = 1 << 16;
+
+void maybe_autotune(mea_process_s* P, const double* mom, int64_t n, mea_hel_mode hm, mea_prec_mode prec,
+                    double* me2, cudaStream_t s) {
+  const int ti = prec == MEA_PREC_FP64 ? 1 : 0;
+  if (!P->opts.auto_tune || P->auto_tuned[ti] || n < kAutoTuneMin || hm != MEA_HEL_SUM_NONZERO) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+  P->auto_tuned[ti] = true;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return;  // the error resurfaces at the evaluation's own launches
+  const std::string keep = g_err;
+  mea_tune_result r;
+  if (mea::autotune_locked(P, mom, kAutoTuneMin, prec, me2, &r) != MEA_OK) g_err = keep;  // keep the heuristic
+}
+
 mea_status do_evaluate(mea_process_s* P, mea::EvalScratch& S, const double* mom, int64_t n, mea_hel_mode hm,
                        const int8_t* hel, mea_prec_mode prec, double* me2, uint8_t* flags,
                        cudaStream_t s) {
+  maybe_autotune(P, mom, n, hm, prec, me2, s);
   if (use_tensor_colour(P, prec, hm)) return do_evaluate_tc(P, S, mom, n, hm, me2, flags, s);
   const mea::Program& G = P->prog;
   int H = (hm == MEA_HEL_SUM_NONZERO) ? G.n_hel : (hm == MEA_HEL_SUM_ALL ? (1 << G.n_ext) : 1);
@@ -321,12 +342,14 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
   P->opts.reeval_fp64 = 1;
   P->opts.colour_mode = 0;
   P->opts.chunk_events = 0;
+  P->opts.auto_tune = 1;
   if (opts) {
     if (opts->alpha_s > 0) P->opts.alpha_s = opts->alpha_s;
     if (opts->flag_threshold > 0) P->opts.flag_threshold = opts->flag_threshold;
     P->opts.reeval_fp64 = opts->reeval_fp64;
     P->opts.colour_mode = opts->colour_mode;
     P->opts.chunk_events = opts->chunk_events;
+    P->opts.auto_tune = opts->auto_tune;
   }
   try {
     P->prog = mea::build_program(std::vector<int>(pdg, pdg + n_ext));

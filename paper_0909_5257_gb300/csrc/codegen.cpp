@@ -196,8 +196,7 @@ int main(int argc, char** argv) {
   o << "const GenEntry* generated_table(int* n) {\n  static const GenEntry t[] = {\n";
   for (auto& e : entries)
     o << "    {\"" << e.first << "\", &gen_launch<Body_" << e.second << "<float>, Body_" << e.second
-      << "<double>>, &gen_kernel_ptr<Body_" << e.second << "<float>, float>, &gen_kernel_ptr<Body_" << e.second
-      << "<double>, double>},\n";
+      << "<double>>, &gen_kernel_for<Body_" << e.second << "<float>, Body_" << e.second << "<double>>},\n";
   o << "  };\n  *n = " << entries.size() << ";\n  return t;\n}\n\n}  // namespace mea\n";
   FILE* f = std::fopen(argv[1], "w");
   if (!f) return 1;

@@ -64,9 +64,18 @@ __device__ __forceinline__ cx<R> jfin(cx<R> hi, cx<R> lo) {
   return hi;
 }
 
-template <typename R, typename Body>
-__global__ void __launch_bounds__(kGenMaxThreads) gen_kernel(const DevProgram P, const AmpLaunch A,
-                                                             const AmpConfig C) {
+// Register-cap variants: MINB resident CTAs of kGenMaxThreads per SM caps a
+// thread at 65536 / (256 MINB) registers.  Spilling part of the long
+// straight-line body to L1 in exchange for two or three times the resident
+// warps wins for the 3-jet bodies (measured on 2^20 events: gg>ggg 14.4 ms at
+// 255 registers, 11.3 ms at 128; uu>uug 2.6 ms at 128, 2.25 ms at 85), so the
+// FP32 bodies come in a 128- and an 85-register variant (the autotuner picks)
+// and the FP64 bodies in the 128-register one.  A module that also held
+// uncapped FP32 variants measured 25-45 % slower on the same 128-register
+// kernel, so none is built.
+template <typename R, typename Body, int MINB>
+__global__ void __launch_bounds__(kGenMaxThreads, MINB) gen_kernel(const DevProgram P, const AmpLaunch A,
+                                                                   const AmpConfig C) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr bool F32 = std::is_same<R, float>::value;
   const int L = blockDim.x;
@@ -119,20 +128,26 @@ __global__ void __launch_bounds__(kGenMaxThreads) gen_kernel(const DevProgram P,
   }
 }
 
-template <typename BodyF, typename BodyD>
-void gen_launch(bool fp64, const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
-  if (fp64) {
-    cudaFuncSetAttribute(gen_kernel<double, BodyD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-    gen_kernel<double, BodyD><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
-  } else {
-    cudaFuncSetAttribute(gen_kernel<float, BodyF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-    gen_kernel<float, BodyF><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
-  }
+template <typename R, typename Body, int MINB>
+void gen_launch_v(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
+  cudaFuncSetAttribute(gen_kernel<R, Body, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  cudaFuncSetAttribute(gen_kernel<R, Body, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_percent(c));
+  gen_kernel<R, Body, MINB><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
 }
 
-template <typename Body, typename R>
-const void* gen_kernel_ptr() {
-  return reinterpret_cast<const void*>(gen_kernel<R, Body>);
+// regvar 0: 128 registers (MINB 2), 1: 85 registers (MINB 3); FP64: MINB 2.
+template <typename BodyF, typename BodyD>
+void gen_launch(bool fp64, int regvar, const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
+  if (fp64) gen_launch_v<double, BodyD, 2>(p, c, a, s);
+  else if (regvar == 1) gen_launch_v<float, BodyF, 3>(p, c, a, s);
+  else gen_launch_v<float, BodyF, 2>(p, c, a, s);
+}
+
+template <typename BodyF, typename BodyD>
+const void* gen_kernel_for(bool fp64, int regvar) {
+  if (fp64) return reinterpret_cast<const void*>(gen_kernel<double, BodyD, 2>);
+  if (regvar == 1) return reinterpret_cast<const void*>(gen_kernel<float, BodyF, 3>);
+  return reinterpret_cast<const void*>(gen_kernel<float, BodyF, 2>);
 }
 
 }  // namespace

@@ -16,10 +16,12 @@ struct AmpLaunch;
 // A straight-line per-process kernel emitted by codegen.cpp at build time.
 struct GenEntry {
   const char* key;  // PDG codes joined by commas
-  void (*launch)(bool fp64, const DevProgram&, const AmpConfig&, const AmpLaunch&, cudaStream_t);
-  const void* (*kernel_f32)();
-  const void* (*kernel_f64)();
+  // regvar: register-cap variant of the FP32 kernel (0: 128, 1: 85
+  // registers per thread); the FP64 kernel has one variant (128)
+  void (*launch)(bool fp64, int regvar, const DevProgram&, const AmpConfig&, const AmpLaunch&, cudaStream_t);
+  const void* (*kernel)(bool fp64, int regvar);
 };
+constexpr int kGenRegVariants = 2;
 const GenEntry* generated_table(int* n);
 const GenEntry* find_generated(const int* pdg, int n_ext);
 
@@ -77,7 +79,15 @@ struct AmpConfig {
   size_t smem = 0;
   bool jamp_in_smem = true;
   bool slots_in_smem = true;
+  int regvar = 0;  // straight-line kernels: register-cap variant (see GenEntry)
+  int per_sm = 1;  // CTAs meant to be resident per SM (sets the shared-memory carveout)
 };
+
+// Shared-memory carveout (percent of the SM's unified L1/shared storage) that
+// holds per_sm CTAs of smem bytes each and leaves the rest as L1: the
+// straight-line kernels spill and the interpreter keeps wavefunction slots in
+// global memory, both of which live in L1.
+int carveout_percent(const AmpConfig& c);
 
 // Choose tile shape and grid for a program, precision and helicity mode.
 AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms,

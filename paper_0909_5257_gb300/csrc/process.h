@@ -63,6 +63,7 @@ struct mea_process_s {
   // configurations chosen by mea_autotune, per precision (0 mixed, 1 FP64), or grid 0
   mea::AmpConfig tuned[2];
   int tuned_H[2] = {0, 0};
+  bool auto_tuned[2] = {false, false};  // tuned once already (explicitly or on first large evaluation)
   // tensor-core colour stage: fp16(K) and K - fp16(K) (null when exact), status word
   const __half* cf_hi = nullptr;
   const __half* cf_lo = nullptr;
@@ -88,6 +89,9 @@ mea_status evaluate_with(mea_process_s* P, EvalScratch& S, const double* mom, in
 // True when evaluations of this precision / helicity mode run the tensor-core
 // path (amplitude-output interpreter + colour-amplitude and colour GEMMs).
 bool uses_tensor_path(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode hm);
+// mea_autotune with the process lock already held.
+mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_prec_mode prec, double* me2,
+                           mea_tune_result* out);
 // Device scratch bytes an evaluation of n events would hold (admission control).
 size_t scratch_estimate(mea_process_s* P, int64_t n, mea_prec_mode prec);
 }  // namespace mea

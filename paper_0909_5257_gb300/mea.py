@@ -36,7 +36,8 @@ class MeaError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("alpha_s", ctypes.c_double), ("flag_threshold", ctypes.c_double),
-                ("reeval_fp64", ctypes.c_int), ("colour_mode", ctypes.c_int), ("chunk_events", ctypes.c_int64)]
+                ("reeval_fp64", ctypes.c_int), ("colour_mode", ctypes.c_int), ("chunk_events", ctypes.c_int64),
+                ("auto_tune", ctypes.c_int)]
 
 
 class ProcessInfo(ctypes.Structure):
@@ -50,7 +51,8 @@ class ProcessInfo(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("events_per_cta", ctypes.c_int), ("grid", ctypes.c_int),
                 ("colour_amps_in_shared", ctypes.c_int), ("slots_in_shared", ctypes.c_int),
-                ("candidates", ctypes.c_int), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+                ("candidates", ctypes.c_int), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("register_cap", ctypes.c_int)]
 
 
 class BatchItem(ctypes.Structure):
@@ -154,12 +156,13 @@ class Process:
     """
 
     def __init__(self, pdg, alpha_s=0.118, flag_threshold=1e-5, reeval_fp64=True,
-                 colour_mode=0, host_only=False, chunk_events=0):
+                 colour_mode=0, host_only=False, chunk_events=0, auto_tune=True):
         lib = load()
         self.pdg = list(pdg)
         self.n_ext = len(self.pdg)
         arr = (ctypes.c_int * self.n_ext)(*self.pdg)
-        opts = Options(alpha_s, flag_threshold, 1 if reeval_fp64 else 0, colour_mode, chunk_events)
+        opts = Options(alpha_s, flag_threshold, 1 if reeval_fp64 else 0, colour_mode, chunk_events,
+                       1 if auto_tune else 0)
         h = ctypes.c_void_p()
         fn = lib.mea_create_process_host_only if host_only else lib.mea_create_process
         _check(fn(arr, self.n_ext, ctypes.byref(opts), ctypes.byref(h)))

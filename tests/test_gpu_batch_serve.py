@@ -61,10 +61,12 @@ def test_batch_graph_matches_individual_evaluations(prec):
     B.close()
 
 
-@pytest.mark.parametrize("pdg,nf,lo,hi", [([21] * 5, 3, 200.0, 2000.0), ([2, -2, 21, 21, 21, 21], 4, 300.0, 3000.0)])
+@pytest.mark.parametrize("pdg,nf,lo,hi", [([21] * 5, 3, 200.0, 2000.0), ([2, 2, 2, 2, 21], 3, 200.0, 2000.0),
+                                         ([2, -2, 21, 21, 21, 21], 4, 300.0, 3000.0)])
 def test_autotune_keeps_results(pdg, nf, lo, hi):
+    """Tile shape, placement and register-cap variant change no result bit."""
     mea = _mea()
-    P = mea.Process(pdg)
+    P = mea.Process(pdg, auto_tune=False)
     mom = _events(nf, 4096, lo, hi)
     ref = _alone(P, mom, mea.PREC_MIXED)
     scratch = torch.empty(2048, dtype=torch.float64, device="cuda")
@@ -127,3 +129,16 @@ def test_server_admission_rejects_and_times_out_without_hanging():
     with pytest.raises(mea.MeaError):
         srv.wait(12345, timeout_ms=10)
     srv.close()
+
+
+def test_autotune_on_first_use():
+    """The first evaluation of >= 2^16 events tunes the process once; the
+    results equal those of an untuned process bit for bit."""
+    mea = _mea()
+    mom = _events(3, 1 << 16, 200.0, 2000.0)
+    auto = mea.Process([2, 2, 2, 2, 21])
+    fixed = mea.Process([2, 2, 2, 2, 21], auto_tune=False)
+    a = _alone(auto, mom, mea.PREC_MIXED)
+    b = _alone(fixed, mom, mea.PREC_MIXED)
+    assert torch.equal(a, b)
+    assert torch.equal(_alone(auto, mom, mea.PREC_MIXED), b)
