@@ -546,6 +546,30 @@ mea_status mea_evaluate(mea_process_t P, const double* mom, int64_t n, mea_hel_m
   return do_evaluate(P, P->scr[0], mom, n, hm, hel, prec, me2, flags, reinterpret_cast<cudaStream_t>(stream));
 }
 
+}  // extern "C"
+
+namespace {
+// Host copy into / out of the pinned staging buffers, split over host threads
+// for large blocks (one core's memcpy bandwidth would bound the pipeline).
+void host_copy(void* dst, const void* src, size_t bytes) {
+  constexpr size_t kPerThread = size_t(4) << 20;
+  const int nt = (int)std::min<size_t>(16, bytes / kPerThread);
+  if (nt <= 1) {
+    std::memcpy(dst, src, bytes);
+    return;
+  }
+  const size_t part = ((bytes + nt - 1) / nt + 63) & ~size_t(63);
+#pragma omp parallel for num_threads(nt) schedule(static)
+  for (int i = 0; i < nt; ++i) {
+    const size_t b0 = (size_t)i * part;
+    if (b0 < bytes)
+      std::memcpy(static_cast<char*>(dst) + b0, static_cast<const char*>(src) + b0, std::min(part, bytes - b0));
+  }
+}
+}  // namespace
+
+extern "C" {
+
 mea_status mea_evaluate_host(mea_process_t P, const double* mom_h, int64_t n, mea_prec_mode prec,
                              double* me2_h, uint8_t* flags_h) {
   if (!P) return fail(MEA_E_ARG, "mea_evaluate_host: null process");
@@ -580,8 +604,8 @@ mea_status mea_evaluate_host(mea_process_t P, const double* mom_h, int64_t n, me
     MEA_CUDA(cudaEventSynchronize(P->done[b]));
     int64_t c0 = pending[b] * chunk;
     int64_t cn = std::min(chunk, n - c0);
-    std::memcpy(me2_h + c0, P->pin_out[b], sizeof(double) * cn);
-    if (flags_h) std::memcpy(flags_h + c0, P->pin_flags[b], cn);
+    host_copy(me2_h + c0, P->pin_out[b], sizeof(double) * cn);
+    if (flags_h) host_copy(flags_h + c0, P->pin_flags[b], cn);
     pending[b] = -1;
     return MEA_OK;
   };
@@ -590,7 +614,7 @@ mea_status mea_evaluate_host(mea_process_t P, const double* mom_h, int64_t n, me
     mea_status s = drain(b);
     if (s != MEA_OK) return s;
     int64_t c0 = k * chunk, cn = std::min(chunk, n - c0);
-    std::memcpy(P->pin_in[b], mom_h + (size_t)c0 * n_ext * 4, sizeof(double) * 4 * n_ext * cn);
+    host_copy(P->pin_in[b], mom_h + (size_t)c0 * n_ext * 4, sizeof(double) * 4 * n_ext * cn);
     MEA_CUDA(cudaMemcpyAsync(P->d_in[b].p, P->pin_in[b], sizeof(double) * 4 * n_ext * cn,
                              cudaMemcpyHostToDevice, P->st[b]));
     s = do_evaluate(P, P->scr[1 + b], reinterpret_cast<const double*>(P->d_in[b].p), cn, MEA_HEL_SUM_NONZERO, nullptr, prec,
