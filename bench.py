@@ -289,7 +289,7 @@ def run_serve(args):
     results = {}
     for prec, pname in ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64")):
         # capacity: back-to-back submission
-        srv = mea.Server(mem_budget_bytes=64 << 30, n_slots=4, chunk_events=1 << 12)
+        srv = mea.Server(mem_budget_bytes=160 << 30, n_slots=4, chunk_events=1 << 12)
         outs = [torch.empty(n, dtype=torch.float64, device="cuda") for _, _, n in reqs]
         t0 = time.perf_counter()
         ids = [srv.submit(procs[nm], m, o, precision=prec) for (nm, m, n), o in zip(reqs, outs)]
@@ -302,7 +302,7 @@ def run_serve(args):
         # Poisson arrivals at 0.8 x capacity
         mean_gap = (total / len(reqs)) / (0.8 * capacity)
         gaps = rng.exponential(mean_gap, size=len(reqs))
-        srv = mea.Server(mem_budget_bytes=64 << 30, n_slots=4, chunk_events=1 << 12)
+        srv = mea.Server(mem_budget_bytes=160 << 30, n_slots=4, chunk_events=1 << 12)
         t0 = time.perf_counter()
         ids = []
         tnext = t0

@@ -99,7 +99,7 @@ bool use_tensor_colour(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode 
 // (kLanesPerSm), with its diagram amplitudes (8 bytes per diagram and pair)
 // between kAmpMin and kAmpMax bytes.
 constexpr size_t kAmpMin = size_t(1) << 30;
-constexpr size_t kAmpMax = size_t(10) << 30;
+constexpr size_t kAmpMax = size_t(24) << 30;
 constexpr int64_t kLanesPerSm = 2048;
 
 int64_t tc_chunk_events(const mea_process_s* P, int H, int64_t n) {
@@ -163,11 +163,9 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
   mea::ColourGemmArgs cg;
   cg.m = m;
   cg.ldj = ldj;
-  cg.nc = std::min(256, ((m + 15) / 16) * 16);
-  cg.np = ((m + cg.nc - 1) / cg.nc) * cg.nc;
-  cg.kp = ((m + 63) / 64) * 64;
-  cg.tmem_cols = 32;
-  while (cg.tmem_cols < cg.nc) cg.tmem_cols *= 2;
+  cg.nc = P->cf_nc;
+  cg.np = P->cf_np;
+  cg.kp = P->cf_kp;
   cg.b_hi = P->cf_hi;
   cg.b_lo = P->cf_lo;
   cg.inv_den = P->dev.cf_inv_den;
@@ -416,25 +414,22 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
   D.g = std::sqrt(4.0 * M_PI * P->opts.alpha_s);
   D.gen = (P->opts.colour_mode == 2) ? nullptr : mea::find_generated(pdg, n_ext);
   {
-    std::vector<__half> hi(G.cf_jamp.size()), lo(G.cf_jamp.size());
-    bool exact = true;
-    for (size_t i = 0; i < G.cf_jamp.size(); ++i) {
-      hi[i] = __float2half_rn((float)G.cf_jamp[i]);
-      double r = (double)G.cf_jamp[i] - (double)__half2float(hi[i]);
-      lo[i] = __float2half_rn((float)r);
-      if (r != 0.0) exact = false;
-    }
+    // colour matrix as tensor-core operand tiles, and the status word
+    mea::ColourTiles T = mea::build_colour_tiles(G.cf_jamp, G.n_jamp);
     const __half* dh = nullptr;
     const __half* dl = nullptr;
     std::vector<int> st(1, 0);
     const int* dst = nullptr;
-    if ((e = upload(P, hi, &dh)) != cudaSuccess || (!exact && (e = upload(P, lo, &dl)) != cudaSuccess) ||
+    if ((e = upload(P, T.hi, &dh)) != cudaSuccess || (!T.exact && (e = upload(P, T.lo, &dl)) != cudaSuccess) ||
         (e = upload(P, st, &dst)) != cudaSuccess) {
       destroy(P);
       return fail(MEA_E_CUDA, std::string("mea_create_process: ") + cudaGetErrorString(e));
     }
     P->cf_hi = dh;
-    P->cf_lo = exact ? nullptr : dl;
+    P->cf_lo = T.exact ? nullptr : dl;
+    P->cf_nc = T.nc;
+    P->cf_np = T.np;
+    P->cf_kp = T.kp;
     P->status = const_cast<int*>(dst);
   }
   {

@@ -1,6 +1,6 @@
 // Colour contraction on the tensor cores (Eq. (color-averaged-amplitude)):
 // for every (event, helicity) pair p with colour amplitudes J_p (FP32, from
-// the amplitude kernel)
+// the colour-amplitude stage)
 //     val_p = 1/D * sum_{ab} J_a K_ab J_b^*  =  1/D * [ Jr.(K Jr) + Ji.(K Ji) ]
 // with the integer colour matrix K (N = K / D).  The rows (Jr, Ji) of 64 pairs
 // form the M = 128 rows of one tile; Z = J K runs as tcgen05.mma kind::f16
@@ -18,10 +18,16 @@
 //     with the compensated dot product Dot2 in FP32 (twice the working
 //     precision; the FP64 pipe of this part is 64 times slower), after which
 //     the row scale is undone.
-// Operands are staged in shared memory in the canonical no-swizzle K-major
-// layout (8-row x 16-byte core matrices).  Every wait is bounded: on expiry
-// the kernel records an error in *status, drains its own MMAs with a bounded
-// wait, frees its tensor memory and returns.
+// Pipeline (one iteration per (column block, K chunk)): the J chunk of the
+// next iteration is prefetched into registers and its K tiles copied
+// asynchronously (cp.async) into the other shared-memory stage while the
+// tensor core works; the MMAs of iteration i write one of two tensor-memory
+// buffers while the epilogue of iteration i-1 reads the other.  Operands are
+// staged in the canonical no-swizzle K-major layout (8-row x 16-byte core
+// matrices); the K tiles are laid out that way once per process
+// (build_colour_tiles).  Every wait is bounded: on expiry the kernel records an
+// error in *status, drains its own MMAs with a bounded wait, frees its tensor
+// memory and returns.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -35,199 +41,290 @@
 namespace mea {
 namespace {
 
-constexpr int kThreads = 128;   // 4 warps: TMEM lanes 0..127 = tile rows
-constexpr int kM = 128;         // tile rows (64 pairs x {re, im})
-constexpr int kKC = 64;         // K elements per shared-memory stage
 using namespace tc;
+
+constexpr int kThreads = 256;  // 8 warps convert; warps w and w+4 share TMEM lanes 32(w%4).. in the epilogue
+constexpr int kM = 128;        // tile rows (64 pairs x {re, im})
+constexpr int kKC = 64;        // K elements per stage
+constexpr int kPlaneA = kM * kKC * 2;
+
+__host__ __device__ constexpr size_t stage_bytes(int nc) { return (size_t)3 * kPlaneA + (size_t)2 * nc * kKC * 2; }
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  // layout: A_hi, A_mid, A_lo [128 x KC], B_hi, B_lo [NC x KC], bars, tmem slot, scales
   const int t = threadIdx.x;
   const int warp = t >> 5;
   const int NC = g.nc;
-  unsigned char* a_hi = smem;
-  unsigned char* a_mid = a_hi + kM * kKC * 2;
-  unsigned char* a_lo = a_mid + kM * kKC * 2;
-  unsigned char* b_hi = a_lo + kM * kKC * 2;
-  unsigned char* b_lo = b_hi + NC * kKC * 2;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(b_lo + NC * kKC * 2);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-  float* rscale = reinterpret_cast<float*>(tslot + 4);  // [128] per-row scale 2^-e
-  int* abort_flag = reinterpret_cast<int*>(rscale + kM);
-  double* rowbuf = reinterpret_cast<double*>(abort_flag + 2);  // [128] row values
+  const size_t SB = stage_bytes(NC);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SB);  // [2] MMA commits of the two TMEM buffers
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  int* abort_flag = reinterpret_cast<int*>(tslot + 1);
+  float* rscale = reinterpret_cast<float*>(tslot + 4);           // [128] per-row scale 2^-e
+  // scratch that lives in stage 1's first operand plane while no MMA reads it:
+  // row-maximum halves at the start of a tile, per-(row, half) values at its end
+  float* rmax = reinterpret_cast<float*>(smem + SB);                     // [256]
+  double* part = reinterpret_cast<double*>(smem + SB + kThreads * 4);    // [256]
 
+  uint32_t tmem_cols = 32;
+  while (tmem_cols < (uint32_t)(2 * NC)) tmem_cols <<= 1;
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"((uint32_t)g.tmem_cols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 0) tmem_alloc(tslot, tmem_cols);
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  uint32_t phase = 0;
-  int pending = -1;  // phase of a wait that expired (drained once more before freeing TMEM)
+
+  uint32_t phase[2] = {0u, 0u};
+  int outstanding[2] = {0, 0};
   const int m = g.m, ldj = g.ldj;
   const int64_t n_rows = 2 * g.n_pairs;
   const int64_t n_tiles = (n_rows + kM - 1) / kM;
+  const int n_kc = g.kp / kKC, n_nb = g.np / NC;
+  const int n_it = n_kc * n_nb;
   const uint32_t idesc = make_idesc(kM, NC);
   const bool use_blo = g.b_lo != nullptr;
+  const int row = t & (kM - 1);
+  const int half = t >> 7;  // conversion: k groups of this thread; epilogue: column half
+  const int nvec = NC * kKC / 8;  // 16-byte vectors per K tile plane
+
+  auto wait_buf = [&](int b) -> bool {
+    if (!outstanding[b]) return true;
+    if (*abort_flag) return false;
+    if (!mbar_wait(&bar[b], phase[b])) {
+      atomicExch(abort_flag, 1);
+      if (g.status) atomicExch(g.status, 1);
+      return false;  // left outstanding: drained once more before TMEM is freed
+    }
+    phase[b] ^= 1u;
+    outstanding[b] = 0;
+    return true;
+  };
 
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t row0 = tile * kM;
+    const int64_t r = row0 + row;
+    const bool row_ok = r < n_rows;
+    const float* jrow = g.J + r * ldj;
     // per-row power-of-two scale so that the largest |J| lands near 2^14
     {
-      const int64_t r = row0 + t;
       float mx = 0.f;
-      if (r < n_rows) {
-        const float* jr = g.J + r * ldj;
-        for (int k = 0; k < m; ++k) mx = fmaxf(mx, fabsf(jr[k]));
+      if (row_ok)
+        for (int k = half; k < m; k += 2) mx = fmaxf(mx, fabsf(jrow[k]));
+      rmax[t] = mx;
+      __syncthreads();
+      if (t < kM) {
+        mx = fmaxf(rmax[t], rmax[t + kM]);
+        int e = 0;
+        if (mx > 0.f && isfinite(mx)) frexpf(mx, &e);
+        rscale[t] = ldexpf(1.f, max(-120, min(120, 14 - e)));
       }
-      int e = 0;
-      if (mx > 0.f && isfinite(mx)) { frexpf(mx, &e); }
-      rscale[t] = ldexpf(1.f, max(-120, min(120, 14 - e)));
+      __syncthreads();
     }
-    float acc_hi = 0.f, acc_lo = 0.f;  // this thread's row: sum_a J_a Z_a (scaled), compensated
-    for (int n0 = 0; n0 < g.np; n0 += NC) {
-      for (int k0 = 0; k0 < g.kp; k0 += kKC) {
-        __syncthreads();  // previous MMAs and epilogue reads are done before overwriting
-        // A tiles: 128 rows x KC columns, three FP16 parts of the scaled J
-        for (int idx = t; idx < kM * kKC; idx += kThreads) {
-          int row = idx / kKC, k = idx - (idx / kKC) * kKC;
-          int64_t r = row0 + row;
-          int kk = k0 + k;
-          float x = 0.f;
-          if (r < n_rows && kk < m) x = g.J[r * ldj + kk] * rscale[row];
-          __half hi = __float2half_rn(x);
-          float r1 = x - __half2float(hi);
-          __half mid = __float2half_rn(r1);
-          __half lo = __float2half_rn(r1 - __half2float(mid));
-          uint32_t off = canon_off(row, k, kKC);
-          *reinterpret_cast<__half*>(a_hi + off) = hi;
-          *reinterpret_cast<__half*>(a_mid + off) = mid;
-          *reinterpret_cast<__half*>(a_lo + off) = lo;
-        }
-        // B tiles: rows n0..n0+NC of the (symmetric) colour matrix, K columns k0..
-        for (int idx = t; idx < NC * kKC; idx += kThreads) {
-          int row = idx / kKC, k = idx - (idx / kKC) * kKC;
-          int nn = n0 + row, kk = k0 + k;
-          __half hi = __float2half_rn(0.f), lo = hi;
-          if (nn < m && kk < m) {
-            hi = g.b_hi[(size_t)nn * m + kk];
-            if (use_blo) lo = g.b_lo[(size_t)nn * m + kk];
-          }
-          uint32_t off = canon_off(row, k, kKC);
-          *reinterpret_cast<__half*>(b_hi + off) = hi;
-          *reinterpret_cast<__half*>(b_lo + off) = lo;
-        }
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (t == 0 && !*abort_flag) {
-          const uint32_t lbo = 128, sbo_a = (kKC / 8) * 128, sbo_b = (kKC / 8) * 128;
-          for (int ks = 0; ks < kKC / 16; ++ks) {
-            uint32_t koff = (uint32_t)(ks * 2 * 128);
-            uint64_t dah = make_desc(smem_u32(a_hi) + koff, lbo, sbo_a);
-            uint64_t dam = make_desc(smem_u32(a_mid) + koff, lbo, sbo_a);
-            uint64_t dal = make_desc(smem_u32(a_lo) + koff, lbo, sbo_a);
-            uint64_t dbh = make_desc(smem_u32(b_hi) + koff, lbo, sbo_b);
-            uint64_t dbl = make_desc(smem_u32(b_lo) + koff, lbo, sbo_b);
-            uint32_t first = (ks == 0) ? 0u : 1u;  // fresh accumulator for every K chunk
-            // smallest terms first
-            mma_f16(tmem, dal, dbh, idesc, first);
-            if (use_blo) {
-              mma_f16(tmem, dam, dbl, idesc, 1u);
-              mma_f16(tmem, dah, dbl, idesc, 1u);
-            }
-            mma_f16(tmem, dam, dbh, idesc, 1u);
-            mma_f16(tmem, dah, dbh, idesc, 1u);
-          }
-          mma_commit(bar);
-        }
-        if (!*abort_flag) {
-          if (!mbar_wait(bar, phase)) {
-            atomicExch(abort_flag, 1);
-            pending = (int)phase;
-            if (g.status) atomicExch(g.status, 1);
-          }
-        }
-        phase ^= 1u;
-        fence_after();
-        // epilogue of this K chunk: this thread owns TMEM lane t (its row)
-        if (!*abort_flag) {
-          const int64_t r = row0 + t;
-          const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-          for (int c0 = 0; c0 < NC && n0 + c0 < m; c0 += 16) {
-            float z[16];
-            tmem_ld16(tmem + lane_base + (uint32_t)c0, z);
-            if (r < n_rows) {
-              const float* jr = g.J + r * ldj + n0 + c0;
+    const float sc = rscale[row];
+    float acc_hi = 0.f, acc_lo = 0.f;  // Dot2 of this thread's (row, column half)
+    float pj[4][8];                    // prefetched J chunk: 4 groups of 8 columns
+
+    auto prefetch = [&](int it) {
+      const int kc = it % n_kc;
 #pragma unroll
-              for (int i = 0; i < 16; ++i)
-                if (n0 + c0 + i < m) {
-                  // Dot2 (Ogita, Rump, Oishi 2005): exact product error by FMA,
-                  // two-sum of the running value, errors collected in acc_lo
-                  const float p = __fmul_rn(jr[i], z[i]);
-                  const float pe = fmaf(jr[i], z[i], -p);
-                  const float s = __fadd_rn(acc_hi, p);
-                  const float bb = __fsub_rn(s, acc_hi);
-                  const float se = __fadd_rn(__fsub_rn(acc_hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-                  acc_hi = s;
-                  acc_lo = __fadd_rn(acc_lo, __fadd_rn(se, pe));
-                }
+      for (int j = 0; j < 4; ++j) {
+        const int kg = half + 2 * j;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int kk = kc * kKC + kg * 8 + i;
+          pj[j][i] = (row_ok && kk < m) ? jrow[kk] : 0.f;
+        }
+      }
+    };
+    auto copy_tiles = [&](int it, int st) {
+      const int nb = it / n_kc, kc = it % n_kc;
+      unsigned char* b_hi = smem + st * SB + 3 * kPlaneA;
+      unsigned char* b_lo = b_hi + (size_t)NC * kKC * 2;
+      const size_t tile_off = ((size_t)nb * n_kc + kc) * NC * kKC;
+      const uint4* shi = reinterpret_cast<const uint4*>(g.b_hi + tile_off);
+      for (int i = t; i < nvec; i += kThreads) cp_async16(b_hi + 16 * i, shi + i);
+      if (use_blo) {
+        const uint4* slo = reinterpret_cast<const uint4*>(g.b_lo + tile_off);
+        for (int i = t; i < nvec; i += kThreads) cp_async16(b_lo + 16 * i, slo + i);
+      }
+      cp_async_commit();
+    };
+    // epilogue of iteration it (buffer it % 2): this thread's row, its half of the columns
+    auto epilogue = [&](int it) {
+      const int b = it & 1;
+      if (!wait_buf(b)) return;
+      fence_after();
+      const int n0 = (it / n_kc) * NC;
+      const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
+      const uint32_t base = tmem + (uint32_t)(b * NC) + lane;
+      for (int c0 = half * (NC / 2); c0 < (half + 1) * (NC / 2); c0 += 16) {
+        float z[16];
+        tmem_ld16(base + (uint32_t)c0, z);
+        if (row_ok) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int a = n0 + c0 + i;
+            if (a < m) {
+              // Dot2 (Ogita, Rump, Oishi 2005): exact product error by FMA,
+              // two-sum of the running value, errors collected in acc_lo
+              const float jv = jrow[a];
+              const float p = __fmul_rn(jv, z[i]);
+              const float pe = fmaf(jv, z[i], -p);
+              const float s = __fadd_rn(acc_hi, p);
+              const float bb = __fsub_rn(s, acc_hi);
+              const float se = __fadd_rn(__fsub_rn(acc_hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+              acc_hi = s;
+              acc_lo = __fadd_rn(acc_lo, __fadd_rn(se, pe));
             }
           }
         }
-        fence_before();
       }
+      fence_before();
+    };
+
+    prefetch(0);
+    copy_tiles(0, 0);
+    for (int it = 0; it < n_it; ++it) {
+      const int st = it & 1;
+      unsigned char* a_hi = smem + st * SB;
+      unsigned char* a_mid = a_hi + kPlaneA;
+      unsigned char* a_lo = a_mid + kPlaneA;
+      unsigned char* b_hi = a_lo + kPlaneA;
+      unsigned char* b_lo = b_hi + (size_t)NC * kKC * 2;
+      // J digits into this stage (free: its MMAs, iteration it-2, were waited
+      // for by the epilogue of it-2 during iteration it-1)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int kg = half + 2 * j;
+        __align__(16) __half hv[8], mv[8], lv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float x = __fmul_rn(pj[j][i], sc);
+          const __half h = __float2half_rn(x);
+          const float r1 = __fsub_rn(x, __half2float(h));
+          const __half md = __float2half_rn(r1);
+          hv[i] = h;
+          mv[i] = md;
+          lv[i] = __float2half_rn(__fsub_rn(r1, __half2float(md)));
+        }
+        const uint32_t off = canon_off(row, kg * 8, kKC);
+        *reinterpret_cast<uint4*>(a_hi + off) = *reinterpret_cast<const uint4*>(hv);
+        *reinterpret_cast<uint4*>(a_mid + off) = *reinterpret_cast<const uint4*>(mv);
+        *reinterpret_cast<uint4*>(a_lo + off) = *reinterpret_cast<const uint4*>(lv);
+      }
+      cp_async_wait_all();  // this stage's K tiles
+      fence_async_smem();
+      fence_before();
       __syncthreads();
       fence_after();
-    }
-    // row value = (J . Z) / scale ; pair value = (re row + im row) / D
-    {
-      double* rowval = rowbuf;
-      rowval[t] = ((double)acc_hi + (double)acc_lo) / (double)rscale[t];
-      __syncthreads();
-      if (t < kM / 2) {
-        int64_t p = tile * (kM / 2) + t;
-        if (p < g.n_pairs) g.pairval[p] = (rowval[2 * t] + rowval[2 * t + 1]) * g.inv_den;
+      if (!*abort_flag) {
+        if (t == 0) {
+          const uint32_t lbo = 128, sbo = (kKC / 8) * 128;
+          const uint32_t d = tmem + (uint32_t)(st * NC);
+          for (int ks = 0; ks < kKC / 16; ++ks) {
+            const uint32_t koff = (uint32_t)(ks * 2 * 128);
+            const uint64_t dah = make_desc(smem_u32(a_hi) + koff, lbo, sbo);
+            const uint64_t dam = make_desc(smem_u32(a_mid) + koff, lbo, sbo);
+            const uint64_t dal = make_desc(smem_u32(a_lo) + koff, lbo, sbo);
+            const uint64_t dbh = make_desc(smem_u32(b_hi) + koff, lbo, sbo);
+            const uint64_t dbl = make_desc(smem_u32(b_lo) + koff, lbo, sbo);
+            const uint32_t first = (ks == 0) ? 0u : 1u;  // fresh accumulator for every K chunk
+            // smallest terms first
+            mma_f16(d, dal, dbh, idesc, first);
+            if (use_blo) {
+              mma_f16(d, dam, dbl, idesc, 1u);
+              mma_f16(d, dah, dbl, idesc, 1u);
+            }
+            mma_f16(d, dam, dbh, idesc, 1u);
+            mma_f16(d, dah, dbh, idesc, 1u);
+          }
+          mma_commit(&bar[st]);
+        }
+        outstanding[st] = 1;
       }
-      __syncthreads();
+      if (it > 0) epilogue(it - 1);
+      if (it + 1 < n_it) {
+        prefetch(it + 1);
+        copy_tiles(it + 1, st ^ 1);
+      }
     }
+    if (n_it > 0) epilogue(n_it - 1);
+    // row value = (J . Z) / scale ; pair value = (re row + im row) / D
+    part[t] = ((double)acc_hi + (double)acc_lo) / (double)sc;
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t < kM / 2) {
+      const int64_t p = tile * (kM / 2) + t;
+      const int a = 2 * t, b = 2 * t + 1;
+      if (p < g.n_pairs) g.pairval[p] = (part[a] + part[a + kM] + part[b] + part[b + kM]) * g.inv_den;
+    }
+    __syncthreads();
   }
   // an expired wait: give the outstanding MMAs one more bounded wait before
   // the tensor memory they write is released
-  if (pending >= 0) mbar_wait(bar, (uint32_t)pending);
-  // free tensor memory (after every tcgen05.ld has completed)
+  for (int b = 0; b < 2; ++b)
+    if (outstanding[b]) mbar_wait(&bar[b], phase[b]);
   fence_before();
   __syncthreads();
   fence_after();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)g.tmem_cols)
-                 : "memory");
+  if (warp == 0) tmem_dealloc(tmem, tmem_cols);
 }
 
 }  // namespace
 
-size_t colour_gemm_smem(int nc) {
-  return (size_t)kM * kKC * 2 * 3 + (size_t)nc * kKC * 2 * 2 + 64 + kM * 4 + 16 + kM * 8;
+ColourTiles build_colour_tiles(const std::vector<int64_t>& K, int m) {
+  ColourTiles T;
+  T.m = m;
+  const int nb = (m + 255) / 256;
+  T.nc = ((m + nb - 1) / nb + 31) / 32 * 32;  // column halves of the epilogue are multiples of 16
+  T.np = nb * T.nc;
+  T.kp = ((m + kKC - 1) / kKC) * kKC;
+  const int n_kc = T.kp / kKC;
+  const size_t per_tile = (size_t)T.nc * kKC;
+  T.hi.assign((size_t)nb * n_kc * per_tile, __float2half(0.f));
+  T.lo.assign(T.hi.size(), __float2half(0.f));
+  T.exact = true;
+  for (int a = 0; a < T.np; ++a)
+    for (int k = 0; k < T.kp; ++k) {
+      const int b = a / T.nc, row = a - b * T.nc, kc = k / kKC, kk = k - kc * kKC;
+      double v = (a < m && k < m) ? (double)K[(size_t)a * m + k] : 0.0;
+      const __half h = __float2half_rn((float)v);
+      const double rest = v - (double)__half2float(h);
+      const __half l = __float2half_rn((float)rest);
+      if (rest != 0.0) T.exact = false;
+      const size_t base = ((size_t)b * n_kc + kc) * per_tile;
+      const uint32_t off = tc::canon_off(row, kk, kKC) / 2;
+      T.hi[base + off] = h;
+      T.lo[base + off] = l;
+    }
+  return T;
 }
+
+size_t colour_gemm_smem(int nc) { return 2 * stage_bytes(nc) + 16 + 16 + (size_t)kM * 4; }
 
 cudaError_t launch_colour_gemm(const ColourGemmArgs& a, int num_sms, cudaStream_t s) {
   if (a.n_pairs <= 0) return cudaSuccess;
+  if (a.nc < 32 || a.nc > 256 || a.nc % 32 != 0 || a.kp % kKC != 0 || a.np % a.nc != 0) return cudaErrorInvalidValue;
   size_t sm = colour_gemm_smem(a.nc);
   cudaError_t e = cudaFuncSetAttribute(colour_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int64_t tiles = (2 * a.n_pairs + kM - 1) / kM;
-  int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms);
+  int tmem = 32;
+  while (tmem < 2 * a.nc) tmem *= 2;
+  const int per_sm = std::max(1, std::min<int>(512 / tmem, (int)((227u << 10) / sm)));
+  int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms * per_sm);
   colour_gemm_kernel<<<grid, kThreads, sm, s>>>(a);
   e = cudaGetLastError();
   if (e == cudaSuccess) ++launch_counter();

@@ -64,9 +64,10 @@ struct mea_process_s {
   mea::AmpConfig tuned[2];
   int tuned_H[2] = {0, 0};
   bool auto_tuned[2] = {false, false};  // tuned once already (explicitly or on first large evaluation)
-  // tensor-core colour stage: fp16(K) and K - fp16(K) (null when exact), status word
-  const __half* cf_hi = nullptr;
+  // status word of the bounded device waits
+  const __half* cf_hi = nullptr;   // colour matrix operand tiles (colour_gemm.h ColourTiles)
   const __half* cf_lo = nullptr;
+  int cf_nc = 0, cf_np = 0, cf_kp = 0;
   int* status = nullptr;
   // diagram -> colour-amplitude map for the tensor-core colour-amplitude stage
   mea::JampMap jmap;                  // host description (tiles released after upload)
