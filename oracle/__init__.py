@@ -41,25 +41,44 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _configure(lib):
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p
+    lib.oq_create.restype = vp
+    lib.oq_create.argtypes = [ctypes.POINTER(ctypes.c_int), i32, ctypes.c_double]
+    lib.oq_destroy.argtypes = [vp]
+    lib.oq_last_error.restype = ctypes.c_char_p
+    lib.oq_info.argtypes = [vp, dp, dp, dp]
+    lib.oq_me2.argtypes = [vp, dp, i64, dp, dp, i32]
+    lib.oq_jamp.argtypes = [vp, dp, i32, i32, dp]
+    lib.oq_colour_matrix.argtypes = [vp, dp]
+    lib.oq_colour_matrix_exact.argtypes = [vp, dp, dp, dp, dp]
+    lib.oq_basis.argtypes = [vp, i32, dp, i32]
+    lib.oq_diagram_colour.argtypes = [vp, i32, dp, dp, dp, i32]
+    lib.oq_max_threads.restype = i32
+    return lib
+
+
+def build_variant(path: str, mutation: int) -> str:
+    """Compile a copy of the oracle with test mutation `mutation` planted
+    (OQ_MUTATION, see qcd_oracle.cpp) into `path`; tests only."""
+    cmd = ["g++", "-O1", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-fno-fast-math",
+           "-ffp-contract=off", f"-DOQ_MUTATION={int(mutation)}", "-o", path, _SRC]
+    subprocess.check_call(cmd)
+    return path
+
+
+def load_variant(path: str):
+    """ctypes handle of a library built by build_variant, for OracleProcess(lib=...)."""
+    return _configure(ctypes.CDLL(path))
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
             lib = ctypes.CDLL(_LIB_PATH)
-            vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p
-            lib.oq_create.restype = vp
-            lib.oq_create.argtypes = [ctypes.POINTER(ctypes.c_int), i32, ctypes.c_double]
-            lib.oq_destroy.argtypes = [vp]
-            lib.oq_last_error.restype = ctypes.c_char_p
-            lib.oq_info.argtypes = [vp, dp, dp, dp]
-            lib.oq_me2.argtypes = [vp, dp, i64, dp, dp, i32]
-            lib.oq_jamp.argtypes = [vp, dp, i32, i32, dp]
-            lib.oq_colour_matrix.argtypes = [vp, dp]
-            lib.oq_colour_matrix_exact.argtypes = [vp, dp, dp, dp, dp]
-            lib.oq_basis.argtypes = [vp, i32, dp, i32]
-            lib.oq_diagram_colour.argtypes = [vp, i32, dp, dp, dp, i32]
-            lib.oq_max_threads.restype = i32
+            _configure(lib)
             _lib = lib
     return _lib
 
@@ -79,8 +98,9 @@ class OracleProcess:
     (21 gluon, 2 u, -2 u-bar).
     """
 
-    def __init__(self, pdg, alpha_s: float = 0.118):
-        lib = _load()
+    def __init__(self, pdg, alpha_s: float = 0.118, lib=None):
+        lib = lib if lib is not None else _load()
+        self._lib = lib
         self.pdg = list(pdg)
         self.n_ext = len(self.pdg)
         self.alpha_s = alpha_s
@@ -96,7 +116,7 @@ class OracleProcess:
     def __del__(self):
         try:
             if getattr(self, "_h", None):
-                _load().oq_destroy(self._h)
+                self._lib.oq_destroy(self._h)
         except Exception:
             pass
 
@@ -113,25 +133,25 @@ class OracleProcess:
         n = mom.shape[0]
         out = np.zeros(n, dtype=np.float64)
         hel = np.zeros((n, 1 << self.n_ext), dtype=np.float64) if per_helicity else None
-        rc = _load().oq_me2(self._h, _ptr(mom), n, _ptr(out),
+        rc = self._lib.oq_me2(self._h, _ptr(mom), n, _ptr(out),
                             _ptr(hel) if hel is not None else None, threads)
         if rc != 0:
-            raise RuntimeError("oracle: " + _load().oq_last_error().decode())
+            raise RuntimeError("oracle: " + self._lib.oq_last_error().decode())
         return (out, hel) if per_helicity else out
 
     def jamp(self, momenta_one, hel: int, ward_leg: int = -1) -> np.ndarray:
         """Colour amplitudes J_alpha (complex [n_colour]) for one event and helicity."""
         mom = np.ascontiguousarray(momenta_one, dtype=np.float64).reshape(self.n_ext, 4)
         out = np.zeros(2 * self.n_colour, dtype=np.float64)
-        rc = _load().oq_jamp(self._h, _ptr(mom), hel, ward_leg, _ptr(out))
+        rc = self._lib.oq_jamp(self._h, _ptr(mom), hel, ward_leg, _ptr(out))
         if rc != 0:
-            raise RuntimeError("oracle: " + _load().oq_last_error().decode())
+            raise RuntimeError("oracle: " + self._lib.oq_last_error().decode())
         return out[0::2] + 1j * out[1::2]
 
     def colour_matrix(self) -> np.ndarray:
         m = self.n_colour
         out = np.zeros((m, m), dtype=np.float64)
-        _load().oq_colour_matrix(self._h, _ptr(out))
+        self._lib.oq_colour_matrix(self._h, _ptr(out))
         return out
 
     def colour_matrix_exact(self):
@@ -140,7 +160,7 @@ class OracleProcess:
         from fractions import Fraction
         m = self.n_colour
         arrs = [np.zeros((m, m), dtype=np.int64) for _ in range(4)]
-        _load().oq_colour_matrix_exact(self._h, *[_ptr(a) for a in arrs])
+        self._lib.oq_colour_matrix_exact(self._h, *[_ptr(a) for a in arrs])
         re = [[Fraction(int(arrs[0][i, j]), int(arrs[1][i, j])) for j in range(m)] for i in range(m)]
         im = [[Fraction(int(arrs[2][i, j]), int(arrs[3][i, j])) for j in range(m)] for i in range(m)]
         return re, im
@@ -148,7 +168,7 @@ class OracleProcess:
     def basis(self, alpha: int):
         """Basis element alpha: list of (closed, row, col, gluon_legs)."""
         buf = np.zeros(256, dtype=np.int32)
-        n = _load().oq_basis(self._h, alpha, _ptr(buf), 256)
+        n = self._lib.oq_basis(self._h, alpha, _ptr(buf), 256)
         if n < 0:
             raise IndexError(alpha)
         out, i = [], 0
@@ -165,6 +185,6 @@ class OracleProcess:
         a = np.zeros(cap, dtype=np.int32)
         re = np.zeros(cap)
         im = np.zeros(cap)
-        n = _load().oq_diagram_colour(self._h, d, _ptr(a), _ptr(re), _ptr(im), cap)
+        n = self._lib.oq_diagram_colour(self._h, d, _ptr(a), _ptr(re), _ptr(im), cap)
         n = min(n, cap)
         return [(int(a[i]), complex(re[i], im[i])) for i in range(n)]

@@ -52,7 +52,18 @@
 #include <omp.h>
 #endif
 
+// Test hook: a nonzero OQ_MUTATION plants one deliberate, plausible mistake
+// (a dropped vertex term, a flipped sign, a slipped index, a wrong colour
+// average, a forgotten crossing sign) so that tests/test_oracle_mutations.py
+// can show that the pins catch it.  Only that test sets it, in a separate build;
+// the oracle's own build never does.
+#ifndef OQ_MUTATION
+#define OQ_MUTATION 0
+#endif
+
 namespace oq {
+
+constexpr int kMutation = OQ_MUTATION;
 
 typedef std::complex<double> cd;
 typedef long long i64;
@@ -783,7 +794,7 @@ static void build_colour(Process& P) {
   // Eq. (color-matrix): N_ab = 1/(n_a n_b) sum_c T_a^c (T_b^c)^*
   P.cmat_exact.assign((size_t)m * m, CQ{qint(0), qint(0)});
   P.cmat.assign((size_t)m * m, 0.0);
-  Q avg = qmk(1, (i128)P.n_a * P.n_b);
+  Q avg = qmk(1, kMutation == 5 ? (i128)64 : (i128)P.n_a * P.n_b);  // mutation 5: gluon averaging for quarks
   std::vector<std::vector<Chain>> bc(m);
   for (int a = 0; a < m; ++a) bc[a] = key_chains(P.basis[a]);
   std::vector<std::pair<int, int>> jobs;
@@ -834,7 +845,8 @@ static void mask_momentum(const EvalCtx& C, uint32_t m, double* K) {
   K[0] = K[1] = K[2] = K[3] = 0.0;
   for (int l = 0; l < C.P->n_ext; ++l)
     if (m >> l & 1u)
-      for (int mu = 0; mu < 4; ++mu) K[mu] += C.k[l][mu];
+      for (int mu = 0; mu < 4; ++mu)  // mutation 7: the crossing sign of outgoing legs forgotten
+        K[mu] += (kMutation == 7 && l >= 2) ? -C.k[l][mu] : C.k[l][mu];
 }
 static double msq(const double* K) {
   return K[0] * K[0] - K[1] * K[1] - K[2] * K[2] - K[3] * K[3];
@@ -849,6 +861,7 @@ static cd ggg_contract(double gs, const double* k[3], const V4* W[3]) {
   static const int sgn[6] = {1, 1, 1, -1, -1, -1};
   cd s = 0;
   for (int p = 0; p < 6; ++p) {
+    if (kMutation == 1 && p == 5) continue;  // mutation: a dropped vertex term
     int a = perm[p][0], b = perm[p][1], c = perm[p][2];
     s += (double)sgn[p] * dot_ul(k[a], *W[b]) * dot_ll(*W[a], *W[c]);
   }
@@ -884,6 +897,7 @@ static cd gggg_contract(double gs, int st, const V4* W[4]) {
     if (quartic_structure(x, &sign) != st) continue;
     s += (double)sign * dot_ll(*W[x[0]], *W[x[2]]) * dot_ll(*W[x[1]], *W[x[3]]);
   } while (std::next_permutation(x, x + 4));
+  if (kMutation == 2 && st == 1) s = -s;  // mutation: a flipped sign
   return cd(0, 1) * (-(gs * gs) / 4.0) * s;
 }
 
@@ -921,7 +935,7 @@ static V4 open_gluon_vertex(const EvalCtx& C, const Node* n, const std::vector<W
     for (int mu = 0; mu < 4; ++mu) {
       cd g[4][4];
       for (int a = 0; a < 4; ++a) for (int b = 0; b < 4; ++b) g[a][b] = kG.m[mu][a][b];
-      out[mu] = cd(0, -C.gs) * row_col(kw[1].s, mat_col(g, kw[0].s));
+      out[mu] = cd(0, kMutation == 6 ? C.gs : -C.gs) * row_col(kw[1].s, mat_col(g, kw[0].s));  // mutation 6
     }
   }
   return out;
@@ -942,7 +956,8 @@ static Wave eval_node(const EvalCtx& C, const Node* n) {
   if (n->kind == KG) {
     // gluon propagator -i g_{mu nu} / K^2
     V4 up = open_gluon_vertex(C, n, kw);
-    for (int mu = 0; mu < 4; ++mu) w.v[mu] = cd(0, -1) * kMetric[mu] * up[mu] / K2;
+    for (int mu = 0; mu < 4; ++mu)
+      w.v[mu] = cd(0, -1) * (kMutation == 3 ? 1.0 : kMetric[mu]) * up[mu] / K2;  // mutation 3: index slip
     return w;
   }
   // qqg vertex -i g gamma^mu T^a (Eq. (qqg-lagrangian)); quark propagator i pslash / p^2
@@ -957,7 +972,8 @@ static Wave eval_node(const EvalCtx& C, const Node* n) {
     for (int a = 0; a < 4; ++a) w.s[a] = cd(0, 1) * u[a] / K2;
   } else {
     // momentum along the arrow (into the subset) = -K
-    double mK[4] = {-K[0], -K[1], -K[2], -K[3]};
+    const double sK = kMutation == 4 ? 1.0 : -1.0;  // mutation 4: wrong momentum direction
+    double mK[4] = {sK * K[0], sK * K[1], sK * K[2], sK * K[3]};
     slash_upper(mK, ps);
     Sp t = row_mat(kw[0].s, vs);
     for (int a = 0; a < 4; ++a) t[a] *= cd(0, -C.gs);
