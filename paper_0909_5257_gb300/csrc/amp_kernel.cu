@@ -46,24 +46,36 @@ union OpWords {
   Op op;
 };
 
+// Wavefunction slots are stored [slot][lane][8 reals]: one lane's wavefunction
+// is 32 (FP32) or 64 (FP64) contiguous bytes, moved with 16-byte vector
+// accesses -- a quarter warp then covers 128 contiguous bytes, conflict-free in
+// shared memory and whole sectors in global memory.
 template <typename R>
 __device__ __forceinline__ W4<R> ld_slot(const R* slots, int s, int L, int t) {
-  const R* b = slots + (size_t)s * 8 * L + t;
+  const R* b = slots + ((size_t)s * L + t) * 8;
   W4<R> w;
+  if constexpr (std::is_same<R, float>::value) {
+    const float4 u = *reinterpret_cast<const float4*>(b);
+    const float4 v = *reinterpret_cast<const float4*>(b + 4);
+    w.c[0] = {u.x, u.y}; w.c[1] = {u.z, u.w}; w.c[2] = {v.x, v.y}; w.c[3] = {v.z, v.w};
+  } else {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    w.c[k].r = b[(2 * k) * L];
-    w.c[k].i = b[(2 * k + 1) * L];
+    for (int k = 0; k < 4; ++k) {
+      const double2 u = *reinterpret_cast<const double2*>(b + 2 * k);
+      w.c[k] = {u.x, u.y};
+    }
   }
   return w;
 }
 template <typename R>
 __device__ __forceinline__ void st_slot(R* slots, int s, int L, int t, const W4<R>& w) {
-  R* b = slots + (size_t)s * 8 * L + t;
+  R* b = slots + ((size_t)s * L + t) * 8;
+  if constexpr (std::is_same<R, float>::value) {
+    *reinterpret_cast<float4*>(b) = make_float4(w.c[0].r, w.c[0].i, w.c[1].r, w.c[1].i);
+    *reinterpret_cast<float4*>(b + 4) = make_float4(w.c[2].r, w.c[2].i, w.c[3].r, w.c[3].i);
+  } else {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    b[(2 * k) * L] = w.c[k].r;
-    b[(2 * k + 1) * L] = w.c[k].i;
+    for (int k = 0; k < 4; ++k) *reinterpret_cast<double2*>(b + 2 * k) = make_double2(w.c[k].r, w.c[k].i);
   }
 }
 

@@ -164,17 +164,22 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
 #pragma unroll
         for (int j = 0; j < kKC / 8 / (kThreads / kM); ++j) {
           const int kg = (t >> 7) + j * (kThreads / kM);
-          __align__(16) __half hv[8], mv[8], lv[8];
+          __align__(16) __half2 hv[4], mv[4], lv[4];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float x = __fmul_rn(pa[j][i], sc);
-            const float h = rintf(x);
-            const float r1 = __fmul_rn(__fsub_rn(x, h), w1);
-            const float mm = rintf(r1);
-            const float l = rintf(__fmul_rn(__fsub_rn(r1, mm), w1));
-            hv[i] = __float2half_rn(h);
-            mv[i] = __float2half_rn(mm);
-            lv[i] = __float2half_rn(l);
+          for (int i = 0; i < 8; i += 2) {
+            float h[2], mm[2], l[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const float x = __fmul_rn(pa[j][i + u], sc);
+              h[u] = rintf(x);
+              const float r1 = __fmul_rn(__fsub_rn(x, h[u]), w1);
+              mm[u] = rintf(r1);
+              l[u] = rintf(__fmul_rn(__fsub_rn(r1, mm[u]), w1));
+            }
+            // integers of at most 2^q <= 2048 in magnitude: exact in FP16
+            hv[i / 2] = __floats2half2_rn(h[0], h[1]);
+            mv[i / 2] = __floats2half2_rn(mm[0], mm[1]);
+            lv[i / 2] = __floats2half2_rn(l[0], l[1]);
           }
           const uint32_t off = canon_off(row, kg * 8, kKC);
           *reinterpret_cast<uint4*>(a_h + off) = *reinterpret_cast<const uint4*>(hv);
