@@ -344,6 +344,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-sampled", action="store_true",
+                    help="skip the sampled-helicity (one helicity per event) throughput")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -458,6 +460,24 @@ def main():
             d["mixed_vs_fp64_rel_err_median"] = float(rel.median().item())
             d["mixed_vs_fp64_rel_err_max"] = float(rel.max().item())
             d["mixed_vs_fp64_rel_err_p99"] = float(torch.quantile(rel.float(), 0.99).item())
+        if not args.no_sampled:
+            # the paper's mode (one helicity per event, drawn from the
+            # non-vanishing set): throughput only, for comparison with its
+            # per-event timings (one sampled helicity = 1/H of a summed event)
+            P = procs[i]
+            hels = torch.from_numpy(P.helicities()).to("cuda")
+            g = torch.Generator(device="cuda").manual_seed(SEED_BASE + 11 + i)
+            pick = torch.randint(0, hels.shape[0], (n,), device="cuda", generator=g)
+            hsel = hels[pick].contiguous()
+            so = torch.empty(n, dtype=torch.float64, device="cuda")
+            P.evaluate(moms[i], so, hel_mode=mea.HEL_GIVEN, hel=hsel, precision=mea.PREC_MIXED, stream=stream)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(3):
+                P.evaluate(moms[i], so, hel_mode=mea.HEL_GIVEN, hel=hsel, precision=mea.PREC_MIXED, stream=stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            d["sampled_helicity_events_per_s"] = n / (ev0.elapsed_time(ev1) / 3 * 1e-3)
         per_sub[name] = d
 
     # roofline of the dominant kernel: the fused amplitude + colour kernel of the

@@ -158,6 +158,15 @@ mea_status mea_destroy_process(mea_process_t proc);
  * results are invalid).  Resets the indicator. */
 mea_status mea_check_status(mea_process_t proc, void *stream);
 
+/* Diagnostics, no counterpart in the paper: enqueue on `stream` a one-warp
+ * kernel that waits on an mbarrier nothing arrives on, with the bounded wait
+ * the tensor-core kernels use, limited to spin_limit polls (1..2^20), and
+ * records the expiry in the process's status word as those kernels do -- so
+ * that the next mea_check_status returns MEA_E_TIMEOUT.  Lets a caller (and
+ * the tests) exercise the timeout path without a hung or faulted GPU; the
+ * context stays usable.  MEA_E_ARG for a limit out of range. */
+mea_status mea_probe_bounded_wait(mea_process_t proc, uint32_t spin_limit, void *stream);
+
 /* ---- evaluation ----------------------------------------------------------- */
 
 /* me2_dev[n_events] (double, device) <- |M|^2 of every event.

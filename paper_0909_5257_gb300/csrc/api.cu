@@ -514,8 +514,16 @@ mea_status mea_check_status(mea_process_t P, void* stream) {
   if (v) {
     int z = 0;
     MEA_CUDA(cudaMemcpy(P->status, &z, sizeof(int), cudaMemcpyHostToDevice));
-    return fail(MEA_E_TIMEOUT, "mea_check_status: a bounded wait in the tensor-core colour kernel expired");
+    return fail(MEA_E_TIMEOUT, "mea_check_status: a bounded wait in a tensor-core kernel expired");
   }
+  return MEA_OK;
+}
+
+mea_status mea_probe_bounded_wait(mea_process_t P, uint32_t spin_limit, void* stream) {
+  if (!P) return fail(MEA_E_ARG, "mea_probe_bounded_wait: null process");
+  if (P->host_only) return fail(MEA_E_UNSUPPORTED, "mea_probe_bounded_wait: host-only process handle");
+  if (spin_limit < 1 || spin_limit > (1u << 20)) return fail(MEA_E_ARG, "mea_probe_bounded_wait: limit out of range");
+  MEA_CUDA(mea::launch_wait_probe(P->status, spin_limit, reinterpret_cast<cudaStream_t>(stream)));
   return MEA_OK;
 }
 

@@ -282,7 +282,27 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
   if (warp == 0) tmem_dealloc(tmem, tmem_cols);
 }
 
+// Probe of the timeout path: waits on an mbarrier that nothing arrives on,
+// with the same bounded wait as the kernels above, and records the expiry in
+// *status exactly as they do.
+__global__ void wait_probe_kernel(int* status, uint32_t limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0u, limit) && status) atomicExch(status, 1);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(int* status, uint32_t spin_limit, cudaStream_t s) {
+  wait_probe_kernel<<<1, 32, 0, s>>>(status, spin_limit);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) ++launch_counter();
+  return e;
+}
 
 ColourTiles build_colour_tiles(const std::vector<int64_t>& K, int m) {
   ColourTiles T;

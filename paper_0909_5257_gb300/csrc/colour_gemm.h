@@ -32,6 +32,10 @@ struct ColourGemmArgs {
   int* status = nullptr;         // set to 1 when a bounded wait expired
 };
 
+// One-warp kernel whose bounded mbarrier wait expires (nothing arrives):
+// exercises the timeout reporting of the tensor-core kernels without a hang.
+cudaError_t launch_wait_probe(int* status, uint32_t spin_limit, cudaStream_t s);
+
 size_t colour_gemm_smem(int nc);
 cudaError_t launch_colour_gemm(const ColourGemmArgs& a, int num_sms, cudaStream_t s);
 

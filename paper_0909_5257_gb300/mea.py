@@ -91,6 +91,7 @@ def load(path: str | None = None):
             lib.mea_helicities.argtypes = [vp, vp, i32, vp]
             lib.mea_destroy_process.argtypes = [vp]
             lib.mea_check_status.argtypes = [vp, vp]
+            lib.mea_probe_bounded_wait.argtypes = [vp, ctypes.c_uint32, vp]
             lib.mea_evaluate.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp, vp]
             lib.mea_evaluate_host.argtypes = [vp, vp, i64, i32, vp, vp]
             lib.mea_evaluate_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp]
@@ -216,6 +217,11 @@ class Process:
         _check(load().mea_autotune(self._h, _ptr(momenta), n_sample, precision, _ptr(scratch_me2),
                                    ctypes.byref(r)))
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
+    def probe_bounded_wait(self, spin_limit=1000, stream=None):
+        """Enqueue the timeout probe (mea_probe_bounded_wait): the next
+        check_status raises MeaError(MEA_E_TIMEOUT)."""
+        _check(load().mea_probe_bounded_wait(self._h, ctypes.c_uint32(spin_limit), _stream(stream)))
 
     def check_status(self, stream=None):
         """Synchronise and raise MeaError(MEA_E_TIMEOUT) if a bounded device wait expired."""

@@ -350,3 +350,25 @@ def test_input_check_flags(pdg):
     assert fm[9] & 0x01  # re-evaluated in FP64
     assert np.isfinite(g64[9]) and g64[9] > 0
     assert gm[9] == g64[9]
+
+
+def test_bounded_wait_timeout_is_reported_and_the_context_survives():
+    """A bounded mbarrier wait that expires (mea_probe_bounded_wait: nothing
+    arrives) is reported by check_status as MEA_E_TIMEOUT, the indicator then
+    resets, and the same context still evaluates correctly on the tensor-core
+    path -- no hang, no fault."""
+    mea = _mea()
+    pdg = [21] * 6
+    P = _proc(pdg)
+    P.check_status()
+    P.probe_bounded_wait(1000)
+    with pytest.raises(mea.MeaError) as e:
+        P.check_status()
+    assert e.value.status == -5
+    P.check_status()
+    with pytest.raises(mea.MeaError):
+        P.probe_bounded_wait(0)
+    mom, ref = _data("gg>gggg")
+    got, _ = _run(pdg, mom, mea.PREC_MIXED)
+    P.check_status()
+    assert np.median(np.abs(got / ref - 1.0)) <= 1e-6
