@@ -8,7 +8,17 @@ every subprocess once.  Momenta are generated on the device before timing and
 stay resident (2^20 x 5 x 32 B = 168 MB per subprocess, larger than L2, so no
 explicit L2 flush is needed between steps).
 
+Before timing, every subprocess is autotuned once per precision
+(mea_autotune on 2^16 events).  The line reports per subprocess the mixed and
+FP64 rates, their relative difference (median / p99 / max), the flagged
+fraction and the rate of the paper's sampled-helicity mode (one helicity per
+event); the roofline of the dominant kernel; e2e through host buffers; clocks;
+the oracle on the host cores as cpu_baseline.  Other workloads: --workload
+2jet | 4jet | batch (one CUDA graph over four uneven subprocesses) | serve
+(Poisson arrivals through the server, p50/p99).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload 3jet|2jet|4jet|batch|serve]
 Prints one JSON line on rank 0.
 """
 from __future__ import annotations

@@ -1,21 +1,28 @@
-// Amplitude stage: one lane per (event, helicity combination).
+// Amplitude stage, table-driven: one lane per (event, helicity combination).
 //
 // A CTA owns a tile of E events x H helicity lanes.  Per tile:
-//   phase 0  FP64 preparation, shared by the helicity lanes of an event:
-//            transverse polarisation bases and helicity spinor building blocks
-//            of every leg, and for every momentum sum ("mask") used by the
-//            program its flowing-out momentum and 1/P^2 computed in FP64
-//            before the cast to the lane precision (Sec. 3.2 step 4);
+//   phase 0  preparation, shared by the helicity lanes of an event
+//            (amp_common.cuh): transverse polarisation bases and helicity
+//            spinor blocks of every leg, and for every momentum sum ("mask")
+//            used by the program its flowing-out momentum and 1/P^2, the
+//            invariant formed in FP64 (FP64 path) or compensated FP32 (FP32
+//            path) before the cast to the lane precision; input checks;
 //   phase 1  every lane runs the process program (op table): external
 //            wavefunctions, shared off-shell currents, one amplitude per
-//            Feynman diagram, each amplitude added into the colour
-//            amplitudes J_alpha of its colour entries (Eq. (color-amplitude);
-//            two-sum compensated in FP32), then the colour quadratic form of
-//            Eq. (color-averaged-amplitude) with the integer colour matrix;
+//            Feynman diagram.  Default mode: each amplitude is added into the
+//            colour amplitudes J_alpha of its colour entries
+//            (Eq. (color-amplitude); two-sum compensated in FP32), then the
+//            colour quadratic form of Eq. (color-averaged-amplitude) with the
+//            integer colour matrix.  Amplitude-output mode (AOUT, FP32): the
+//            diagram amplitudes go to global memory for the tensor-core colour
+//            stages (jamp_gemm.cu, colour_gemm.cu), with per-row maxima and
+//            the cancellation mass;
 //   phase 2  the helicity sum of each event in fixed order, x 1/4, written to
-//            me2 together with the event flags.
-// Wavefunction slots and colour amplitudes live in shared memory in
-// [item][component][lane] order, so consecutive lanes touch consecutive words.
+//            me2 together with the event flags (default mode; in AOUT mode
+//            finish_kernel does it after the colour stages).
+// Wavefunction slots live in shared or global memory as [slot][lane][8 reals];
+// colour amplitudes as [alpha][component][lane], so consecutive lanes touch
+// consecutive words.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -36,7 +36,7 @@ enum OpType : uint8_t {
 struct Op {
   uint8_t type;
   uint8_t n_in;
-  uint16_t out;        // output slot (currents); unused for amplitudes
+  uint16_t out;        // output slot (currents); diagram ordinal (amplitudes)
   uint16_t in[4];      // input slots
   uint16_t mout;       // mask-table row of the produced line (momentum, 1/P^2)
   uint16_t min[4];     // mask-table rows of the inputs
@@ -85,6 +85,10 @@ struct Program {
   int n_hel = 0;
   std::vector<int8_t> hel_all;        // [2^n_ext][n_ext]
   double flops_per_hel = 0;
+  // cooperative schedule: ops of wave w are wave_ops[wave_begin[w] .. wave_begin[w+1])
+  std::vector<uint32_t> wave_ops;
+  std::vector<int> wave_begin;
+  int n_waves = 0;
   std::string basis_text;             // human-readable basis (debug)
 };
 
