@@ -86,6 +86,93 @@ __device__ __forceinline__ void st_slot(R* slots, int s, int L, int t, const W4<
   }
 }
 
+// One op of the process program for the (pair) lane t of a slot array with
+// stride L: external wavefunction or current into its slot (returns false), or
+// a diagram amplitude into amp (returns true).
+template <typename R>
+__device__ __forceinline__ bool eval_op(const Op& op, const DevProgram& P, R* slots, int L, int t, const R* et,
+                                        const R* mt, uint32_t lam_bits, R g, R gg, cx<R>& amp) {
+  switch (op.type) {
+    case OP_EXT: {
+      int l = op.leg;
+      int type = P.leg_info[4 * l], kind = P.leg_info[4 * l + 1];
+      bool in = P.leg_info[4 * l + 2] != 0;
+      const R* o = et + 8 * l;
+      W4<R> x;
+      int lam = (lam_bits >> l & 1u) ? 1 : -1;
+      if (type == 0) x = ext_gluon<R>(o, o + 3, lam, !in);
+      else x = ext_spinor<R>(o[0], o[1], mk<R>(o[2], o[3]), lam, kind);
+      st_slot(slots, op.out, L, t, x);
+      return false;
+    }
+    case OP_JVV: {
+      W4<R> a = ld_slot(slots, op.in[0], L, t);
+      W4<R> b = ld_slot(slots, op.in[1], L, t);
+      const R* pa = mt + 5 * op.min[0];
+      const R* pb = mt + 5 * op.min[1];
+      W4<R> j = jvv<R>(a, b, pa, pb, mt[5 * op.mout + 4], g);
+      st_slot(slots, op.out, L, t, j);
+      return false;
+    }
+    case OP_JGGG: {
+      W4<R> a = ld_slot(slots, op.in[0], L, t);
+      W4<R> b = ld_slot(slots, op.in[1], L, t);
+      W4<R> c = ld_slot(slots, op.in[2], L, t);
+      W4<R> j = jggg<R>(a, b, c, mt[5 * op.mout + 4], gg);
+      st_slot(slots, op.out, L, t, j);
+      return false;
+    }
+    case OP_FVI: {
+      W4<R> f = ld_slot(slots, op.in[0], L, t);
+      W4<R> v = ld_slot(slots, op.in[1], L, t);
+      const R* pq = mt + 5 * op.mout;
+      W4<R> j = fvi<R>(f, v, pq, pq[4], g);
+      st_slot(slots, op.out, L, t, j);
+      return false;
+    }
+    case OP_FVO: {
+      W4<R> f = ld_slot(slots, op.in[0], L, t);
+      W4<R> v = ld_slot(slots, op.in[1], L, t);
+      const R* pq = mt + 5 * op.mout;
+      W4<R> j = fvo<R>(f, v, pq, pq[4], g);
+      st_slot(slots, op.out, L, t, j);
+      return false;
+    }
+    case OP_JIO: {
+      W4<R> f = ld_slot(slots, op.in[0], L, t);
+      W4<R> o = ld_slot(slots, op.in[1], L, t);
+      W4<R> j = jio<R>(f, o, mt[5 * op.mout + 4], g);
+      st_slot(slots, op.out, L, t, j);
+      return false;
+    }
+    case OP_AVVV: {
+      W4<R> a = ld_slot(slots, op.in[0], L, t);
+      W4<R> b = ld_slot(slots, op.in[1], L, t);
+      W4<R> c = ld_slot(slots, op.in[2], L, t);
+      amp = vvv_amp<R>(a, b, c, mt + 5 * op.min[0], mt + 5 * op.min[1], mt + 5 * op.min[2], g);
+      return true;
+    }
+    case OP_AGGGG: {
+      W4<R> a = ld_slot(slots, op.in[0], L, t);
+      W4<R> b = ld_slot(slots, op.in[1], L, t);
+      W4<R> c = ld_slot(slots, op.in[2], L, t);
+      W4<R> d = ld_slot(slots, op.in[3], L, t);
+      amp = gggg_amp<R>(a, b, c, d, gg);
+      return true;
+    }
+    case OP_AIOV: {
+      W4<R> f = ld_slot(slots, op.in[0], L, t);
+      W4<R> o = ld_slot(slots, op.in[1], L, t);
+      W4<R> v = ld_slot(slots, op.in[2], L, t);
+      amp = iov_amp<R>(f, o, v, g);
+      return true;
+    }
+    default:
+      return false;
+  }
+  return false;
+}
+
 template <typename R, bool JSMEM, bool SSMEM, bool AOUT>
 __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, const AmpLaunch A,
                                                    const AmpConfig C) {
@@ -170,88 +257,7 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
         w.v[1] = __ldg(&ops[i].v[1]);
         const Op& op = w.op;
         cx<R> amp;
-        bool is_amp = false;
-        switch (op.type) {
-          case OP_EXT: {
-            int l = op.leg;
-            int type = P.leg_info[4 * l], kind = P.leg_info[4 * l + 1];
-            bool in = P.leg_info[4 * l + 2] != 0;
-            const R* o = et + 8 * l;
-            W4<R> x;
-            int lam = (lam_bits >> l & 1u) ? 1 : -1;
-            if (type == 0) x = ext_gluon<R>(o, o + 3, lam, !in);
-            else x = ext_spinor<R>(o[0], o[1], mk<R>(o[2], o[3]), lam, kind);
-            st_slot(slots, op.out, L, t, x);
-            break;
-          }
-          case OP_JVV: {
-            W4<R> a = ld_slot(slots, op.in[0], L, t);
-            W4<R> b = ld_slot(slots, op.in[1], L, t);
-            const R* pa = mt + 5 * op.min[0];
-            const R* pb = mt + 5 * op.min[1];
-            W4<R> j = jvv<R>(a, b, pa, pb, mt[5 * op.mout + 4], g);
-            st_slot(slots, op.out, L, t, j);
-            break;
-          }
-          case OP_JGGG: {
-            W4<R> a = ld_slot(slots, op.in[0], L, t);
-            W4<R> b = ld_slot(slots, op.in[1], L, t);
-            W4<R> c = ld_slot(slots, op.in[2], L, t);
-            W4<R> j = jggg<R>(a, b, c, mt[5 * op.mout + 4], gg);
-            st_slot(slots, op.out, L, t, j);
-            break;
-          }
-          case OP_FVI: {
-            W4<R> f = ld_slot(slots, op.in[0], L, t);
-            W4<R> v = ld_slot(slots, op.in[1], L, t);
-            const R* pq = mt + 5 * op.mout;
-            W4<R> j = fvi<R>(f, v, pq, pq[4], g);
-            st_slot(slots, op.out, L, t, j);
-            break;
-          }
-          case OP_FVO: {
-            W4<R> f = ld_slot(slots, op.in[0], L, t);
-            W4<R> v = ld_slot(slots, op.in[1], L, t);
-            const R* pq = mt + 5 * op.mout;
-            W4<R> j = fvo<R>(f, v, pq, pq[4], g);
-            st_slot(slots, op.out, L, t, j);
-            break;
-          }
-          case OP_JIO: {
-            W4<R> f = ld_slot(slots, op.in[0], L, t);
-            W4<R> o = ld_slot(slots, op.in[1], L, t);
-            W4<R> j = jio<R>(f, o, mt[5 * op.mout + 4], g);
-            st_slot(slots, op.out, L, t, j);
-            break;
-          }
-          case OP_AVVV: {
-            W4<R> a = ld_slot(slots, op.in[0], L, t);
-            W4<R> b = ld_slot(slots, op.in[1], L, t);
-            W4<R> c = ld_slot(slots, op.in[2], L, t);
-            amp = vvv_amp<R>(a, b, c, mt + 5 * op.min[0], mt + 5 * op.min[1], mt + 5 * op.min[2], g);
-            is_amp = true;
-            break;
-          }
-          case OP_AGGGG: {
-            W4<R> a = ld_slot(slots, op.in[0], L, t);
-            W4<R> b = ld_slot(slots, op.in[1], L, t);
-            W4<R> c = ld_slot(slots, op.in[2], L, t);
-            W4<R> d = ld_slot(slots, op.in[3], L, t);
-            amp = gggg_amp<R>(a, b, c, d, gg);
-            is_amp = true;
-            break;
-          }
-          case OP_AIOV: {
-            W4<R> f = ld_slot(slots, op.in[0], L, t);
-            W4<R> o = ld_slot(slots, op.in[1], L, t);
-            W4<R> v = ld_slot(slots, op.in[2], L, t);
-            amp = iov_amp<R>(f, o, v, g);
-            is_amp = true;
-            break;
-          }
-          default:
-            break;
-        }
+        const bool is_amp = eval_op<R>(op, P, slots, L, t, et, mt, lam_bits, g, gg, amp);
         if (AOUT && is_amp) {
           // hand the diagram amplitude to the tensor-core colour-amplitude stage
           float2* dst = reinterpret_cast<float2*>(A.amp_out + (size_t)d_amp * A.lda + 2 * pair);
@@ -291,6 +297,7 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
         A.amp_rowmax[2 * pair] = finite_amps ? mx_re : nan;
         A.amp_rowmax[2 * pair + 1] = finite_amps ? mx_im : nan;
         A.pair_kappa[pair] = abs_mass;  // divided by sum |J| after the colour-amplitude stage
+
       } else {
       // ---- colour sum: sum_ab J_a K_ab J_b^* / D
       R tot = (R)0;

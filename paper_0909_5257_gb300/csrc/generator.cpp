@@ -835,42 +835,6 @@ double op_flops(int type) {
 
 }  // namespace
 
-// Waves for cooperative execution: consecutive ops of the program, in order,
-// as long as no op of the wave reads a slot another op of the same wave writes,
-// or writes a slot another one reads or writes; then all ops of a wave can run
-// at once (the slot reuse of the sequential schedule is kept).  Within a wave
-// the ops are grouped by type, so that neighbouring threads run the same
-// function.  At most kWaveMax ops per wave.
-static void build_waves(Program& P) {
-  constexpr int kWaveMax = 4096;
-  P.wave_ops.clear();
-  P.wave_begin.assign(1, 0);
-  std::vector<int> cur;
-  std::vector<int> mark_r(P.n_slots + 1, -1), mark_w(P.n_slots + 1, -1);
-  int wave = 0;
-  auto flush = [&]() {
-    std::stable_sort(cur.begin(), cur.end(), [&](int a, int b) { return P.ops[a].type < P.ops[b].type; });
-    for (int i : cur) P.wave_ops.push_back((uint32_t)i);
-    P.wave_begin.push_back((int)P.wave_ops.size());
-    cur.clear();
-    ++wave;
-  };
-  for (int i = 0; i < (int)P.ops.size(); ++i) {
-    const Op& op = P.ops[i];
-    const bool writes = op.type <= OP_JIO;
-    bool conflict = (int)cur.size() >= kWaveMax;
-    for (int k = 0; k < op.n_in && !conflict; ++k)
-      if (mark_w[op.in[k]] == wave) conflict = true;
-    if (writes && (mark_r[op.out] == wave || mark_w[op.out] == wave)) conflict = true;
-    if (conflict) flush();
-    for (int k = 0; k < op.n_in; ++k) mark_r[op.in[k]] = wave;
-    if (writes) mark_w[op.out] = wave;
-    cur.push_back(i);
-  }
-  if (!cur.empty()) flush();
-  P.n_waves = (int)P.wave_begin.size() - 1;
-}
-
 Program build_program(const std::vector<int>& pdg) {
   Program P;
   Builder B;
@@ -1018,7 +982,6 @@ Program build_program(const std::vector<int>& pdg) {
     for (Op& op : P.ops)
       if (op.type >= OP_AVVV) op.out = d++;
   }
-  build_waves(P);
   {
     double f = 0;
     for (const Op& op : P.ops) f += op_flops(op.type) + ((op.type >= OP_AVVV) ? 4.0 * op.col_count : 0.0);

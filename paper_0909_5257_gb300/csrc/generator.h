@@ -85,10 +85,6 @@ struct Program {
   int n_hel = 0;
   std::vector<int8_t> hel_all;        // [2^n_ext][n_ext]
   double flops_per_hel = 0;
-  // cooperative schedule: ops of wave w are wave_ops[wave_begin[w] .. wave_begin[w+1])
-  std::vector<uint32_t> wave_ops;
-  std::vector<int> wave_begin;
-  int n_waves = 0;
   std::string basis_text;             // human-readable basis (debug)
 };
 
