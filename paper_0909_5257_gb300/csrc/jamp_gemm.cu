@@ -43,10 +43,12 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 256;  // 8 warps convert; warps 0..3 own TMEM lanes 0..127 in the epilogue
+constexpr int kThreads = 512;  // 16 warps convert; warps 0..3 own TMEM lanes 0..127 in the epilogue
+constexpr int kTileVec = kThreads >= 1024 ? 1 : 1024 / kThreads;  // 16-byte tile vectors per thread (nc <= 128)
 constexpr int kM = 128;
 constexpr int kKC = 64;
 constexpr int kStageA = kM * kKC * 2;  // one FP16 digit plane of A
+constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
 constexpr int kMaxNC = 128;            // 3 accumulators of nc columns in 512 TMEM columns; 4 tile vectors per thread
 
 __host__ __device__ constexpr size_t stage_bytes(int nc) { return (size_t)3 * kStageA + (size_t)nc * kKC * 2; }
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
     const int64_t r = row0 + row;
     const bool row_ok = r < n_rows;
     float pa[kKC / 8 / (kThreads / kM)][8];
-    uint4 pb[4];
+    uint4 pb[kTileVec];
     const int nb = NC * kKC / 8;  // 16-byte vectors per coefficient tile
     auto prefetch = [&](int kc) {
 #pragma unroll
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
       }
       const uint4* src = reinterpret_cast<const uint4*>(g.tiles + ((size_t)split * n_kc + kc) * NC * kKC);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < kTileVec; ++j) {
         const int i = t + j * kThreads;
         if (i < nb) pb[j] = __ldg(src + i);
       }
@@ -170,11 +172,14 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
             float h[2], mm[2], l[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
+              // round to the nearest integer by adding and removing 1.5 * 2^23
+              // (exact for |x| < 2^22; here |x| <= 2^12), on the FMA pipe
               const float x = __fmul_rn(pa[j][i + u], sc);
-              h[u] = rintf(x);
+              h[u] = __fsub_rn(__fadd_rn(x, kRoundMagic), kRoundMagic);
               const float r1 = __fmul_rn(__fsub_rn(x, h[u]), w1);
-              mm[u] = rintf(r1);
-              l[u] = rintf(__fmul_rn(__fsub_rn(r1, mm[u]), w1));
+              mm[u] = __fsub_rn(__fadd_rn(r1, kRoundMagic), kRoundMagic);
+              const float r2 = __fmul_rn(__fsub_rn(r1, mm[u]), w1);
+              l[u] = __fsub_rn(__fadd_rn(r2, kRoundMagic), kRoundMagic);
             }
             // integers of at most 2^q <= 2048 in magnitude: exact in FP16
             hv[i / 2] = __floats2half2_rn(h[0], h[1]);
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
       {
         uint4* dst = reinterpret_cast<uint4*>(b_t);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kTileVec; ++j) {
           const int i = t + j * kThreads;
           if (i < nb) dst[i] = pb[j];
         }
