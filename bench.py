@@ -519,8 +519,8 @@ def main():
     e2e = None
     if rank == 0 or ws > 1:
         host = [m.cpu().numpy() for m in moms]
-        for P, h in zip(procs, host):
-            P.evaluate_host(h[: 1 << 12], precision=mea.PREC_MIXED)
+        for P, h in zip(procs, host):  # warm-up at full size: sizes the pinned staging buffers
+            P.evaluate_host(h, precision=mea.PREC_MIXED)
         barrier()
         t0 = time.perf_counter()
         e2e_steps = max(1, min(args.steps, 3))

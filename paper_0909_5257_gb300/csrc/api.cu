@@ -113,7 +113,7 @@ int64_t tc_chunk_events(const mea_process_s* P, int H, int64_t n) {
 
 // Launch configuration of the amplitude-output interpreter for H lanes per event.
 mea::AmpConfig tc_amp_config(const mea_process_s* P, const mea::DevProgram& dp, int H, int64_t cn) {
-  mea::AmpConfig c = mea::plan_amp(dp, false, H, cn, P->num_sms, P->smem_optin, P->smem_per_sm);
+  mea::AmpConfig c = mea::cached_plan(const_cast<mea_process_s*>(P), dp, false, true, H, cn);
   if (P->tuned[0].grid > 0 && P->tuned_H[0] == H) {  // configuration chosen by mea_autotune
     c = P->tuned[0];
     int64_t tiles = (cn + c.E_cta - 1) / c.E_cta;
@@ -205,7 +205,7 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
                                 reinterpret_cast<const float*>(S.pairk.p), s,
                                 reinterpret_cast<const float*>(S.jabs.p), JM.n_splits));
     if (reeval) {
-      mea::AmpConfig c2 = mea::plan_amp(P->dev, true, H, cn, P->num_sms, P->smem_optin, P->smem_per_sm);
+      mea::AmpConfig c2 = mea::cached_plan(P, P->dev, true, false, H, cn);
       mea::AmpLaunch b = f;
       b.event_list = f.flag_list;
       b.list_count = f.flag_count;
@@ -247,7 +247,7 @@ mea_status do_evaluate(mea_process_s* P, mea::EvalScratch& S, const double* mom,
   const mea::Program& G = P->prog;
   int H = (hm == MEA_HEL_SUM_NONZERO) ? G.n_hel : (hm == MEA_HEL_SUM_ALL ? (1 << G.n_ext) : 1);
   bool fp64 = prec == MEA_PREC_FP64;
-  mea::AmpConfig c = mea::plan_amp(P->dev, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
+  mea::AmpConfig c = mea::cached_plan(P, P->dev, fp64, false, H, n);
   const int ti = fp64 ? 1 : 0;
   if (P->tuned[ti].grid > 0 && P->tuned_H[ti] == H) {  // configuration chosen by mea_autotune
     c = P->tuned[ti];
@@ -274,7 +274,7 @@ mea_status do_evaluate(mea_process_s* P, mea::EvalScratch& S, const double* mom,
   MEA_CUDA(mea::launch_amp(P->dev, fp64, c, a, s));
   if (reeval) {
     // FP64 re-evaluation of the flagged events; their count is read on the device
-    mea::AmpConfig c2 = mea::plan_amp(P->dev, true, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
+    mea::AmpConfig c2 = mea::cached_plan(P, P->dev, true, false, H, n);
     mea::AmpLaunch b = a;
     b.event_list = a.flag_list;
     b.list_count = a.flag_count;
@@ -291,6 +291,22 @@ mea_status do_evaluate(mea_process_s* P, mea::EvalScratch& S, const double* mom,
 
 namespace mea {
 mea_status set_error(mea_status s, const std::string& msg) { return fail(s, msg); }
+
+AmpConfig cached_plan(mea_process_s* P, const DevProgram& dp, bool fp64, bool tc, int H, int64_t n) {
+  AmpConfig c;
+  {
+    std::lock_guard<std::mutex> lk(P->plan_mu);
+    auto key = std::make_tuple(fp64, tc, H);
+    auto it = P->plan_cache.find(key);
+    if (it == P->plan_cache.end())
+      it = P->plan_cache.emplace(key, plan_amp(dp, fp64, H, (int64_t)1 << 40, P->num_sms, P->smem_optin,
+                                               P->smem_per_sm)).first;
+    c = it->second;
+  }
+  const int64_t tiles = (n + c.E_cta - 1) / c.E_cta;
+  if (tiles < c.grid) c.grid = (int)std::max<int64_t>(tiles, 1);
+  return c;
+}
 bool uses_tensor_path(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode hm) {
   return use_tensor_colour(P, prec, hm);
 }
@@ -582,7 +598,7 @@ mea_status mea_evaluate_host(mea_process_t P, const double* mom_h, int64_t n, me
   if (!mom_h || !me2_h) return fail(MEA_E_ARG, "mea_evaluate_host: null buffer");
   std::lock_guard<std::mutex> lk(P->mu);
   const int n_ext = P->prog.n_ext;
-  const int64_t chunk = std::min<int64_t>(n, 1 << 17);
+  const int64_t chunk = std::min<int64_t>(n, 1 << 18);
   if (P->pipe_chunk < chunk) {
     for (int i = 0; i < 2; ++i) {
       if (P->pin_in[i]) cudaFreeHost(P->pin_in[i]);
@@ -674,8 +690,8 @@ mea_status mea_evaluate_noalloc(mea_process_t P, const double* mom, int64_t n, m
   const int H = G.n_hel;
   const bool fp64 = prec == MEA_PREC_FP64;
   const bool reeval = !fp64 && P->opts.reeval_fp64;
-  mea::AmpConfig c = mea::plan_amp(P->dev, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
-  mea::AmpConfig c2 = mea::plan_amp(P->dev, true, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
+  mea::AmpConfig c = mea::cached_plan(P, P->dev, fp64, false, H, n);
+  mea::AmpConfig c2 = mea::cached_plan(P, P->dev, true, false, H, n);
   auto work_bytes = [&](bool f64, const mea::AmpConfig& cc) {
     size_t jb = (mea::jamp_scratch_bytes_needed(P->dev, f64, cc) + 255) & ~size_t(255);
     return jb + ((mea::slot_scratch_bytes_needed(P->dev, f64, cc) + 255) & ~size_t(255));

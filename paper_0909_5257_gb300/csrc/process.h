@@ -4,7 +4,9 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -64,6 +66,10 @@ struct mea_process_s {
   mea::AmpConfig tuned[2];
   int tuned_H[2] = {0, 0};
   bool auto_tuned[2] = {false, false};  // tuned once already (explicitly or on first large evaluation)
+  // heuristic launch plans, computed once per (FP64?, tensor path?, H) with an
+  // unbounded event count; each call only caps the grid by its tiles
+  std::map<std::tuple<bool, bool, int>, mea::AmpConfig> plan_cache;
+  std::mutex plan_mu;
   // status word of the bounded device waits
   const __half* cf_hi = nullptr;   // colour matrix operand tiles (colour_gemm.h ColourTiles)
   const __half* cf_lo = nullptr;
@@ -93,6 +99,9 @@ bool uses_tensor_path(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode h
 // mea_autotune with the process lock already held.
 mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_prec_mode prec, double* me2,
                            mea_tune_result* out);
+// Heuristic launch plan of this process for n events (cached per precision,
+// path and helicity count); dp is P->dev or its tensor-path copy.
+AmpConfig cached_plan(mea_process_s* P, const DevProgram& dp, bool fp64, bool tc, int H, int64_t n);
 // Device scratch bytes an evaluation of n events would hold (admission control).
 size_t scratch_estimate(mea_process_s* P, int64_t n, mea_prec_mode prec);
 }  // namespace mea
