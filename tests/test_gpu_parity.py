@@ -372,3 +372,25 @@ def test_bounded_wait_timeout_is_reported_and_the_context_survives():
     got, _ = _run(pdg, mom, mea.PREC_MIXED)
     P.check_status()
     assert np.median(np.abs(got / ref - 1.0)) <= 1e-6
+
+
+@pytest.mark.parametrize("pdg,nf", [([2, 2, 2, 2, 21], 3), ([21] * 6, 4)])
+def test_host_pipeline_across_chunks_equals_device_path(pdg, nf):
+    """mea_evaluate_host stages through pinned buffers in chunks of 2^18 events
+    on two streams; across several chunks (and a ragged last one) and a second
+    call that reuses the buffers, every result and flag equals the
+    device-resident evaluation bit for bit (straight-line and tensor-core
+    paths)."""
+    mea = _mea()
+    n = (1 << 18) * 2 + 12345 if nf == 3 else 3001
+    P = _proc(pdg)
+    d_mom = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
+    mea.generate_phase_space(nf, n, d_mom, seed=ps.SEED_BASE + 401, rs_lo=300.0, rs_hi=3000.0)
+    ref = torch.empty(n, dtype=torch.float64, device="cuda")
+    rfl = torch.empty(n, dtype=torch.uint8, device="cuda")
+    P.evaluate(d_mom, ref, precision=mea.PREC_MIXED, flags=rfl)
+    h = d_mom.cpu().numpy()
+    for _ in range(2):
+        got, fl = P.evaluate_host(h, precision=mea.PREC_MIXED, with_flags=True)
+        assert np.array_equal(got, ref.cpu().numpy())
+        assert np.array_equal(fl, rfl.cpu().numpy())
