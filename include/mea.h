@@ -321,6 +321,32 @@ typedef struct {
 mea_status mea_generate_phase_space(const mea_ps_config *cfg, uint64_t first_event, int64_t n,
                                     double *momenta_dev, int32_t *attempts_dev, void *stream);
 
+/* ---- partonic cross section ------------------------------------------------ *
+ * sigma_hat(s_hat) = 1/(2 s_hat) * S * integral over the cut region of
+ * dPhi_n |M|^2, with |M|^2 as mea_evaluate returns it (initial helicities and
+ * colours averaged), S = 1 / prod k! over identical final-state partons, and
+ * the Lorentz-invariant n-body phase space of massless partons,
+ * Phi_n(s) = (2 pi)^(4-3n) (pi/2)^(n-1) s^(n-2) / ((n-1)! (n-2)!).
+ * Estimated at fixed sqrt(s_hat) by the seeded generator (flat RAMBO points,
+ * cut points redrawn): sigma = 1/(2 s) S Phi_n sum_accepted |M|^2 / (points
+ * drawn), error from the variance over all drawn points (rejected ones count
+ * 0).  Events first_event .. first_event + n_events - 1 of the generator with
+ * rs_lo = rs_hi = sqrt_s; device work in chunks on an internal stream;
+ * synchronous.  Result in pb (1 GeV^-2 = 0.3893794e9 pb).  MEA_E_ARG for bad
+ * arguments; the generator's config must have n_final = n_ext - 2. */
+typedef struct {
+  double sigma_pb;       /* estimate */
+  double error_pb;       /* one standard deviation, statistical */
+  int64_t n_accepted;    /* events evaluated */
+  int64_t n_drawn;       /* phase-space points drawn (accepted + rejected) */
+  double phase_space;    /* Phi_n(s_hat), GeV^(2n-4) */
+  double symmetry;       /* S */
+} mea_xsec_result;
+
+mea_status mea_partonic_cross_section(mea_process_t proc, double sqrt_s, const mea_ps_config *cuts,
+                                      uint64_t first_event, int64_t n_events, mea_prec_mode prec,
+                                      mea_xsec_result *out);
+
 /* ---- diagnostics ------------------------------------------------------------ */
 
 const char *mea_last_error(void);

@@ -225,7 +225,6 @@ __device__ __forceinline__ void tile_finish(const AmpLaunch& A, int t, int E, in
           double v = res[t * H + hh];
           s += v;
           wk += v * (double)kap[t * H + hh];
-          if (A.pair_out) A.pair_out[gev * H + hh] = v;
         }
         double me = 0.25 * s;
         A.me2[gev] = me;

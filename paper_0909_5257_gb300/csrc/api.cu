@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <stdexcept>
@@ -751,6 +752,84 @@ mea_status mea_generate_phase_space(const mea_ps_config* cfg, uint64_t first_eve
   if (!mom) return fail(MEA_E_ARG, "mea_generate_phase_space: null momenta");
   mea::PsConfigDev c{cfg->seed, cfg->n_final, cfg->rs_lo, cfg->rs_hi, cfg->pt_min, cfg->eta_max, cfg->dr_min};
   MEA_CUDA(mea::launch_phase_space(c, first_event, n, mom, attempts, reinterpret_cast<cudaStream_t>(stream)));
+  return MEA_OK;
+}
+
+mea_status mea_partonic_cross_section(mea_process_t P, double sqrt_s, const mea_ps_config* cuts,
+                                      uint64_t first_event, int64_t n, mea_prec_mode prec, mea_xsec_result* out) {
+  if (!P || !cuts || !out || n <= 0 || !(sqrt_s > 0) || !std::isfinite(sqrt_s))
+    return fail(MEA_E_ARG, "mea_partonic_cross_section: bad arguments");
+  if (P->host_only) return fail(MEA_E_UNSUPPORTED, "mea_partonic_cross_section: host-only process handle");
+  if (prec != MEA_PREC_FP64 && prec != MEA_PREC_MIXED) return fail(MEA_E_ARG, "mea_partonic_cross_section: bad precision");
+  const mea::Program& G = P->prog;
+  const int n_ext = G.n_ext, nf = n_ext - 2;
+  if (cuts->n_final != nf) return fail(MEA_E_ARG, "mea_partonic_cross_section: cuts->n_final != n_ext - 2");
+  // Phi_n(s) = (2 pi)^(4-3n) (pi/2)^(n-1) s^(n-2) / ((n-1)! (n-2)!), symmetry 1/prod k!
+  const double s_hat = sqrt_s * sqrt_s;
+  double fact_n1 = 1.0, fact_n2 = 1.0;
+  for (int k = 2; k <= nf - 1; ++k) fact_n1 *= k;
+  for (int k = 2; k <= nf - 2; ++k) fact_n2 *= k;
+  const double phi = std::pow(2.0 * M_PI, 4.0 - 3.0 * nf) * std::pow(M_PI / 2.0, nf - 1) * std::pow(s_hat, nf - 2) /
+                     (fact_n1 * fact_n2);
+  std::map<int, int> count;
+  for (int l = 2; l < n_ext; ++l) count[G.pdg[l]]++;
+  double sym = 1.0;
+  for (auto& kv : count)
+    for (int k = 2; k <= kv.second; ++k) sym /= k;
+  const int64_t chunk = std::min<int64_t>(n, 1 << 20);
+  constexpr int kBlocks = 256;
+  mea::DevBuf mom, me2, att, pf, pf2, pa;
+  MEA_CUDA(mom.ensure(sizeof(double) * 4 * n_ext * chunk));
+  MEA_CUDA(me2.ensure(sizeof(double) * chunk));
+  MEA_CUDA(att.ensure(sizeof(int32_t) * chunk));
+  MEA_CUDA(pf.ensure(sizeof(double) * kBlocks));
+  MEA_CUDA(pf2.ensure(sizeof(double) * kBlocks));
+  MEA_CUDA(pa.ensure(sizeof(long long) * 2 * kBlocks));
+  cudaStream_t s;
+  MEA_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  mea::PsConfigDev c{cuts->seed, nf, sqrt_s, sqrt_s, cuts->pt_min, cuts->eta_max, cuts->dr_min};
+  double sum_f = 0.0, sum_f2 = 0.0;
+  long long drawn = 0, accepted = 0;
+  std::vector<double> hf(kBlocks), hf2(kBlocks);
+  std::vector<long long> ha(2 * kBlocks);
+  mea_status st = MEA_OK;
+  {
+    std::lock_guard<std::mutex> lk(P->mu);
+    for (int64_t c0 = 0; c0 < n && st == MEA_OK; c0 += chunk) {
+      const int64_t cn = std::min(chunk, n - c0);
+      cudaError_t e = mea::launch_phase_space(c, first_event + (uint64_t)c0, cn, reinterpret_cast<double*>(mom.p),
+                                              reinterpret_cast<int32_t*>(att.p), s);
+      if (e != cudaSuccess) { st = fail(MEA_E_CUDA, cudaGetErrorString(e)); break; }
+      st = do_evaluate(P, P->scr[0], reinterpret_cast<const double*>(mom.p), cn, MEA_HEL_SUM_NONZERO, nullptr, prec,
+                       reinterpret_cast<double*>(me2.p), nullptr, s);
+      if (st != MEA_OK) break;
+      e = mea::launch_xsec_sums(reinterpret_cast<const double*>(me2.p), reinterpret_cast<const int32_t*>(att.p), cn,
+                                reinterpret_cast<double*>(pf.p), reinterpret_cast<double*>(pf2.p),
+                                reinterpret_cast<long long*>(pa.p), kBlocks, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(hf.data(), pf.p, sizeof(double) * kBlocks, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(hf2.data(), pf2.p, sizeof(double) * kBlocks, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ha.data(), pa.p, sizeof(long long) * 2 * kBlocks, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) { st = fail(MEA_E_CUDA, cudaGetErrorString(e)); break; }
+      for (int b = 0; b < kBlocks; ++b) {
+        sum_f += hf[b];
+        sum_f2 += hf2[b];
+        drawn += ha[2 * b];
+        accepted += ha[2 * b + 1];
+      }
+    }
+  }
+  cudaStreamDestroy(s);
+  if (st != MEA_OK) return st;
+  const double pre = sym * phi / (2.0 * s_hat) * 0.3893794e9;
+  const double mean = sum_f / (double)drawn;
+  const double var = std::max(0.0, sum_f2 / (double)drawn - mean * mean);
+  out->sigma_pb = pre * mean;
+  out->error_pb = pre * std::sqrt(var / (double)drawn);
+  out->n_accepted = accepted;
+  out->n_drawn = drawn;
+  out->phase_space = phi;
+  out->symmetry = sym;
   return MEA_OK;
 }
 

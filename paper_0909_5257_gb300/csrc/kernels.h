@@ -60,7 +60,6 @@ struct AmpLaunch {
   int write_flags_mode = 0;           // 0: write flags; 1: OR in MEA_FLAG_REEVALUATED (re-evaluation)
   int32_t* flag_list = nullptr;       // mixed path: indices of flagged events are appended here
   int32_t* flag_count = nullptr;
-  double* pair_out = nullptr;         // optional [event][H] per-helicity values (tests)
   float* pair_kappa = nullptr;        // per-pair indicator (see amp_out)
   uint8_t* ev_flags = nullptr;        // amplitude-output mode: per-event input-check bits out;
                                       //   finish_kernel ORs them into the flags
@@ -117,6 +116,10 @@ struct PsConfigDev {
 };
 cudaError_t launch_phase_space(const PsConfigDev& cfg, uint64_t first_event, int64_t n,
                                double* mom, int32_t* attempts, cudaStream_t s);
+// Per-block sums for the partonic cross section (blocks x 256 threads);
+// part_a[2b], part_a[2b+1] = points drawn, points accepted.
+cudaError_t launch_xsec_sums(const double* me2, const int32_t* att, int64_t n, double* part_f, double* part_f2,
+                             long long* part_a, int blocks, cudaStream_t s);
 
 uint64_t& launch_counter();
 

@@ -19,7 +19,54 @@ __global__ void ps_kernel(ps_config cfg, uint64_t first, int64_t n, double* mom,
   if (att) att[i] = a;
 }
 
+// Partonic cross-section sums over a chunk: per block, in a fixed order, the
+// sums of f and f^2 with f = me2 for accepted points (attempt index >= 0) and
+// 0 otherwise, and the number of phase-space points drawn (attempt index + 1,
+// or all PS_MAX_ATTEMPTS when none was accepted) and of accepted points;
+// part_a holds (drawn, accepted) pairs.
+__global__ void xsec_sum_kernel(const double* me2, const int32_t* att, int64_t n, double* part_f,
+                                double* part_f2, long long* part_a) {
+  __shared__ double sf[256], sf2[256];
+  __shared__ long long sa[256], sn[256];
+  const int t = threadIdx.x;
+  double f = 0.0, f2 = 0.0;
+  long long a = 0, acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + t; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = att[i];
+    if (k >= 0) {
+      const double v = me2[i];
+      f += v;
+      f2 += v * v;
+      a += k + 1;
+      ++acc;
+    } else {
+      a += PS_MAX_ATTEMPTS;
+    }
+  }
+  sf[t] = f; sf2[t] = f2; sa[t] = a; sn[t] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (t < w) { sf[t] += sf[t + w]; sf2[t] += sf2[t + w]; sa[t] += sa[t + w]; sn[t] += sn[t + w]; }
+    __syncthreads();
+  }
+  if (t == 0) {
+    part_f[blockIdx.x] = sf[0];
+    part_f2[blockIdx.x] = sf2[0];
+    part_a[2 * blockIdx.x] = sa[0];
+    part_a[2 * blockIdx.x + 1] = sn[0];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_xsec_sums(const double* me2, const int32_t* att, int64_t n, double* part_f, double* part_f2,
+                             long long* part_a, int blocks, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  xsec_sum_kernel<<<blocks, 256, 0, s>>>(me2, att, n, part_f, part_f2, part_a);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) ++launch_counter();
+  return e;
+}
 
 cudaError_t launch_phase_space(const PsConfigDev& c, uint64_t first_event, int64_t n, double* mom,
                                int32_t* attempts, cudaStream_t s) {

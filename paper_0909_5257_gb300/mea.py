@@ -96,6 +96,7 @@ def load(path: str | None = None):
             lib.mea_evaluate_host.argtypes = [vp, vp, i64, i32, vp, vp]
             lib.mea_evaluate_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp]
             lib.mea_generate_phase_space.argtypes = [vp, ctypes.c_uint64, i64, vp, vp, vp]
+            lib.mea_partonic_cross_section.argtypes = [vp, ctypes.c_double, vp, ctypes.c_uint64, i64, i32, vp]
             lib.mea_autotune.argtypes = [vp, vp, i64, i32, vp, vp]
             lib.mea_batch_create.argtypes = [vp, i32, i32, vp]
             lib.mea_batch_launch.argtypes = [vp, vp]
@@ -235,6 +236,17 @@ class Process:
         _check(load().mea_evaluate_noalloc(self._h, _ptr(momenta), n_events, precision, _ptr(me2),
                                            _ptr(flags), _stream(stream)))
 
+    def partonic_cross_section(self, sqrt_s, n_events, seed=0x09095257, first_event=0, pt_min=20.0,
+                               eta_max=2.5, dr_min=0.4, precision=PREC_FP64):
+        """sigma_hat at fixed sqrt(s_hat) in pb with its statistical error
+        (mea_partonic_cross_section): generator events first_event .. + n_events."""
+        cfg = PsConfig(seed, self.n_ext - 2, sqrt_s, sqrt_s, pt_min, eta_max, dr_min)
+        r = XsecResult()
+        _check(load().mea_partonic_cross_section(self._h, ctypes.c_double(sqrt_s), ctypes.byref(cfg),
+                                                 ctypes.c_uint64(first_event), n_events, precision,
+                                                 ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _ in XsecResult._fields_}
+
     def evaluate_host(self, momenta: np.ndarray, precision=PREC_MIXED, with_flags=False):
         """|M|^2 of host momenta through the library's pinned, pipelined copies."""
         mom = np.ascontiguousarray(momenta, dtype=np.float64)
@@ -251,6 +263,11 @@ def generate_phase_space(n_final, n, momenta, first_event=0, seed=0x09095257, rs
     cfg = PsConfig(seed, n_final, rs_lo, rs_hi, pt_min, eta_max, dr_min)
     _check(load().mea_generate_phase_space(ctypes.byref(cfg), first_event, n, _ptr(momenta),
                                            _ptr(attempts), _stream(stream)))
+
+
+class XsecResult(ctypes.Structure):
+    _fields_ = [("sigma_pb", ctypes.c_double), ("error_pb", ctypes.c_double), ("n_accepted", ctypes.c_int64),
+                ("n_drawn", ctypes.c_int64), ("phase_space", ctypes.c_double), ("symmetry", ctypes.c_double)]
 
 
 class Batch:
