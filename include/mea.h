@@ -178,10 +178,12 @@ mea_status mea_evaluate(mea_process_t proc, const double *momenta_dev, int64_t n
                         double *me2_dev, uint8_t *flags_dev, void *stream);
 
 /* Same result through host buffers: momenta_host[n_events][n_ext][4] and
- * me2_host[n_events] (flags_host nullable) are ordinary host memory.  The
- * library stages them through its own pinned buffers in chunks, overlapping
- * copies with compute on two streams, and returns when me2_host is filled
- * (synchronous). */
+ * me2_host[n_events] (flags_host nullable) are host memory.  The library
+ * works in chunks, overlapping copies with compute on two streams, and
+ * returns when me2_host is filled (synchronous).  A buffer that is
+ * page-locked over its whole extent (cudaHostAlloc, cudaHostRegister, a
+ * pinned PyTorch tensor) is copied to or from the device directly; pageable
+ * memory goes through the library's own pinned staging buffers. */
 mea_status mea_evaluate_host(mea_process_t proc, const double *momenta_host, int64_t n_events,
                              mea_prec_mode prec, double *me2_host, uint8_t *flags_host);
 

@@ -586,6 +586,21 @@ void host_copy(void* dst, const void* src, size_t bytes) {
       std::memcpy(static_cast<char*>(dst) + b0, static_cast<const char*>(src) + b0, std::min(part, bytes - b0));
   }
 }
+// True when [p, p + bytes) starts and ends in page-locked host memory, so the
+// DMA engines can read or write it without a staging copy.
+bool page_locked(const void* p, size_t bytes) {
+  if (!p || bytes == 0) return false;
+  const void* ends[2] = {p, static_cast<const char*>(p) + bytes - 1};
+  for (const void* q : ends) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (at.type != cudaMemoryTypeHost) return false;
+  }
+  return true;
+}
 }  // namespace
 
 extern "C" {
@@ -618,14 +633,18 @@ mea_status mea_evaluate_host(mea_process_t P, const double* mom_h, int64_t n, me
     P->pipe_chunk = chunk;
   }
   const int64_t n_chunks = (n + chunk - 1) / chunk;
+  // page-locked caller buffers are read and written by the copy engines directly
+  const bool in_direct = page_locked(mom_h, sizeof(double) * 4 * n_ext * (size_t)n);
+  const bool out_direct = page_locked(me2_h, sizeof(double) * (size_t)n);
+  const bool fl_direct = flags_h && page_locked(flags_h, (size_t)n);
   int64_t pending[2] = {-1, -1};
   auto drain = [&](int b) -> mea_status {
     if (pending[b] < 0) return MEA_OK;
     MEA_CUDA(cudaEventSynchronize(P->done[b]));
     int64_t c0 = pending[b] * chunk;
     int64_t cn = std::min(chunk, n - c0);
-    host_copy(me2_h + c0, P->pin_out[b], sizeof(double) * cn);
-    if (flags_h) host_copy(flags_h + c0, P->pin_flags[b], cn);
+    if (!out_direct) host_copy(me2_h + c0, P->pin_out[b], sizeof(double) * cn);
+    if (flags_h && !fl_direct) host_copy(flags_h + c0, P->pin_flags[b], cn);
     pending[b] = -1;
     return MEA_OK;
   };
@@ -634,14 +653,20 @@ mea_status mea_evaluate_host(mea_process_t P, const double* mom_h, int64_t n, me
     mea_status s = drain(b);
     if (s != MEA_OK) return s;
     int64_t c0 = k * chunk, cn = std::min(chunk, n - c0);
-    host_copy(P->pin_in[b], mom_h + (size_t)c0 * n_ext * 4, sizeof(double) * 4 * n_ext * cn);
-    MEA_CUDA(cudaMemcpyAsync(P->d_in[b].p, P->pin_in[b], sizeof(double) * 4 * n_ext * cn,
-                             cudaMemcpyHostToDevice, P->st[b]));
+    const double* src = mom_h + (size_t)c0 * n_ext * 4;
+    if (!in_direct) {
+      host_copy(P->pin_in[b], src, sizeof(double) * 4 * n_ext * cn);
+      src = static_cast<const double*>(P->pin_in[b]);
+    }
+    MEA_CUDA(cudaMemcpyAsync(P->d_in[b].p, src, sizeof(double) * 4 * n_ext * cn, cudaMemcpyHostToDevice, P->st[b]));
     s = do_evaluate(P, P->scr[1 + b], reinterpret_cast<const double*>(P->d_in[b].p), cn, MEA_HEL_SUM_NONZERO, nullptr, prec,
                     reinterpret_cast<double*>(P->d_out[b].p), reinterpret_cast<uint8_t*>(P->d_flags[b].p), P->st[b]);
     if (s != MEA_OK) return s;
-    MEA_CUDA(cudaMemcpyAsync(P->pin_out[b], P->d_out[b].p, sizeof(double) * cn, cudaMemcpyDeviceToHost, P->st[b]));
-    MEA_CUDA(cudaMemcpyAsync(P->pin_flags[b], P->d_flags[b].p, cn, cudaMemcpyDeviceToHost, P->st[b]));
+    MEA_CUDA(cudaMemcpyAsync(out_direct ? me2_h + c0 : P->pin_out[b], P->d_out[b].p, sizeof(double) * cn,
+                             cudaMemcpyDeviceToHost, P->st[b]));
+    if (flags_h)
+      MEA_CUDA(cudaMemcpyAsync(fl_direct ? flags_h + c0 : P->pin_flags[b], P->d_flags[b].p, cn, cudaMemcpyDeviceToHost,
+                               P->st[b]));
     MEA_CUDA(cudaEventRecord(P->done[b], P->st[b]));
     pending[b] = k;
   }

@@ -247,12 +247,24 @@ class Process:
                                                  ctypes.byref(r)))
         return {k: getattr(r, k) for k, _ in XsecResult._fields_}
 
-    def evaluate_host(self, momenta: np.ndarray, precision=PREC_MIXED, with_flags=False):
-        """|M|^2 of host momenta through the library's pinned, pipelined copies."""
+    def evaluate_host(self, momenta: np.ndarray, precision=PREC_MIXED, with_flags=False, out=None, flags=None):
+        """|M|^2 of host momenta through the library's pipelined copies.
+
+        out / flags: optional host arrays (float64[n] / uint8[n]) to fill; page-locked
+        arrays (e.g. from a pinned torch tensor) are copied to and from the device
+        directly, pageable ones through the library's staging buffers."""
         mom = np.ascontiguousarray(momenta, dtype=np.float64)
         n = mom.shape[0]
-        out = np.zeros(n, dtype=np.float64)
-        fl = np.zeros(n, dtype=np.uint8) if with_flags else None
+        if out is None:
+            out = np.zeros(n, dtype=np.float64)
+        if out.dtype != np.float64 or out.shape != (n,) or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous float64 array of n_events")
+        fl = flags
+        if fl is None and with_flags:
+            fl = np.zeros(n, dtype=np.uint8)
+        if fl is not None and (fl.dtype != np.uint8 or fl.shape != (n,) or not fl.flags.c_contiguous):
+            raise ValueError("flags must be a contiguous uint8 array of n_events")
+        with_flags = with_flags or flags is not None
         _check(load().mea_evaluate_host(self._h, _ptr(mom), n, precision, _ptr(out), _ptr(fl)))
         return (out, fl) if with_flags else out
 

@@ -376,8 +376,8 @@ def test_bounded_wait_timeout_is_reported_and_the_context_survives():
 
 @pytest.mark.parametrize("pdg,nf", [([2, 2, 2, 2, 21], 3), ([21] * 6, 4)])
 def test_host_pipeline_across_chunks_equals_device_path(pdg, nf):
-    """mea_evaluate_host stages through pinned buffers in chunks of 2^18 events
-    on two streams; across several chunks (and a ragged last one) and a second
+    """mea_evaluate_host works in chunks of 2^18 events on two streams, staging
+    pageable buffers and copying page-locked ones directly; across several chunks (and a ragged last one) and a second
     call that reuses the buffers, every result and flag equals the
     device-resident evaluation bit for bit (straight-line and tensor-core
     paths)."""
@@ -394,3 +394,14 @@ def test_host_pipeline_across_chunks_equals_device_path(pdg, nf):
         got, fl = P.evaluate_host(h, precision=mea.PREC_MIXED, with_flags=True)
         assert np.array_equal(got, ref.cpu().numpy())
         assert np.array_equal(fl, rfl.cpu().numpy())
+    # page-locked input and outputs: copied by the DMA engines without staging
+    hp = d_mom.cpu().pin_memory().numpy()
+    out = torch.full((n,), -1.0, dtype=torch.float64).pin_memory().numpy()
+    fl = torch.full((n,), 0xEE, dtype=torch.uint8).pin_memory().numpy()
+    got, fl2 = P.evaluate_host(hp, precision=mea.PREC_MIXED, out=out, flags=fl)
+    assert got is out and fl2 is fl
+    assert np.array_equal(out, ref.cpu().numpy())
+    assert np.array_equal(fl, rfl.cpu().numpy())
+    # pinned momenta, pageable results (mixed placement)
+    got = P.evaluate_host(hp, precision=mea.PREC_MIXED)
+    assert np.array_equal(got, ref.cpu().numpy())
