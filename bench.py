@@ -496,7 +496,13 @@ def main():
 
     # roofline of the dominant kernel: the fused amplitude + colour kernel of the
     # most expensive subprocess, FP32 pipe (ALU-bound), algorithmic FLOPs per launch
-    cost = [procs[i].info["n_hel_nonzero"] * (procs[i].info["flops_per_hel"] + procs[i].info["colour_flops_per_hel"])
+    # FLOPs of the straight-line body the tuner chose: with the shared vertex
+    # partials, or one vertex call per diagram (flops_per_hel_plain)
+    def body_flops(i):
+        name = subs[i][0]
+        plain = name in tuned and not tuned[name]["mixed"].get("vertex_partials", 1)
+        return procs[i].info["flops_per_hel_plain" if plain else "flops_per_hel"]
+    cost = [procs[i].info["n_hel_nonzero"] * (body_flops(i) + procs[i].info["colour_flops_per_hel"])
             for i in range(len(procs))]
     dom = int(np.argmax([c * statistics.median(per_mixed[i]) for i, c in enumerate(cost)]))
     ms_dom = statistics.mean(per_mixed[dom])
@@ -558,7 +564,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload], "events_per_subprocess_per_gpu": n,
                    "l2": "inputs larger than L2 (no flush)", "alpha_s": 0.118,
-                   "autotuned": {k: {pn: {kk: v[pn][kk] for kk in ("threads", "events_per_cta", "register_cap")}
+                   "autotuned": {k: {pn: {kk: v[pn][kk] for kk in ("threads", "events_per_cta", "register_cap", "vertex_partials")}
                                      for pn in v} for k, v in tuned.items()}},
         "per_subprocess": per_sub,
         "fp64": fp64,

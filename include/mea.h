@@ -120,9 +120,12 @@ typedef struct {
   int64_t cf_denominator; /* N = K / cf_denominator with K integer */
   int64_t cf_max_abs_numerator; /* max |K| */
   double flops_per_hel;   /* algorithmic FLOPs of the amplitude stage per
-                             (event, helicity): wavefunctions, vertices,
-                             currents and colour-amplitude accumulation */
+                             (event, helicity): wavefunctions, vertices (with
+                             the shared vertex partials), currents and
+                             colour-amplitude accumulation */
   double colour_flops_per_hel; /* 4 n_colour_amplitudes^2: FLOPs of the colour quadratic form */
+  double flops_per_hel_plain;  /* flops_per_hel when every diagram amplitude is its own
+                                  vertex call (no shared vertex partials) */
 } mea_process_info_t;
 
 /* ---- process handles ---------------------------------------------------- */
@@ -206,6 +209,9 @@ typedef struct {
   double default_ms;     /* time of the heuristic default on the sample */
   int register_cap;      /* straight-line kernels: registers per thread of the
                             chosen variant (128 or 85); 0 for the interpreter */
+  int vertex_partials;   /* 1: diagrams sharing a vertex partial use it (always
+                            for the interpreter and FP64); 0: the straight-line
+                            body with one vertex call per diagram was faster */
 } mea_tune_result;
 
 mea_status mea_autotune(mea_process_t proc, const double *momenta_dev, int64_t n_sample,

@@ -167,6 +167,34 @@ __device__ __forceinline__ bool eval_op(const Op& op, const DevProgram& P, R* sl
       amp = iov_amp<R>(f, o, v, g);
       return true;
     }
+    case OP_ADOT: {  // diagram amplitude from its free wavefunction and the group's partial
+      W4<R> w = ld_slot(slots, op.in[0], L, t);
+      W4<R> p = ld_slot(slots, op.in[1], L, t);
+      amp = part_contract<R>(w, p, (op.leg & 1u) != 0, (op.leg & 2u) != 0);
+      return true;
+    }
+    case OP_PVVV: {
+      W4<R> b = ld_slot(slots, op.in[0], L, t);
+      W4<R> c = ld_slot(slots, op.in[1], L, t);
+      W4<R> u = vvv_part<R>(b, c, mt + 5 * op.min[0], mt + 5 * op.min[1], mt + 5 * op.min[2], g);
+      st_slot(slots, op.out, L, t, u);
+      return false;
+    }
+    case OP_PGGGG: {
+      W4<R> x = ld_slot(slots, op.in[0], L, t);
+      W4<R> y = ld_slot(slots, op.in[1], L, t);
+      W4<R> z = ld_slot(slots, op.in[2], L, t);
+      W4<R> u = gggg_part<R>(x, y, z, gg);
+      st_slot(slots, op.out, L, t, u);
+      return false;
+    }
+    case OP_PIOV: {  // free fi: (fo, V); free fo: (fi, V); free V: (fi, fo)
+      W4<R> a = ld_slot(slots, op.in[0], L, t);
+      W4<R> b = ld_slot(slots, op.in[1], L, t);
+      W4<R> u = op.leg == 0 ? iov_part_i<R>(a, b, g) : (op.leg == 1 ? iov_part_o<R>(a, b, g) : iov_part_v<R>(a, b, g));
+      st_slot(slots, op.out, L, t, u);
+      return false;
+    }
     default:
       return false;
   }

@@ -501,6 +501,7 @@ mea_status mea_process_info(mea_process_t P, mea_process_info_t* info) {
   info->n_colour_amplitudes = G.n_jamp;
   info->flops_per_hel = G.flops_per_hel;
   info->colour_flops_per_hel = 4.0 * (double)G.n_jamp * (double)G.n_jamp;
+  info->flops_per_hel_plain = G.flops_per_hel_plain;
   return MEA_OK;
 }
 

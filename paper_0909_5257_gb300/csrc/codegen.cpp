@@ -42,10 +42,10 @@ std::string lit(double v) {
   return "R(" + s + ")";
 }
 
-void emit_body(std::ostringstream& o, const mea::Program& P, const std::string& id) {
+void emit_body(std::ostringstream& o, const mea::Program& P, const std::string& name) {
   using namespace mea;
   const int m = P.n_jamp;  // colour amplitudes accumulated (folded for gluons)
-  o << "template <typename R>\nstruct Body_" << id << " {\n";
+  o << "template <typename R>\nstruct " << name << " {\n";
   o << "  static constexpr int kColour = " << m << ";\n";
   o << "  __device__ __forceinline__ static void run(const R* __restrict__ et, const R* __restrict__ mt,\n"
        "                                             uint32_t lam, R g, R gg, double inv_den, double& val,\n"
@@ -104,11 +104,26 @@ void emit_body(std::ostringstream& o, const mea::Program& P, const std::string& 
       case OP_JIO:
         o << "    const W4<R> " << w << " = jio<R>(" << in(0) << ", " << in(1) << ", " << minv(op.mout) << ", g);\n";
         break;
+      case OP_PVVV:
+        o << "    const W4<R> " << w << " = vvv_part<R>(" << in(0) << ", " << in(1) << ", " << mrow(op.min[0]) << ", "
+          << mrow(op.min[1]) << ", " << mrow(op.min[2]) << ", g);\n";
+        break;
+      case OP_PGGGG:
+        o << "    const W4<R> " << w << " = gggg_part<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", gg);\n";
+        break;
+      case OP_PIOV:
+        o << "    const W4<R> " << w << " = " << (op.leg == 0 ? "iov_part_i" : op.leg == 1 ? "iov_part_o" : "iov_part_v")
+          << "<R>(" << in(0) << ", " << in(1) << ", g);\n";
+        break;
       case OP_AVVV:
       case OP_AGGGG:
-      case OP_AIOV: {
+      case OP_AIOV:
+      case OP_ADOT: {
         o << "    {\n      const cx<R> a = ";
-        if (op.type == OP_AVVV)
+        if (op.type == OP_ADOT)
+          o << "part_contract<R>(" << in(0) << ", " << in(1) << ", " << ((op.leg & 1) ? "true" : "false") << ", "
+            << ((op.leg & 2) ? "true" : "false") << ");\n";
+        else if (op.type == OP_AVVV)
           o << "vvv_amp<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", " << mrow(op.min[0]) << ", "
             << mrow(op.min[1]) << ", " << mrow(op.min[2]) << ", g);\n";
         else if (op.type == OP_AGGGG)
@@ -140,7 +155,7 @@ void emit_body(std::ostringstream& o, const mea::Program& P, const std::string& 
       default:
         throw std::runtime_error("codegen: unknown op");
     }
-    if (op.type <= OP_JIO) slot_op[op.out] = (int)i;
+    if (!is_amp_op(op.type)) slot_op[op.out] = (int)i;
   }
   // colour quadratic form with the integer colour matrix (symmetric)
   o << "    cx<R> F[" << m << "];\n    float jabs = 0.f;\n";
@@ -187,16 +202,22 @@ int main(int argc, char** argv) {
       pdg.push_back(std::atoi(s.substr(pos, e - pos).c_str()));
       pos = e + 1;
     }
-    mea::Program P = mea::build_program(pdg);
+    // two bodies per process: with vertex partials and with one vertex call
+    // per diagram (fewer FLOPs against fewer live values; the tuner picks)
     std::string id = ident_of(pdg);
-    emit_body(o, P, id);
+    mea::BuildOptions with, without;
+    with.group_together = true;
+    without.vertex_partials = false;
+    emit_body(o, mea::build_program(pdg, with), "Body_" + id);
+    emit_body(o, mea::build_program(pdg, without), "BodyN_" + id);
     entries.push_back({key_of(pdg), id});
   }
   o << "}  // namespace\n\n";
   o << "const GenEntry* generated_table(int* n) {\n  static const GenEntry t[] = {\n";
-  for (auto& e : entries)
-    o << "    {\"" << e.first << "\", &gen_launch<Body_" << e.second << "<float>, Body_" << e.second
-      << "<double>>, &gen_kernel_for<Body_" << e.second << "<float>, Body_" << e.second << "<double>>},\n";
+  for (auto& e : entries) {
+    const std::string args = "Body_" + e.second + "<float>, BodyN_" + e.second + "<float>, Body_" + e.second + "<double>";
+    o << "    {\"" << e.first << "\", &gen_launch<" << args << ">, &gen_kernel_for<" << args << ">},\n";
+  }
   o << "  };\n  *n = " << entries.size() << ";\n  return t;\n}\n\n}  // namespace mea\n";
   FILE* f = std::fopen(argv[1], "w");
   if (!f) return 1;

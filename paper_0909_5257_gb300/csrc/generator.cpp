@@ -729,7 +729,7 @@ void fold_reflection(Builder& B, Program& P) {
   }
   const int sgn = (B.n % 2 == 0) ? 1 : -1;
   for (const Op& op : P.ops) {
-    if (op.type < OP_AVVV) continue;
+    if (!is_amp_op(op.type)) continue;
     std::map<int, std::pair<int, int>> c;
     for (uint32_t k = 0; k < op.col_count; ++k) {
       const ColEntry& e = P.col[op.col_begin + k];
@@ -758,7 +758,7 @@ void fold_reflection(Builder& B, Program& P) {
   // remap colour entries, dropping the reflected ones
   std::vector<ColEntry> col;
   for (Op& op : P.ops) {
-    if (op.type < OP_AVVV) continue;
+    if (!is_amp_op(op.type)) continue;
     uint32_t b = (uint32_t)col.size();
     for (uint32_t k = 0; k < op.col_count; ++k) {
       ColEntry e = P.col[op.col_begin + k];
@@ -817,7 +817,8 @@ bool helicity_allowed(const Builder& B, const std::vector<int>& lam) {
 // Algorithmic real-FLOP cost of each operation, counted from heget.cuh with
 // real add/sub/mul = 1, complex mul = 6, complex add = 2, real x complex = 2:
 // complex 4-vector dot = 30, real.complex dot = 14, slash(V) psi = 64,
-// slash(P) psi = 42.
+// slash(P) psi = 42.  Vertex partials: the ops that make them, and one
+// contraction (30) per diagram.
 double op_flops(int type) {
   switch (type) {
     case OP_EXT: return 12;
@@ -829,13 +830,18 @@ double op_flops(int type) {
     case OP_AVVV: return 204;
     case OP_AGGGG: return 136;
     case OP_AIOV: return 96;
+    case OP_ADOT: return 30;
+    case OP_PVVV: return 148;
+    case OP_PGGGG: return 120;
+    case OP_PIOV: return 72;  // fo slash(V) or slash(V) fi, scaled (the vector fo gamma fi: 128)
   }
   return 0;
 }
+double op_cost(const Op& op) { return (op.type == OP_PIOV && op.leg == 2) ? 128 : op_flops(op.type); }
 
 }  // namespace
 
-Program build_program(const std::vector<int>& pdg) {
+Program build_program(const std::vector<int>& pdg, const BuildOptions& opt) {
   Program P;
   Builder B;
   int n = (int)pdg.size();
@@ -877,32 +883,146 @@ Program build_program(const std::vector<int>& pdg) {
   P.n_diagrams = (int)B.amps.size();
   P.n_colour = B.n_colour;
 
-  // ---- schedule: amplitudes grouped by their largest current, currents on demand
-  int nn = (int)B.nodes.size();
-  std::vector<int> uses(nn, 0);
+  // ---- vertex partials.  Every amplitude vertex is linear in each input; an
+  // amplitude whose vertex shares all inputs but one with other amplitudes
+  // joins their group, which computes the partial vertex once (one op) and
+  // contracts it with each member's free input (one op per diagram).  Each
+  // amplitude takes, among its possible free inputs, the one whose shared
+  // remainder occurs most often; groups of one stay plain vertex calls.
+  struct Choice {
+    std::vector<int> key;   // {partial op, shared node ids..., free-input mask}
+    int free_k = -1;        // index of the free input in the amplitude's kids
+    bool neg = false;       // contraction negated (ggggxx orientation)
+  };
+  auto candidates = [&](const Amp& a) {
+    std::vector<Choice> out;
+    const std::vector<int>& x = a.kids;
+    if (a.type == OP_AVVV) {
+      for (int k = 0; k < 3; ++k) {  // cyclic shift: free x[k], shared (x[k+1], x[k+2])
+        int b = x[(k + 1) % 3], c = x[(k + 2) % 3];
+        out.push_back({{OP_PVVV, b, c, (int)B.nodes[x[k]]->mask}, k, false});
+      }
+    } else if (a.type == OP_AGGGG) {
+      // ggggxx(a,b,c,d) = a.G(b,c,d) = b.G(a,d,c) = c.G(d,a,b) = d.G(c,b,a), G(x,y,z) = -G(x,z,y)
+      static const int arg[4][3] = {{1, 2, 3}, {0, 3, 2}, {3, 0, 1}, {2, 1, 0}};
+      for (int k = 0; k < 4; ++k) {
+        int gx = x[arg[k][0]], gy = x[arg[k][1]], gz = x[arg[k][2]];
+        out.push_back({{OP_PGGGG, gx, std::min(gy, gz), std::max(gy, gz)}, k, gy > gz});
+      }
+    } else if (a.type == OP_AIOV) {  // kids (fi, fo, V)
+      out.push_back({{OP_PIOV, 0, x[1], x[2]}, 0, false});
+      out.push_back({{OP_PIOV, 1, x[0], x[2]}, 1, false});
+      out.push_back({{OP_PIOV, 2, x[0], x[1]}, 2, false});
+    }
+    return out;
+  };
+  const int n_amp = (int)B.amps.size();
+  std::vector<Choice> choice(n_amp);
+  {
+    std::map<std::vector<int>, int> freq;
+    std::vector<std::vector<Choice>> cand(n_amp);
+    for (int i = 0; i < n_amp && opt.vertex_partials; ++i) {
+      cand[i] = candidates(B.amps[i]);
+      for (auto& c : cand[i]) freq[c.key]++;
+    }
+    std::map<std::vector<int>, int> taken;
+    for (int i = 0; i < n_amp; ++i) {
+      if (cand[i].empty()) continue;
+      size_t best = 0;
+      for (size_t k = 1; k < cand[i].size(); ++k)
+        if (freq[cand[i][k].key] > freq[cand[i][best].key]) best = k;
+      choice[i] = cand[i][best];
+      taken[choice[i].key]++;
+    }
+    for (int i = 0; i < n_amp; ++i)
+      if (choice[i].free_k >= 0 && taken[choice[i].key] < 2) choice[i] = Choice();
+  }
+  // groups: amplitudes sharing one partial (the shared inputs in the partial's call order)
+  struct Group {
+    std::vector<int> shared;
+    std::vector<int> members;
+  };
+  std::vector<Group> groups;
+  std::vector<int> group_of(n_amp, -1);
+  {
+    std::map<std::vector<int>, int> gid;
+    for (int i = 0; i < n_amp; ++i) {
+      if (choice[i].free_k < 0) continue;
+      const Amp& a = B.amps[i];
+      auto it = gid.find(choice[i].key);
+      if (it == gid.end()) {
+        Group gr;
+        const int k = choice[i].free_k;
+        if (a.type == OP_AVVV) gr.shared = {a.kids[(k + 1) % 3], a.kids[(k + 2) % 3]};
+        else if (a.type == OP_AGGGG) gr.shared = {choice[i].key[1], choice[i].key[2], choice[i].key[3]};
+        else
+          for (int j = 0; j < 3; ++j)
+            if (j != k) gr.shared.push_back(a.kids[j]);
+        it = gid.emplace(choice[i].key, (int)groups.size()).first;
+        groups.push_back(gr);
+      }
+      group_of[i] = it->second;
+      groups[it->second].members.push_back(i);
+    }
+  }
+  const int n_groups = (int)groups.size();
+
+  // ---- schedule: amplitudes in a given order, currents on demand, a group's
+  // partial made before its first member, every slot freed after its last use.
+  // Two orders: amplitudes sorted by their largest input current, and groups
+  // kept together (sorted by their shared inputs, members by their free
+  // input).  The one with fewer live slots is kept unless the options ask for
+  // groups together.
+  const int nn = (int)B.nodes.size();
   std::vector<char> needed(nn, 0);
   std::function<void(int)> mark = [&](int id) {
     if (needed[id]) return;
     needed[id] = 1;
-    for (int k : B.nodes[id]->kids) { mark(k); }
+    for (int k : B.nodes[id]->kids) mark(k);
   };
   for (auto& a : B.amps)
     for (int k : a.kids) mark(k);
+  std::vector<int> uses0(nn + n_groups, 0);  // value ids: nodes, then one partial per group
   for (int id = 0; id < nn; ++id)
     if (needed[id])
-      for (int k : B.nodes[id]->kids) uses[k]++;
-  for (auto& a : B.amps)
-    for (int k : a.kids) uses[k]++;
-  std::vector<int> order(B.amps.size());
-  std::iota(order.begin(), order.end(), 0);
-  auto keyf = [&](int i) {
-    std::vector<int> k = B.amps[i].kids;
+      for (int k : B.nodes[id]->kids) uses0[k]++;
+  for (int i = 0; i < n_amp; ++i)
+    if (group_of[i] < 0)
+      for (int k : B.amps[i].kids) uses0[k]++;
+    else
+      uses0[B.amps[i].kids[choice[i].free_k]]++;
+  for (int gI = 0; gI < n_groups; ++gI) {
+    for (int k : groups[gI].shared) uses0[k]++;
+    uses0[nn + gI] = (int)groups[gI].members.size();
+  }
+  auto sorted_desc = [](std::vector<int> k) {
     std::sort(k.rbegin(), k.rend());
     return k;
   };
-  std::vector<std::vector<int>> keys(B.amps.size());
-  for (size_t i = 0; i < B.amps.size(); ++i) keys[i] = keyf((int)i);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return keys[a] < keys[b]; });
+  std::vector<std::vector<int>> orders;
+  {
+    std::vector<int> o(n_amp);
+    std::iota(o.begin(), o.end(), 0);
+    std::vector<std::vector<int>> key(n_amp);
+    for (int i = 0; i < n_amp; ++i) key[i] = sorted_desc(B.amps[i].kids);
+    std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return key[a] < key[b]; });
+    orders.push_back(o);
+    // groups together
+    std::vector<std::pair<std::vector<int>, std::vector<int>>> units;  // (sort key, amplitudes)
+    for (int i : o)
+      if (group_of[i] < 0) units.push_back({key[i], {i}});
+    for (const Group& gr : groups) {
+      std::vector<int> m = gr.members;
+      std::stable_sort(m.begin(), m.end(), [&](int a, int b) {
+        return B.amps[a].kids[choice[a].free_k] > B.amps[b].kids[choice[b].free_k];
+      });
+      units.push_back({sorted_desc(gr.shared), m});
+    }
+    std::stable_sort(units.begin(), units.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    std::vector<int> o2;
+    for (auto& u : units) o2.insert(o2.end(), u.second.begin(), u.second.end());
+    orders.push_back(o2);
+  }
 
   std::map<uint32_t, int> mask_row;
   auto row_of = [&](uint32_t m) {
@@ -913,65 +1033,142 @@ Program build_program(const std::vector<int>& pdg) {
     mask_row[m] = r;
     return r;
   };
-  std::vector<int> slot(nn, -1);
-  std::vector<int> free_slots;
-  int n_slots = 0;
-  auto alloc = [&]() {
-    if (!free_slots.empty()) { int s = free_slots.back(); free_slots.pop_back(); return s; }
-    return n_slots++;
-  };
-  auto release = [&](int id) {
-    if (--uses[id] == 0) free_slots.push_back(slot[id]);
-  };
   double flops = 0;
-  int n_cur = 0;
-  std::function<void(int)> ensure = [&](int id) {
-    if (slot[id] >= 0) return;
-    Node& nd = *B.nodes[id];
-    for (int k : nd.kids) ensure(k);
-    Op op;
-    std::memset(&op, 0, sizeof(op));
-    op.type = (uint8_t)nd.type;
-    op.n_in = (uint8_t)nd.kids.size();
-    for (size_t k = 0; k < nd.kids.size(); ++k) {
-      op.in[k] = (uint16_t)slot[nd.kids[k]];
-      op.min[k] = (uint16_t)row_of(B.nodes[nd.kids[k]]->mask);
+  int n_cur = 0, n_part = 0, n_slots = 0;
+  std::vector<int> vertex_type;  // vertex function of each emitted amplitude op, in program order
+  // Runs the schedule of `order`; emits the ops when emit is set.  Returns the slot count.
+  auto run = [&](const std::vector<int>& order, bool emit) {
+    std::vector<int> uses = uses0;
+    std::vector<int> slot(nn + n_groups, -1);
+    std::vector<int> free_slots;
+    int ns = 0;
+    auto alloc = [&]() {
+      if (!free_slots.empty()) { int s = free_slots.back(); free_slots.pop_back(); return s; }
+      return ns++;
+    };
+    auto release = [&](int id) {
+      if (--uses[id] == 0) free_slots.push_back(slot[id]);
+    };
+    std::function<void(int)> ensure = [&](int id) {
+      if (slot[id] >= 0) return;
+      Node& nd = *B.nodes[id];
+      for (int k : nd.kids) ensure(k);
+      Op op;
+      std::memset(&op, 0, sizeof(op));
+      if (emit) {
+        op.type = (uint8_t)nd.type;
+        op.n_in = (uint8_t)nd.kids.size();
+        for (size_t k = 0; k < nd.kids.size(); ++k) {
+          op.in[k] = (uint16_t)slot[nd.kids[k]];
+          op.min[k] = (uint16_t)row_of(B.nodes[nd.kids[k]]->mask);
+        }
+        op.mout = (uint16_t)row_of(nd.mask);
+        if (nd.type == OP_EXT) op.leg = (uint16_t)__builtin_ctz(nd.mask);
+      }
+      for (int k : nd.kids) release(k);
+      slot[id] = alloc();
+      if (emit) {
+        op.out = (uint16_t)slot[id];
+        P.ops.push_back(op);
+        flops += op_flops(nd.type);
+        if (nd.type != OP_EXT) ++n_cur;
+      }
+    };
+    auto add_colour = [&](Op& op, const Amp& a) {
+      op.col_begin = (uint32_t)P.col.size();
+      for (auto& e : a.col) {
+        if (e.second.re < -127 || e.second.re > 127 || e.second.im < -127 || e.second.im > 127)
+          throw std::runtime_error("generator: colour coefficient out of int8 range");
+        P.col.push_back(ColEntry{(uint16_t)e.first, (int8_t)e.second.re, (int8_t)e.second.im});
+      }
+      op.col_count = (uint32_t)a.col.size();
+    };
+    for (int i : order) {
+      const Amp& a = B.amps[i];
+      const int gI = group_of[i];
+      if (gI < 0) {  // plain vertex amplitude
+        for (int k : a.kids) ensure(k);
+        if (emit) {
+          Op op;
+          std::memset(&op, 0, sizeof(op));
+          op.type = (uint8_t)a.type;
+          op.n_in = (uint8_t)a.kids.size();
+          for (size_t k = 0; k < a.kids.size(); ++k) {
+            op.in[k] = (uint16_t)slot[a.kids[k]];
+            op.min[k] = (uint16_t)row_of(B.nodes[a.kids[k]]->mask);
+          }
+          add_colour(op, a);
+          P.ops.push_back(op);
+          vertex_type.push_back(a.type);
+          flops += op_flops(a.type) + 4.0 * a.col.size();
+        }
+        for (int k : a.kids) release(k);
+        continue;
+      }
+      const Group& gr = groups[gI];
+      if (slot[nn + gI] < 0) {  // the group's partial, before its first member
+        const Amp& a0 = B.amps[gr.members[0]];
+        const Choice& c0 = choice[gr.members[0]];
+        for (int k : gr.shared) ensure(k);
+        Op pop;
+        std::memset(&pop, 0, sizeof(pop));
+        if (emit) {
+          pop.type = (uint8_t)c0.key[0];
+          pop.n_in = (uint8_t)gr.shared.size();
+          for (size_t k = 0; k < gr.shared.size(); ++k) {
+            pop.in[k] = (uint16_t)slot[gr.shared[k]];
+            pop.min[k + (a0.type == OP_AVVV ? 1 : 0)] = (uint16_t)row_of(B.nodes[gr.shared[k]]->mask);
+          }
+          if (a0.type == OP_AVVV) pop.min[0] = (uint16_t)row_of(B.nodes[a0.kids[c0.free_k]]->mask);
+          if (a0.type == OP_AIOV) pop.leg = (uint16_t)c0.free_k;
+        }
+        for (int k : gr.shared) release(k);
+        slot[nn + gI] = alloc();
+        if (emit) {
+          pop.out = (uint16_t)slot[nn + gI];
+          P.ops.push_back(pop);
+          flops += op_cost(pop);
+          ++n_part;
+        }
+      }
+      const int fr = a.kids[choice[i].free_k];
+      ensure(fr);
+      if (emit) {
+        Op op;
+        std::memset(&op, 0, sizeof(op));
+        op.type = OP_ADOT;
+        op.n_in = 2;
+        op.in[0] = (uint16_t)slot[fr];
+        op.in[1] = (uint16_t)slot[nn + gI];
+        op.min[0] = (uint16_t)row_of(B.nodes[fr]->mask);
+        const bool plain = a.type == OP_AIOV && choice[i].free_k != 2;
+        op.leg = (uint16_t)((plain ? 1 : 0) | (choice[i].neg ? 2 : 0));
+        add_colour(op, a);
+        P.ops.push_back(op);
+        vertex_type.push_back(a.type);
+        flops += op_flops(OP_ADOT) + 4.0 * a.col.size();
+      }
+      release(fr);
+      release(nn + gI);
     }
-    op.mout = (uint16_t)row_of(nd.mask);
-    if (nd.type == OP_EXT) op.leg = (uint16_t)__builtin_ctz(nd.mask);
-    for (int k : nd.kids) release(k);
-    slot[id] = alloc();
-    op.out = (uint16_t)slot[id];
-    P.ops.push_back(op);
-    flops += op_flops(nd.type);
-    if (nd.type != OP_EXT) ++n_cur;
+    return ns;
   };
-  for (int i : order) {
-    Amp& a = B.amps[i];
-    for (int k : a.kids) ensure(k);
-    Op op;
-    std::memset(&op, 0, sizeof(op));
-    op.type = (uint8_t)a.type;
-    op.n_in = (uint8_t)a.kids.size();
-    for (size_t k = 0; k < a.kids.size(); ++k) {
-      op.in[k] = (uint16_t)slot[a.kids[k]];
-      op.min[k] = (uint16_t)row_of(B.nodes[a.kids[k]]->mask);
+  size_t best = 0;
+  if (opt.group_together && n_groups > 0) {
+    best = 1;
+  } else {
+    int best_slots = run(orders[0], false);
+    for (size_t k = 1; k < orders.size(); ++k) {
+      const int ns = run(orders[k], false);
+      if (ns < best_slots) { best_slots = ns; best = k; }
     }
-    op.col_begin = (uint32_t)P.col.size();
-    for (auto& e : a.col) {
-      if (e.second.re < -127 || e.second.re > 127 || e.second.im < -127 || e.second.im > 127)
-        throw std::runtime_error("generator: colour coefficient out of int8 range");
-      P.col.push_back(ColEntry{(uint16_t)e.first, (int8_t)e.second.re, (int8_t)e.second.im});
-    }
-    op.col_count = (uint32_t)a.col.size();
-    P.ops.push_back(op);
-    flops += op_flops(a.type) + 4.0 * a.col.size();
-    for (int k : a.kids) release(k);
   }
+  n_slots = run(orders[best], true);
   if (n_slots > 65535 || P.masks.size() > 65535 || B.n_colour > 65535)
     throw std::runtime_error("generator: program too large");
   P.n_slots = n_slots;
   P.n_currents = n_cur;
+  P.n_partials = n_part;
   P.flops_per_hel = flops;  // recounted after the colour folding below
 
   colour_matrix(B, P);
@@ -980,12 +1177,19 @@ Program build_program(const std::vector<int>& pdg) {
   {
     uint16_t d = 0;
     for (Op& op : P.ops)
-      if (op.type >= OP_AVVV) op.out = d++;
+      if (is_amp_op(op.type)) op.out = d++;
   }
   {
-    double f = 0;
-    for (const Op& op : P.ops) f += op_flops(op.type) + ((op.type >= OP_AVVV) ? 4.0 * op.col_count : 0.0);
+    double f = 0, fp = 0;
+    size_t k = 0;
+    for (const Op& op : P.ops) {
+      const double col = is_amp_op(op.type) ? 4.0 * op.col_count : 0.0;
+      f += op_cost(op) + col;
+      if (is_amp_op(op.type)) fp += op_flops(vertex_type[k++]) + col;
+      else if (!is_partial_op(op.type)) fp += op_cost(op);
+    }
     P.flops_per_hel = f;
+    P.flops_per_hel_plain = fp;
   }
 
   // helicities

@@ -12,6 +12,9 @@
 //     two strings joined by one exchanged gluon for two quark lines);
 //   * the exact colour matrix N = K / D of Eq. (color-matrix), K integer;
 //   * the helicity combinations allowed by the massless selection rules;
+//   * vertex partials: diagram amplitudes whose amplitude vertex shares all
+//     inputs but one are evaluated as contractions of that input with the
+//     shared partial vertex (heget.cuh, "vertex partials");
 //   * an evaluation order with wavefunction-slot reuse.
 #pragma once
 #include <cstdint>
@@ -30,7 +33,19 @@ enum OpType : uint8_t {
   OP_AVVV = 7,   // amplitude vvvxxx(in[0], in[1], in[2])
   OP_AGGGG = 8,  // amplitude ggggxx(in[0..3]) in call order
   OP_AIOV = 9,   // amplitude iovxx0(fi = in[0], fo = in[1], v = in[2])
+  OP_ADOT = 10,  // amplitude: free wavefunction in[0] contracted with the vertex partial in[1];
+                 // leg bit 0: plain (spinor) instead of metric contraction, bit 1: negate
+  OP_PVVV = 11,  // vertex partial of vvvxxx with a free first argument: in[0], in[1] the other two,
+                 // min[0] the free argument's row, min[1], min[2] those of in[0], in[1]
+  OP_PGGGG = 12, // vertex partial G(in[0], in[1], in[2]) of ggggxx (heget.cuh gggg_part)
+  OP_PIOV = 13,  // vertex partial of iovxx0, leg = free argument (0 fi, 1 fo, 2 V):
+                 // (fo, V), (fi, V) or (fi, fo) in in[0], in[1]
 };
+
+// Amplitude operations (one per Feynman diagram, in diagram-ordinal order).
+inline bool is_amp_op(int t) { return t == OP_AVVV || t == OP_AGGGG || t == OP_AIOV || t == OP_ADOT; }
+// Vertex partials: like currents they fill a wavefunction slot.
+inline bool is_partial_op(int t) { return t >= OP_PVVV && t <= OP_PIOV; }
 
 // 32-byte operation record, read uniformly by every lane.
 struct Op {
@@ -68,6 +83,7 @@ struct Program {
   int n_slots = 0;
   int n_diagrams = 0;
   int n_currents = 0;
+  int n_partials = 0;                 // vertex partials shared by several diagram amplitudes
   int n_colour = 0;                   // colour basis size (Table 1)
   int n_a = 1, n_b = 1;
   std::vector<int64_t> cf_num;        // [m*m] exact colour matrix K of the basis, N = K / cf_den
@@ -85,11 +101,23 @@ struct Program {
   int n_hel = 0;
   std::vector<int8_t> hel_all;        // [2^n_ext][n_ext]
   double flops_per_hel = 0;
+  double flops_per_hel_plain = 0;     // the same with one vertex call per diagram
   std::string basis_text;             // human-readable basis (debug)
 };
 
-// Throws std::runtime_error on unsupported input.
-Program build_program(const std::vector<int>& pdg);
+struct BuildOptions {
+  // false: every diagram amplitude is its own vertex call (no shared partials)
+  bool vertex_partials = true;
+  // schedule: false keeps the order with fewer live wavefunction slots (the
+  // interpreter's memory traffic); true keeps each partial's diagrams together
+  // (shorter live ranges in the straight-line kernels' registers)
+  bool group_together = false;
+};
+
+// Throws std::runtime_error on unsupported input.  The diagram amplitudes and
+// their colour coefficients do not depend on the options; their order and the
+// rounding of the amplitudes do.
+Program build_program(const std::vector<int>& pdg, const BuildOptions& opt = BuildOptions());
 
 // Distinct signed non-zero values of the upper triangle of K (Table 5 count).
 int count_unique_colour_values(const Program& p);

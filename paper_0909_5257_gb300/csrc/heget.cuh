@@ -222,6 +222,88 @@ MEA_HD W4<R> jio(const W4<R>& fi, const W4<R>& fo, R inv_q2, R g) {
   return j;
 }
 
+// ------------------------------------------------------- vertex partials
+// Every amplitude vertex is linear in each of its wavefunctions.  Diagrams
+// whose amplitude vertex shares all but one input (the "free" one) share the
+// vertex with that input taken out -- a complex 4-vector, the partial -- and
+// each diagram amplitude is then the contraction of its free wavefunction
+// with the partial.  The amplitude of every diagram is still formed and
+// summed into the colour amplitudes on its own; only the common factor of the
+// vertex is computed once.
+
+// vvvxxx with the first wavefunction free:  vvv_amp(ga, gb, gc) = ga . U
+//   U = -g [ gb (pa-pb).gc + (pb-pc) (gb.gc) + gc (pc-pa).gb ]
+// (vvv_amp is invariant under a cyclic shift of (wavefunction, momentum), so
+// any of its three arguments can be the free one).
+template <typename R>
+MEA_HD W4<R> vvv_part(const W4<R>& gb, const W4<R>& gc, const R* pa, const R* pb, const R* pc, R g) {
+  R d1[4], d2[4], d3[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    d1[m] = pa[m] - pb[m];
+    d2[m] = pb[m] - pc[m];
+    d3[m] = pc[m] - pa[m];
+  }
+  const R ng = -g;
+  const cx<R> s1 = ng * dot(d1, gc), s3 = ng * dot(d3, gb), bc = ng * dot(gb, gc);
+  W4<R> u;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) u.c[m] = s1 * gb.c[m] + d2[m] * bc + s3 * gc.c[m];
+  return u;
+}
+
+// ggggxx with one wavefunction free, written as free . G(x, y, z) with
+//   G(x, y, z) = gg [ z (x.y) - y (x.z) ]
+// ggggxx(a, b, c, d) = a.G(b, c, d) = b.G(a, d, c) = c.G(d, a, b) = d.G(c, b, a).
+template <typename R>
+MEA_HD W4<R> gggg_part(const W4<R>& x, const W4<R>& y, const W4<R>& z, R gg) {
+  const cx<R> xy = gg * dot(x, y), xz = gg * dot(x, z);
+  W4<R> o;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) o.c[m] = xy * z.c[m] - xz * y.c[m];
+  return o;
+}
+
+// iovxx0 = g fo slash(V) fi with V free: the vector g fo gamma^mu fi, so that
+// iov_amp = V . P (metric contraction).
+template <typename R>
+MEA_HD W4<R> iov_part_v(const W4<R>& fi, const W4<R>& fo, R g) {
+  const W4<R>& a = fo;
+  const W4<R>& b = fi;
+  W4<R> j;
+  j.c[0] = g * (a.c[0] * b.c[2] + a.c[1] * b.c[3] + a.c[2] * b.c[0] + a.c[3] * b.c[1]);
+  j.c[1] = g * (a.c[0] * b.c[3] + a.c[1] * b.c[2] - a.c[2] * b.c[1] - a.c[3] * b.c[0]);
+  j.c[2] = g * times_i(a.c[1] * b.c[2] - a.c[0] * b.c[3] + a.c[2] * b.c[1] - a.c[3] * b.c[0]);
+  j.c[3] = g * (a.c[0] * b.c[2] - a.c[1] * b.c[3] - a.c[2] * b.c[0] + a.c[3] * b.c[1]);
+  return j;
+}
+// ... with fi free: the row spinor g fo slash(V), iov_amp = sum_k P_k fi_k.
+template <typename R>
+MEA_HD W4<R> iov_part_i(const W4<R>& fo, const W4<R>& v, R g) {
+  W4<R> t = row_slash(fo, v);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) t.c[m] = g * t.c[m];
+  return t;
+}
+// ... with fo free: the column spinor g slash(V) fi, iov_amp = sum_k fo_k P_k.
+template <typename R>
+MEA_HD W4<R> iov_part_o(const W4<R>& fi, const W4<R>& v, R g) {
+  W4<R> t = slash_col(v, fi);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) t.c[m] = g * t.c[m];
+  return t;
+}
+
+// Contraction of a free wavefunction with a partial: metric (vector partials)
+// or plain (spinor partials), negated when neg is set.
+template <typename R>
+MEA_HD cx<R> part_contract(const W4<R>& w, const W4<R>& p, bool plain, bool neg) {
+  cx<R> s = w.c[0] * p.c[0];
+  if (plain) s = s + w.c[1] * p.c[1] + w.c[2] * p.c[2] + w.c[3] * p.c[3];
+  else s = s - w.c[1] * p.c[1] - w.c[2] * p.c[2] - w.c[3] * p.c[3];
+  return neg ? -s : s;
+}
+
 // ------------------------------------------------------- external states
 // Gluon of helicity lam with transverse unit vectors e1, e2 (e1 x e2 = p_hat):
 // eps = (-lam e1 - i e2)/sqrt2, conjugated for an outgoing gluon.

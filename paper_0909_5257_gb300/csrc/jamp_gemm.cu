@@ -281,7 +281,7 @@ JampMap build_jamp_map(const Program& p) {
   int g = 0;
   bool real = true;
   for (const Op& op : p.ops) {
-    if (op.type < OP_AVVV) continue;
+    if (!is_amp_op(op.type)) continue;
     ++kd;
     for (uint32_t k = 0; k < op.col_count; ++k) {
       const ColEntry& c = p.col[op.col_begin + k];
@@ -303,7 +303,7 @@ JampMap build_jamp_map(const Program& p) {
   M.tiles.assign((size_t)M.n_splits * n_kc * M.nc * kKC, __float2half(0.f));
   int d = 0;
   for (const Op& op : p.ops) {
-    if (op.type < OP_AVVV) continue;
+    if (!is_amp_op(op.type)) continue;
     for (uint32_t k = 0; k < op.col_count; ++k) {
       const ColEntry& c = p.col[op.col_begin + k];
       const int n = c.re / g;

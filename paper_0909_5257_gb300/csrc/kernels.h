@@ -16,12 +16,13 @@ struct AmpLaunch;
 // A straight-line per-process kernel emitted by codegen.cpp at build time.
 struct GenEntry {
   const char* key;  // PDG codes joined by commas
-  // regvar: register-cap variant of the FP32 kernel (0: 128, 1: 85
-  // registers per thread); the FP64 kernel has one variant (128)
+  // regvar: variant of the FP32 kernel -- 0 / 1 body with vertex partials at
+  // 128 / 85 registers per thread, 2 / 3 body with one vertex call per diagram
+  // at 128 / 85; the FP64 kernel has one variant (partials, 128)
   void (*launch)(bool fp64, int regvar, const DevProgram&, const AmpConfig&, const AmpLaunch&, cudaStream_t);
   const void* (*kernel)(bool fp64, int regvar);
 };
-constexpr int kGenRegVariants = 2;
+constexpr int kGenRegVariants = 4;
 const GenEntry* generated_table(int* n);
 const GenEntry* find_generated(const int* pdg, int n_ext);
 

@@ -45,14 +45,15 @@ class ProcessInfo(ctypes.Structure):
                 ("n_hel_nonzero", ctypes.c_int), ("n_currents", ctypes.c_int), ("n_ops", ctypes.c_int),
                 ("n_slots", ctypes.c_int), ("n_colour_amplitudes", ctypes.c_int),
                 ("cf_denominator", ctypes.c_int64), ("cf_max_abs_numerator", ctypes.c_int64),
-                ("flops_per_hel", ctypes.c_double), ("colour_flops_per_hel", ctypes.c_double)]
+                ("flops_per_hel", ctypes.c_double), ("colour_flops_per_hel", ctypes.c_double),
+                ("flops_per_hel_plain", ctypes.c_double)]
 
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("events_per_cta", ctypes.c_int), ("grid", ctypes.c_int),
                 ("colour_amps_in_shared", ctypes.c_int), ("slots_in_shared", ctypes.c_int),
                 ("candidates", ctypes.c_int), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
-                ("register_cap", ctypes.c_int)]
+                ("register_cap", ctypes.c_int), ("vertex_partials", ctypes.c_int)]
 
 
 class BatchItem(ctypes.Structure):

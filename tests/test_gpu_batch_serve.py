@@ -64,7 +64,9 @@ def test_batch_graph_matches_individual_evaluations(prec):
 @pytest.mark.parametrize("pdg,nf,lo,hi", [([21] * 5, 3, 200.0, 2000.0), ([2, 2, 2, 2, 21], 3, 200.0, 2000.0),
                                          ([2, -2, 21, 21, 21, 21], 4, 300.0, 3000.0)])
 def test_autotune_keeps_results(pdg, nf, lo, hi):
-    """Tile shape, placement and register-cap variant change no result bit."""
+    """Tile shape, placement and register-cap variant change no result bit; the
+    straight-line body without vertex partials (a tuning choice for the small
+    processes) changes only the FP32 rounding order."""
     mea = _mea()
     P = mea.Process(pdg, auto_tune=False)
     mom = _events(nf, 4096, lo, hi)
@@ -73,7 +75,11 @@ def test_autotune_keeps_results(pdg, nf, lo, hi):
     r = P.autotune(mom[:2048], scratch, precision=mea.PREC_MIXED)
     assert r["candidates"] >= 1 and r["best_ms"] > 0 and r["best_ms"] <= r["default_ms"] * 1.0001
     got = _alone(P, mom, mea.PREC_MIXED)
-    assert torch.equal(got, ref)
+    if r["vertex_partials"]:
+        assert torch.equal(got, ref)
+    else:
+        assert r["register_cap"] > 0  # only straight-line kernels have the variant
+        assert torch.allclose(got, ref, rtol=2e-5, atol=0)
 
 
 def test_server_results_identical_alone_and_in_mix():
@@ -133,12 +139,14 @@ def test_server_admission_rejects_and_times_out_without_hanging():
 
 def test_autotune_on_first_use():
     """The first evaluation of >= 2^16 events tunes the process once; the
-    results equal those of an untuned process bit for bit."""
+    results equal those of an untuned process up to the FP32 rounding order
+    of the chosen body (bit for bit when the tuner keeps the default body),
+    and later evaluations repeat the first bit for bit."""
     mea = _mea()
     mom = _events(3, 1 << 16, 200.0, 2000.0)
     auto = mea.Process([2, 2, 2, 2, 21])
     fixed = mea.Process([2, 2, 2, 2, 21], auto_tune=False)
     a = _alone(auto, mom, mea.PREC_MIXED)
     b = _alone(fixed, mom, mea.PREC_MIXED)
-    assert torch.equal(a, b)
-    assert torch.equal(_alone(auto, mom, mea.PREC_MIXED), b)
+    assert torch.allclose(a, b, rtol=2e-5, atol=0)
+    assert torch.equal(_alone(auto, mom, mea.PREC_MIXED), a)
