@@ -93,6 +93,12 @@ typedef struct {
                             precision with MEA_HEL_SUM_NONZERO, outside stream capture,
                             synchronises its stream and runs mea_autotune on those
                             events (me2 as scratch) before evaluating; 0: off */
+  int kernel_variant;    /* straight-line kernels (processes with up to five partons),
+                            MEA_PREC_MIXED: 0 (default) the tuned or heuristic variant;
+                            1 / 2 the body with shared vertex partials at 128 / 85
+                            registers per thread, 3 / 4 the body with one vertex call
+                            per diagram at 128 / 85 (pins the rounding order for
+                            reproducible results); other values -> MEA_E_ARG */
 } mea_options;
 
 /* Per-event flag bits written to flags_dev. */

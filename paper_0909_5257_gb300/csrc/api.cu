@@ -255,6 +255,7 @@ mea_status do_evaluate(mea_process_s* P, mea::EvalScratch& S, const double* mom,
     int64_t tiles = (n + c.E_cta - 1) / c.E_cta;
     if (tiles < c.grid) c.grid = (int)std::max<int64_t>(tiles, 1);
   }
+  if (!fp64 && P->dev.gen && P->opts.kernel_variant > 0) c.regvar = P->opts.kernel_variant - 1;
   mea::AmpLaunch a;
   a.mom = mom;
   a.n_events = n;
@@ -358,7 +359,13 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
   P->opts.colour_mode = 0;
   P->opts.chunk_events = 0;
   P->opts.auto_tune = 1;
+  P->opts.kernel_variant = 0;
+  if (opts && (opts->kernel_variant < 0 || opts->kernel_variant > mea::kGenRegVariants)) {
+    destroy(P);
+    return fail(MEA_E_ARG, "mea_create_process: kernel_variant out of range");
+  }
   if (opts) {
+    P->opts.kernel_variant = opts->kernel_variant;
     if (opts->alpha_s > 0) P->opts.alpha_s = opts->alpha_s;
     if (opts->flag_threshold > 0) P->opts.flag_threshold = opts->flag_threshold;
     P->opts.reeval_fp64 = opts->reeval_fp64;

@@ -1164,6 +1164,31 @@ Program build_program(const std::vector<int>& pdg, const BuildOptions& opt) {
     }
   }
   n_slots = run(orders[best], true);
+  // Canonical mask-table numbering (by leg count, then bit pattern), so that
+  // programs built with different options -- the straight-line kernels'
+  // bodies and the runtime program whose table the kernels read -- agree on
+  // every row.  Every row field of every op is remapped (unused fields are
+  // never read).
+  {
+    std::vector<uint32_t> sorted = P.masks;
+    std::sort(sorted.begin(), sorted.end(), [](uint32_t a, uint32_t b) {
+      const int pa = __builtin_popcount(a), pb = __builtin_popcount(b);
+      return pa != pb ? pa < pb : a < b;
+    });
+    std::vector<uint16_t> remap(P.masks.size());
+    for (size_t r = 0; r < P.masks.size(); ++r)
+      remap[r] = (uint16_t)(std::lower_bound(sorted.begin(), sorted.end(), P.masks[r],
+                                             [](uint32_t a, uint32_t b) {
+                                               const int pa = __builtin_popcount(a), pb = __builtin_popcount(b);
+                                               return pa != pb ? pa < pb : a < b;
+                                             }) -
+                            sorted.begin());
+    for (Op& op : P.ops) {
+      for (int k = 0; k < 4; ++k) op.min[k] = remap[op.min[k]];
+      op.mout = remap[op.mout];
+    }
+    P.masks = sorted;
+  }
   if (n_slots > 65535 || P.masks.size() > 65535 || B.n_colour > 65535)
     throw std::runtime_error("generator: program too large");
   P.n_slots = n_slots;

@@ -37,7 +37,7 @@ class MeaError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("alpha_s", ctypes.c_double), ("flag_threshold", ctypes.c_double),
                 ("reeval_fp64", ctypes.c_int), ("colour_mode", ctypes.c_int), ("chunk_events", ctypes.c_int64),
-                ("auto_tune", ctypes.c_int)]
+                ("auto_tune", ctypes.c_int), ("kernel_variant", ctypes.c_int)]
 
 
 class ProcessInfo(ctypes.Structure):
@@ -159,13 +159,13 @@ class Process:
     """
 
     def __init__(self, pdg, alpha_s=0.118, flag_threshold=1e-5, reeval_fp64=True,
-                 colour_mode=0, host_only=False, chunk_events=0, auto_tune=True):
+                 colour_mode=0, host_only=False, chunk_events=0, auto_tune=True, kernel_variant=0):
         lib = load()
         self.pdg = list(pdg)
         self.n_ext = len(self.pdg)
         arr = (ctypes.c_int * self.n_ext)(*self.pdg)
         opts = Options(alpha_s, flag_threshold, 1 if reeval_fp64 else 0, colour_mode, chunk_events,
-                       1 if auto_tune else 0)
+                       1 if auto_tune else 0, kernel_variant)
         h = ctypes.c_void_p()
         fn = lib.mea_create_process_host_only if host_only else lib.mea_create_process
         _check(fn(arr, self.n_ext, ctypes.byref(opts), ctypes.byref(h)))
