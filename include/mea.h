@@ -91,8 +91,10 @@ typedef struct {
                             <= 0 -> automatic (enough lanes to fill the GPU) */
   int auto_tune;         /* 1 (default): the first mea_evaluate of >= 65536 events per
                             precision with MEA_HEL_SUM_NONZERO, outside stream capture,
-                            synchronises its stream and runs mea_autotune on those
-                            events (me2 as scratch) before evaluating; 0: off */
+                            synchronises its stream and runs mea_autotune on its first
+                            65536 events (up to 2^20 for the straight-line FP32 kernels
+                            of processes with up to five partons; me2 as scratch)
+                            before evaluating; 0: off */
   int kernel_variant;    /* straight-line kernels (processes with up to five partons),
                             MEA_PREC_MIXED: 0 (default) the tuned or heuristic variant;
                             1 / 2 the body with shared vertex partials at 128 / 85

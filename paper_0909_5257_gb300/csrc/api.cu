@@ -222,10 +222,15 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
 
 // Tuning on first use: the first evaluation of at least kAutoTuneMin events
 // with the non-zero helicity sum (outside stream capture) waits for its
-// stream, times the candidate tiles on its first kAutoTuneMin events with me2
-// as scratch (mea_autotune), and then evaluates with the chosen tile.  The
-// choice never changes a result: per-event arithmetic does not depend on it.
+// stream, times the candidate tiles on its first events with me2 as scratch
+// (mea_autotune), and then evaluates with the chosen tile.  The sample is
+// kAutoTuneMin events, or up to kAutoTuneGen for the straight-line kernels,
+// whose choice between bodies depends on how their spills share L2 with the
+// streamed inputs at full size.  Tile shape and register cap never change a
+// result bit; the body (vertex partials or not) changes the FP32 rounding
+// order only (kernel_variant pins it).
 constexpr int64_t kAutoTuneMin = 1 << 16;
+constexpr int64_t kAutoTuneGen = 1 << 20;
 
 void maybe_autotune(mea_process_s* P, const double* mom, int64_t n, mea_hel_mode hm, mea_prec_mode prec,
                     double* me2, cudaStream_t s) {
@@ -237,7 +242,8 @@ void maybe_autotune(mea_process_s* P, const double* mom, int64_t n, mea_hel_mode
   if (cudaStreamSynchronize(s) != cudaSuccess) return;  // the error resurfaces at the evaluation's own launches
   const std::string keep = g_err;
   mea_tune_result r;
-  if (mea::autotune_locked(P, mom, kAutoTuneMin, prec, me2, &r) != MEA_OK) g_err = keep;  // keep the heuristic
+  const int64_t sample = (P->dev.gen && prec != MEA_PREC_FP64) ? std::min(n, kAutoTuneGen) : kAutoTuneMin;
+  if (mea::autotune_locked(P, mom, sample, prec, me2, &r) != MEA_OK) g_err = keep;  // keep the heuristic
 }
 
 mea_status do_evaluate(mea_process_s* P, mea::EvalScratch& S, const double* mom, int64_t n, mea_hel_mode hm,
