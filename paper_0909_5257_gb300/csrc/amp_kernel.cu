@@ -439,6 +439,24 @@ const GenEntry* find_generated(const int* pdg, int n_ext) {
 // Straight-line kernels keep the lane state in registers: pick the tile so
 // that threads <= kGenMaxThreads with few idle lanes, then fill the SMs by
 // occupancy.
+//
+// Body of the FP32 straight-line kernel at a register cap (0: 128, 1: 85):
+// the one with shared vertex partials (fewer FLOPs) unless it needs more
+// local memory (spills) than the body with one vertex call per diagram.
+// Spilled lines compete with the streamed inputs for L2 and reach DRAM at
+// full size, which costs more than the FLOPs save (gg>ggg at 2^20 events:
+// 82.7 M events/s with partials, 92.2 M without; the partials body spills
+// 1104 bytes per thread at 128 registers, the other 936).  The rule depends
+// only on the compiled kernels, so the choice -- and the FP32 rounding order
+// -- is the same on every run.
+static int gen_body_variant(const DevProgram& p, int cap) {
+  cudaFuncAttributes with, without;
+  if (cudaFuncGetAttributes(&with, p.gen->kernel(false, cap)) != cudaSuccess ||
+      cudaFuncGetAttributes(&without, p.gen->kernel(false, cap + 2)) != cudaSuccess)
+    return cap;
+  return without.localSizeBytes < with.localSizeBytes ? cap + 2 : cap;
+}
+
 static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms) {
   AmpConfig best;
   best.H = H;
@@ -447,7 +465,7 @@ static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n
   const int tab_stride = event_table_stride(p.n_ext, p.n_masks);
   double best_score = -1;
   // default: the 128-register variant (mea_autotune also tries 85 registers)
-  const int regvar = 0;
+  const int regvar = fp64 ? 0 : gen_body_variant(p, 0);
   const void* k = p.gen->kernel(fp64, regvar);
   cudaFuncAttributes fa;
   int max_threads = 256;
@@ -544,7 +562,11 @@ std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, 
     return c;
   };
   if (p.gen) {
-    for (int rv = 0; rv < (fp64 ? 1 : kGenRegVariants); ++rv) {
+    // FP64: one variant; FP32: both register caps, each with its body (see
+    // gen_body_variant)
+    const int n_caps = fp64 ? 1 : 2;
+    for (int cap_i = 0; cap_i < n_caps; ++cap_i) {
+    const int rv = fp64 ? 0 : gen_body_variant(p, cap_i);
     const void* k = p.gen->kernel(fp64, rv);
     cudaFuncAttributes fa;
     int max_threads = 256;

@@ -136,17 +136,11 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
     }
     return t_best;
   };
-  // The straight-line body without vertex partials (regvar >= 2) computes the
-  // same amplitudes in another rounding order; it is taken only when it is
-  // clearly faster, so that near-equal timings keep the default body and the
-  // choice is stable from run to run.
-  auto score = [&](size_t i, double t) { return (!fp64 && dp.gen && cands[i].regvar >= 2) ? t * 1.03 : t; };
-  double best_score = 1e30;
   std::vector<double> round1(cands.size(), 1e30);
   for (size_t i = 0; i < cands.size(); ++i) {
     round1[i] = time_cand(i, 3);
     if (i == 0) def_ms = round1[i];
-    if (score(i, round1[i]) < best_score) { best_score = score(i, round1[i]); best = round1[i]; best_i = (int)i; }
+    if (round1[i] < best) { best = round1[i]; best_i = (int)i; }
   }
   // second round: the three fastest candidates again, five repetitions each,
   // so that timing noise on the sample does not decide between near-equal tiles
@@ -154,17 +148,16 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
   // default_ms come from the same round)
   if (st == MEA_OK && cands.size() > 1) {
     std::vector<std::pair<double, int>> order;
-    for (size_t i = 0; i < round1.size(); ++i) order.push_back({score(i, round1[i]), (int)i});
+    for (size_t i = 0; i < round1.size(); ++i) order.push_back({round1[i], (int)i});
     std::sort(order.begin(), order.end());
     std::vector<int> again{0};
     for (size_t r = 0; r < order.size() && again.size() < 4; ++r)
       if (order[r].second != 0 && order[r].first < 1e30) again.push_back(order[r].second);
     best = 1e30;
-    best_score = 1e30;
     for (int i : again) {
       const double t = time_cand((size_t)i, 5);
       if (i == 0) def_ms = t;
-      if (score((size_t)i, t) < best_score) { best_score = score((size_t)i, t); best = t; best_i = i; }
+      if (t < best) { best = t; best_i = i; }
     }
   }
   S.release();

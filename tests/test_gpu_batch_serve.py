@@ -64,9 +64,9 @@ def test_batch_graph_matches_individual_evaluations(prec):
 @pytest.mark.parametrize("pdg,nf,lo,hi", [([21] * 5, 3, 200.0, 2000.0), ([2, 2, 2, 2, 21], 3, 200.0, 2000.0),
                                          ([2, -2, 21, 21, 21, 21], 4, 300.0, 3000.0)])
 def test_autotune_keeps_results(pdg, nf, lo, hi):
-    """Tile shape, placement and register-cap variant change no result bit; the
-    straight-line body without vertex partials (a tuning choice for the small
-    processes) changes only the FP32 rounding order."""
+    """Tile shape, placement and register cap change no result bit; the
+    straight-line body (with or without vertex partials, fixed per register
+    cap by the kernels' spill footprint) changes only the FP32 rounding order."""
     mea = _mea()
     P = mea.Process(pdg, auto_tune=False)
     mom = _events(nf, 4096, lo, hi)
