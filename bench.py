@@ -39,10 +39,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "helicity-summed |M|^2 events/s per subprocess, mixed vs FP64 path; p50/p99"
-# ncu, 2^20-event launches of the mixed-path kernels (128-/85-register variants)
-TRAFFIC_BYTES_PER_EVENT = {"gg>ggg": (210698240 + 8088984576) / 2 ** 20,
-                           "uu~>ggg": (167966976 + 8074496) / 2 ** 20,
-                           "uu>uug": (167913728 + 27724032) / 2 ** 20}
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum), one 2^20-event launch of
+# the mixed-path kernel each subprocess runs: gg>ggg the per-diagram body at
+# 128 registers, uu~>ggg the vertex-partial body at 128, uu>uug the per-diagram
+# body at 85
+TRAFFIC_BYTES_PER_EVENT = {"gg>ggg": (206848000 + 7545397760) / 2 ** 20,
+                           "uu~>ggg": (168618752 + 7403264) / 2 ** 20,
+                           "uu>uug": (168189952 + 21019136) / 2 ** 20}
 SEED_BASE = 0x09095257
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2070.0
@@ -514,9 +517,9 @@ def main():
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak = n_sms * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
     # DRAM bytes per event of each kernel from one ncu capture of the current
-    # kernels (profiles/gen_kernel_gg3g_mixed.md: dram__bytes_read.sum +
-    # dram__bytes_write.sum of one 2^20-event launch, divided by the events);
-    # scaled to this launch's events.  Mostly spill write-back for gg>ggg.
+    # kernels (dram__bytes_read.sum + dram__bytes_write.sum of one 2^20-event
+    # launch, divided by the events), scaled to this launch's events.  Mostly
+    # spill write-back for gg>ggg.
     traffic_per_event = TRAFFIC_BYTES_PER_EVENT.get(subs[dom][0])
     traffic = None if traffic_per_event is None else traffic_per_event * n
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
