@@ -70,22 +70,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
                         os.path.join(CSRC, "generator.cpp")], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"codegen tool build failed:\n{r.stderr}")
-    gen_cu = os.path.join(BUILD_DIR, "generated.cu")
-    r = subprocess.run([tool, gen_cu] + GENERATED, capture_output=True, text=True)
+    gen_dir = os.path.join(BUILD_DIR, "generated")
+    os.makedirs(gen_dir, exist_ok=True)
+    for f in os.listdir(gen_dir):
+        os.remove(os.path.join(gen_dir, f))
+    r = subprocess.run([tool, gen_dir] + GENERATED, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"codegen failed:\n{r.stderr}")
+    gen_sources = sorted(os.listdir(gen_dir))
 
-    def compile_generated(_):
-        obj = os.path.join(BUILD_DIR, "generated.cu.o")
-        cmd = [cc] + common + ["-I", CSRC, "-c", gen_cu, "-o", obj]
+    def compile_generated(name):
+        # one translation unit (one device module) per kernel variant, plus the table
+        obj = os.path.join(BUILD_DIR, name + ".o")
+        cmd = [cc] + common + ["-I", CSRC, "-c", os.path.join(gen_dir, name), "-o", obj]
         rr = subprocess.run(cmd, capture_output=True, text=True)
         if rr.returncode != 0:
-            raise RuntimeError(f"nvcc failed on generated.cu:\n{rr.stdout}\n{rr.stderr}")
+            raise RuntimeError(f"nvcc failed on {name}:\n{rr.stdout}\n{rr.stderr}")
         return obj
 
     # 2. compile everything in parallel
-    jobs = [(compile_one, s) for s in SOURCES] + [(compile_generated, None)]
-    with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+    jobs = [(compile_one, s) for s in SOURCES] + [(compile_generated, g) for g in gen_sources]
+    with cf.ThreadPoolExecutor(max_workers=max(4, min(len(jobs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(lambda j: j[0](j[1]), jobs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fopenmp", "-lcudart"]

@@ -183,15 +183,37 @@ void emit_body(std::ostringstream& o, const mea::Program& P, const std::string& 
 
 }  // namespace
 
+// Usage: mea_codegen OUT_DIR pdg,pdg,... [...]
+// Writes, per process, one translation unit (device module) per kernel
+// variant, OUT_DIR/generated_<process>_<variant>.cu, and
+// OUT_DIR/generated_table.cu with the per-process dispatch and the table.
 int main(int argc, char** argv) {
   if (argc < 3) {
-    std::fprintf(stderr, "usage: %s out.cu pdg,pdg,... [...]\n", argv[0]);
+    std::fprintf(stderr, "usage: %s out_dir pdg,pdg,... [...]\n", argv[0]);
     return 2;
   }
-  std::ostringstream o;
-  o << "// Generated by mea_codegen from the process generator; do not edit.\n"
-       "#include \"gen_kernel.cuh\"\n\nnamespace mea {\nnamespace {\n\n";
-  std::vector<std::pair<std::string, std::string>> entries;
+  const std::string dir = argv[1];
+  auto write = [](const std::string& path, const std::string& txt) {
+    FILE* f = std::fopen(path.c_str(), "w");
+    if (!f) return false;
+    std::fwrite(txt.data(), 1, txt.size(), f);
+    std::fclose(f);
+    return true;
+  };
+  // (suffix, real type, body, register-cap MINB): regvar 0..3 FP32, then FP64
+  struct Variant {
+    const char* suffix;
+    const char* real;
+    bool partials;
+    int minb;
+  };
+  static const Variant kVariants[] = {
+      {"f_part_128", "float", true, 2}, {"f_part_85", "float", true, 3},
+      {"f_diag_128", "float", false, 2}, {"f_diag_85", "float", false, 3},
+      {"d_part_128", "double", true, 2}};
+  std::ostringstream t;
+  t << "// Generated by mea_codegen; do not edit.\n#include \"kernels.h\"\n\nnamespace mea {\n\n";
+  std::vector<std::string> ids, pdg_keys;
   for (int i = 2; i < argc; ++i) {
     std::vector<int> pdg;
     std::string s = argv[i];
@@ -203,26 +225,53 @@ int main(int argc, char** argv) {
       pos = e + 1;
     }
     // two bodies per process: with vertex partials and with one vertex call
-    // per diagram (fewer FLOPs against fewer live values; the tuner picks)
-    std::string id = ident_of(pdg);
+    // per diagram (fewer FLOPs against fewer live values)
+    const std::string id = ident_of(pdg);
     mea::BuildOptions with, without;
     with.group_together = true;
     without.vertex_partials = false;
-    emit_body(o, mea::build_program(pdg, with), "Body_" + id);
-    emit_body(o, mea::build_program(pdg, without), "BodyN_" + id);
-    entries.push_back({key_of(pdg), id});
+    std::ostringstream body_part, body_diag;
+    emit_body(body_part, mea::build_program(pdg, with), "Body_" + id);
+    emit_body(body_diag, mea::build_program(pdg, without), "BodyN_" + id);
+    for (const Variant& v : kVariants) {
+      const std::string fn = id + "_" + v.suffix;
+      const std::string body = std::string(v.partials ? "Body_" : "BodyN_") + id + "<" + v.real + ">";
+      const std::string inst = std::string("gen_kernel<") + v.real + ", " + body + ", " + std::to_string(v.minb) + ">";
+      std::ostringstream o;
+      o << "// Generated by mea_codegen from the process generator; do not edit.\n"
+           "#include \"gen_kernel.cuh\"\n\nnamespace mea {\nnamespace {\n\n"
+        << (v.partials ? body_part.str() : body_diag.str()) << "}  // namespace\n\n";
+      o << "void gen_launch_" << fn << "(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {\n"
+        << "  gen_launch_v<" << v.real << ", " << body << ", " << v.minb << ">(p, c, a, s);\n}\n";
+      o << "const void* gen_kernel_" << fn << "() { return reinterpret_cast<const void*>(" << inst << "); }\n\n"
+        << "}  // namespace mea\n";
+      if (!write(dir + "/generated_" + fn + ".cu", o.str())) return 1;
+      t << "void gen_launch_" << fn << "(const DevProgram&, const AmpConfig&, const AmpLaunch&, cudaStream_t);\n"
+        << "const void* gen_kernel_" << fn << "();\n";
+    }
+    // dispatch: regvar 0..3 are the FP32 variants in kVariants order
+    t << "static void launch_" << id << "(bool fp64, int regvar, const DevProgram& p, const AmpConfig& c, "
+         "const AmpLaunch& a, cudaStream_t s) {\n"
+      << "  if (fp64) return gen_launch_" << id << "_d_part_128(p, c, a, s);\n"
+      << "  switch (regvar) {\n"
+      << "    case 1: return gen_launch_" << id << "_f_part_85(p, c, a, s);\n"
+      << "    case 2: return gen_launch_" << id << "_f_diag_128(p, c, a, s);\n"
+      << "    case 3: return gen_launch_" << id << "_f_diag_85(p, c, a, s);\n"
+      << "    default: return gen_launch_" << id << "_f_part_128(p, c, a, s);\n  }\n}\n";
+    t << "static const void* kernel_" << id << "(bool fp64, int regvar) {\n"
+      << "  if (fp64) return gen_kernel_" << id << "_d_part_128();\n"
+      << "  switch (regvar) {\n"
+      << "    case 1: return gen_kernel_" << id << "_f_part_85();\n"
+      << "    case 2: return gen_kernel_" << id << "_f_diag_128();\n"
+      << "    case 3: return gen_kernel_" << id << "_f_diag_85();\n"
+      << "    default: return gen_kernel_" << id << "_f_part_128();\n  }\n}\n\n";
+    ids.push_back(id);
+    pdg_keys.push_back(key_of(pdg));
   }
-  o << "}  // namespace\n\n";
-  o << "const GenEntry* generated_table(int* n) {\n  static const GenEntry t[] = {\n";
-  for (auto& e : entries) {
-    const std::string args = "Body_" + e.second + "<float>, BodyN_" + e.second + "<float>, Body_" + e.second + "<double>";
-    o << "    {\"" << e.first << "\", &gen_launch<" << args << ">, &gen_kernel_for<" << args << ">},\n";
-  }
-  o << "  };\n  *n = " << entries.size() << ";\n  return t;\n}\n\n}  // namespace mea\n";
-  FILE* f = std::fopen(argv[1], "w");
-  if (!f) return 1;
-  std::string txt = o.str();
-  std::fwrite(txt.data(), 1, txt.size(), f);
-  std::fclose(f);
+  t << "const GenEntry* generated_table(int* n) {\n  static const GenEntry t[] = {\n";
+  for (size_t k = 0; k < ids.size(); ++k)
+    t << "    {\"" << pdg_keys[k] << "\", &launch_" << ids[k] << ", &kernel_" << ids[k] << "},\n";
+  t << "  };\n  *n = " << ids.size() << ";\n  return t;\n}\n\n}  // namespace mea\n";
+  if (!write(dir + "/generated_table.cu", t.str())) return 1;
   return 0;
 }

@@ -135,26 +135,13 @@ void gen_launch_v(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, c
   gen_kernel<R, Body, MINB><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
 }
 
-// Variants of the FP32 body (GenEntry::launch): regvar 0 / 1 with vertex
-// partials at 128 / 85 registers (MINB 2 / 3), 2 / 3 the body with one vertex
-// call per diagram at 128 / 85.  FP64: the body with partials, MINB 2.
-template <typename BodyF, typename BodyFN, typename BodyD>
-void gen_launch(bool fp64, int regvar, const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
-  if (fp64) gen_launch_v<double, BodyD, 2>(p, c, a, s);
-  else if (regvar == 1) gen_launch_v<float, BodyF, 3>(p, c, a, s);
-  else if (regvar == 2) gen_launch_v<float, BodyFN, 2>(p, c, a, s);
-  else if (regvar == 3) gen_launch_v<float, BodyFN, 3>(p, c, a, s);
-  else gen_launch_v<float, BodyF, 2>(p, c, a, s);
-}
-
-template <typename BodyF, typename BodyFN, typename BodyD>
-const void* gen_kernel_for(bool fp64, int regvar) {
-  if (fp64) return reinterpret_cast<const void*>(gen_kernel<double, BodyD, 2>);
-  if (regvar == 1) return reinterpret_cast<const void*>(gen_kernel<float, BodyF, 3>);
-  if (regvar == 2) return reinterpret_cast<const void*>(gen_kernel<float, BodyFN, 2>);
-  if (regvar == 3) return reinterpret_cast<const void*>(gen_kernel<float, BodyFN, 3>);
-  return reinterpret_cast<const void*>(gen_kernel<float, BodyF, 2>);
-}
-
+// Each kernel variant of a process -- FP32 body with vertex partials at 128 /
+// 85 registers (regvar 0 / 1), FP32 body with one vertex call per diagram at
+// 128 / 85 (regvar 2 / 3), FP64 body with partials at 128 -- is instantiated
+// in a translation unit (device module) of its own by codegen.cpp, behind two
+// plain functions: gen_launch_v and the kernel's address.  One variant's code
+// then does not change where another's lands: the 3-jet straight-line kernels
+// are instruction-fetch bound, and their speed moved by up to 20 % with the
+// other code around them in a shared module.
 }  // namespace
 }  // namespace mea

@@ -1164,30 +1164,43 @@ Program build_program(const std::vector<int>& pdg, const BuildOptions& opt) {
     }
   }
   n_slots = run(orders[best], true);
-  // Canonical mask-table numbering (by leg count, then bit pattern), so that
-  // programs built with different options -- the straight-line kernels'
-  // bodies and the runtime program whose table the kernels read -- agree on
-  // every row.  Every row field of every op is remapped (unused fields are
-  // never read).
+  // Canonical mask-table numbering, so that programs built with different
+  // options -- the straight-line kernels' bodies and the runtime program whose
+  // table the kernels read -- agree on every row: the order in which the
+  // schedule without vertex partials (amplitudes by their largest input
+  // current, currents on demand) first uses each mask.  Every row field of
+  // every op is remapped (unused fields are never read).
   {
-    std::vector<uint32_t> sorted = P.masks;
-    std::sort(sorted.begin(), sorted.end(), [](uint32_t a, uint32_t b) {
-      const int pa = __builtin_popcount(a), pb = __builtin_popcount(b);
-      return pa != pb ? pa < pb : a < b;
-    });
+    std::vector<uint32_t> canon;
+    std::map<uint32_t, int> rank;
+    auto use = [&](uint32_t m) {
+      if (rank.emplace(m, (int)canon.size()).second) canon.push_back(m);
+    };
+    std::vector<char> done(nn, 0);
+    std::function<void(int)> visit = [&](int id) {
+      if (done[id]) return;
+      done[id] = 1;
+      const Node& nd = *B.nodes[id];
+      for (int k : nd.kids) visit(k);
+      for (int k : nd.kids) use(B.nodes[k]->mask);
+      use(nd.mask);
+    };
+    for (int i : orders[0]) {
+      for (int k : B.amps[i].kids) visit(k);
+      for (int k : B.amps[i].kids) use(B.nodes[k]->mask);
+    }
+    if (canon.size() != P.masks.size()) throw std::runtime_error("generator: mask table mismatch");
     std::vector<uint16_t> remap(P.masks.size());
-    for (size_t r = 0; r < P.masks.size(); ++r)
-      remap[r] = (uint16_t)(std::lower_bound(sorted.begin(), sorted.end(), P.masks[r],
-                                             [](uint32_t a, uint32_t b) {
-                                               const int pa = __builtin_popcount(a), pb = __builtin_popcount(b);
-                                               return pa != pb ? pa < pb : a < b;
-                                             }) -
-                            sorted.begin());
+    for (size_t r = 0; r < P.masks.size(); ++r) {
+      auto it = rank.find(P.masks[r]);
+      if (it == rank.end()) throw std::runtime_error("generator: mask outside the canonical table");
+      remap[r] = (uint16_t)it->second;
+    }
     for (Op& op : P.ops) {
       for (int k = 0; k < 4; ++k) op.min[k] = remap[op.min[k]];
       op.mout = remap[op.mout];
     }
-    P.masks = sorted;
+    P.masks = canon;
   }
   if (n_slots > 65535 || P.masks.size() > 65535 || B.n_colour > 65535)
     throw std::runtime_error("generator: program too large");
