@@ -97,10 +97,12 @@ typedef struct {
                             before evaluating; 0: off */
   int kernel_variant;    /* straight-line kernels (processes with up to five partons),
                             MEA_PREC_MIXED: 0 (default) the tuned or heuristic variant;
-                            1 / 2 the body with shared vertex partials at 128 / 85
-                            registers per thread, 3 / 4 the body with one vertex call
-                            per diagram at 128 / 85 (pins the rounding order for
-                            reproducible results); other values -> MEA_E_ARG */
+                            1..6 pin one (planning and tuning then use only it):
+                            1 / 2 at 128 registers per thread, 3 / 4 at 85, 5 / 6 at
+                            168, the odd ones the body with shared vertex partials, the
+                            even ones the body with one vertex call per diagram (pins
+                            the rounding order for reproducible results); other
+                            values -> MEA_E_ARG */
 } mea_options;
 
 /* Per-event flag bits written to flags_dev. */
@@ -216,7 +218,7 @@ typedef struct {
   double best_ms;        /* time of the chosen configuration on the sample */
   double default_ms;     /* time of the heuristic default on the sample */
   int register_cap;      /* straight-line kernels: registers per thread of the
-                            chosen variant (128 or 85); 0 for the interpreter */
+                            chosen variant (128, 85 or 168); 0 for the interpreter */
   int vertex_partials;   /* 1: diagrams sharing a vertex partial use it (always
                             for the interpreter and FP64); 0: the straight-line
                             body with one vertex call per diagram was faster */

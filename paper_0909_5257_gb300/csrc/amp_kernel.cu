@@ -451,10 +451,10 @@ const GenEntry* find_generated(const int* pdg, int n_ext) {
 // -- is the same on every run.
 static int gen_body_variant(const DevProgram& p, int cap) {
   cudaFuncAttributes with, without;
-  if (cudaFuncGetAttributes(&with, p.gen->kernel(false, cap)) != cudaSuccess ||
-      cudaFuncGetAttributes(&without, p.gen->kernel(false, cap + 2)) != cudaSuccess)
-    return cap;
-  return without.localSizeBytes < with.localSizeBytes ? cap + 2 : cap;
+  if (cudaFuncGetAttributes(&with, p.gen->kernel(false, 2 * cap)) != cudaSuccess ||
+      cudaFuncGetAttributes(&without, p.gen->kernel(false, 2 * cap + 1)) != cudaSuccess)
+    return 2 * cap;
+  return without.localSizeBytes < with.localSizeBytes ? 2 * cap + 1 : 2 * cap;
 }
 
 static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms) {
@@ -465,7 +465,7 @@ static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n
   const int tab_stride = event_table_stride(p.n_ext, p.n_masks);
   double best_score = -1;
   // default: the 128-register variant (mea_autotune also tries 85 registers)
-  const int regvar = fp64 ? 0 : gen_body_variant(p, 0);
+  const int regvar = fp64 ? 0 : (p.gen_forced >= 0 ? p.gen_forced : gen_body_variant(p, 0));
   const void* k = p.gen->kernel(fp64, regvar);
   cudaFuncAttributes fa;
   int max_threads = 256;
@@ -562,11 +562,11 @@ std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, 
     return c;
   };
   if (p.gen) {
-    // FP64: one variant; FP32: both register caps, each with its body (see
+    // FP64: one variant; FP32: every register cap, each with its body (see
     // gen_body_variant)
-    const int n_caps = fp64 ? 1 : 2;
+    const int n_caps = (fp64 || p.gen_forced >= 0) ? 1 : kGenCaps;
     for (int cap_i = 0; cap_i < n_caps; ++cap_i) {
-    const int rv = fp64 ? 0 : gen_body_variant(p, cap_i);
+    const int rv = fp64 ? 0 : (p.gen_forced >= 0 ? p.gen_forced : gen_body_variant(p, cap_i));
     const void* k = p.gen->kernel(fp64, rv);
     cudaFuncAttributes fa;
     int max_threads = 256;

@@ -261,7 +261,6 @@ mea_status do_evaluate(mea_process_s* P, mea::EvalScratch& S, const double* mom,
     int64_t tiles = (n + c.E_cta - 1) / c.E_cta;
     if (tiles < c.grid) c.grid = (int)std::max<int64_t>(tiles, 1);
   }
-  if (!fp64 && P->dev.gen && P->opts.kernel_variant > 0) c.regvar = P->opts.kernel_variant - 1;
   mea::AmpLaunch a;
   a.mom = mom;
   a.n_events = n;
@@ -443,6 +442,7 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
   D.hel_all = dhall;
   D.g = std::sqrt(4.0 * M_PI * P->opts.alpha_s);
   D.gen = (P->opts.colour_mode == 2) ? nullptr : mea::find_generated(pdg, n_ext);
+  D.gen_forced = (D.gen && P->opts.kernel_variant > 0) ? P->opts.kernel_variant - 1 : -1;
   {
     // colour matrix as tensor-core operand tiles, and the status word
     mea::ColourTiles T = mea::build_colour_tiles(G.cf_jamp, G.n_jamp);

@@ -195,8 +195,8 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
     out->candidates = (int)cands.size();
     out->best_ms = best;
     out->default_ms = def_ms;
-    out->register_cap = dp.gen ? ((!fp64 && (c.regvar & 1)) ? 85 : 128) : 0;
-    out->vertex_partials = (dp.gen && !fp64 && c.regvar >= 2) ? 0 : 1;
+    out->register_cap = dp.gen ? (fp64 ? 128 : mea::kGenCapRegisters[c.regvar / 2]) : 0;
+    out->vertex_partials = (dp.gen && !fp64 && (c.regvar & 1)) ? 0 : 1;
   }
   return MEA_OK;
 }

@@ -200,17 +200,20 @@ int main(int argc, char** argv) {
     std::fclose(f);
     return true;
   };
-  // (suffix, real type, body, register-cap MINB): regvar 0..3 FP32, then FP64
+  // (suffix, real type, body, MINB, MAXT): the FP32 variants in regvar order
+  // (2 * cap + body, kernels.h), then the FP64 one
   struct Variant {
     const char* suffix;
     const char* real;
     bool partials;
-    int minb;
+    int minb, maxt;
   };
   static const Variant kVariants[] = {
-      {"f_part_128", "float", true, 2}, {"f_part_85", "float", true, 3},
-      {"f_diag_128", "float", false, 2}, {"f_diag_85", "float", false, 3},
-      {"d_part_128", "double", true, 2}};
+      {"f_part_128", "float", true, 2, 256},  {"f_diag_128", "float", false, 2, 256},
+      {"f_part_85", "float", true, 3, 256},   {"f_diag_85", "float", false, 3, 256},
+      {"f_part_168", "float", true, 2, 192},  {"f_diag_168", "float", false, 2, 192},
+      {"d_part_128", "double", true, 2, 256}};
+  const int n_f32 = 6;
   std::ostringstream t;
   t << "// Generated by mea_codegen; do not edit.\n#include \"kernels.h\"\n\nnamespace mea {\n\n";
   std::vector<std::string> ids, pdg_keys;
@@ -236,35 +239,35 @@ int main(int argc, char** argv) {
     for (const Variant& v : kVariants) {
       const std::string fn = id + "_" + v.suffix;
       const std::string body = std::string(v.partials ? "Body_" : "BodyN_") + id + "<" + v.real + ">";
-      const std::string inst = std::string("gen_kernel<") + v.real + ", " + body + ", " + std::to_string(v.minb) + ">";
+      const std::string targs = std::string(v.real) + ", " + body + ", " + std::to_string(v.minb) + ", " +
+                                std::to_string(v.maxt);
+      const std::string inst = "gen_kernel<" + targs + ">";
       std::ostringstream o;
       o << "// Generated by mea_codegen from the process generator; do not edit.\n"
            "#include \"gen_kernel.cuh\"\n\nnamespace mea {\nnamespace {\n\n"
         << (v.partials ? body_part.str() : body_diag.str()) << "}  // namespace\n\n";
       o << "void gen_launch_" << fn << "(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {\n"
-        << "  gen_launch_v<" << v.real << ", " << body << ", " << v.minb << ">(p, c, a, s);\n}\n";
+        << "  gen_launch_v<" << targs << ">(p, c, a, s);\n}\n";
       o << "const void* gen_kernel_" << fn << "() { return reinterpret_cast<const void*>(" << inst << "); }\n\n"
         << "}  // namespace mea\n";
       if (!write(dir + "/generated_" + fn + ".cu", o.str())) return 1;
       t << "void gen_launch_" << fn << "(const DevProgram&, const AmpConfig&, const AmpLaunch&, cudaStream_t);\n"
         << "const void* gen_kernel_" << fn << "();\n";
     }
-    // dispatch: regvar 0..3 are the FP32 variants in kVariants order
+    // dispatch: regvar 0..n_f32-1 are the FP32 variants in kVariants order
     t << "static void launch_" << id << "(bool fp64, int regvar, const DevProgram& p, const AmpConfig& c, "
          "const AmpLaunch& a, cudaStream_t s) {\n"
-      << "  if (fp64) return gen_launch_" << id << "_d_part_128(p, c, a, s);\n"
-      << "  switch (regvar) {\n"
-      << "    case 1: return gen_launch_" << id << "_f_part_85(p, c, a, s);\n"
-      << "    case 2: return gen_launch_" << id << "_f_diag_128(p, c, a, s);\n"
-      << "    case 3: return gen_launch_" << id << "_f_diag_85(p, c, a, s);\n"
-      << "    default: return gen_launch_" << id << "_f_part_128(p, c, a, s);\n  }\n}\n";
+      << "  if (fp64) return gen_launch_" << id << "_" << kVariants[n_f32].suffix << "(p, c, a, s);\n"
+      << "  switch (regvar) {\n";
+    for (int k = 1; k < n_f32; ++k)
+      t << "    case " << k << ": return gen_launch_" << id << "_" << kVariants[k].suffix << "(p, c, a, s);\n";
+    t << "    default: return gen_launch_" << id << "_" << kVariants[0].suffix << "(p, c, a, s);\n  }\n}\n";
     t << "static const void* kernel_" << id << "(bool fp64, int regvar) {\n"
-      << "  if (fp64) return gen_kernel_" << id << "_d_part_128();\n"
-      << "  switch (regvar) {\n"
-      << "    case 1: return gen_kernel_" << id << "_f_part_85();\n"
-      << "    case 2: return gen_kernel_" << id << "_f_diag_128();\n"
-      << "    case 3: return gen_kernel_" << id << "_f_diag_85();\n"
-      << "    default: return gen_kernel_" << id << "_f_part_128();\n  }\n}\n\n";
+      << "  if (fp64) return gen_kernel_" << id << "_" << kVariants[n_f32].suffix << "();\n"
+      << "  switch (regvar) {\n";
+    for (int k = 1; k < n_f32; ++k)
+      t << "    case " << k << ": return gen_kernel_" << id << "_" << kVariants[k].suffix << "();\n";
+    t << "    default: return gen_kernel_" << id << "_" << kVariants[0].suffix << "();\n  }\n}\n\n";
     ids.push_back(id);
     pdg_keys.push_back(key_of(pdg));
   }

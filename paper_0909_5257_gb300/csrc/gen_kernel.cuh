@@ -64,17 +64,19 @@ __device__ __forceinline__ cx<R> jfin(cx<R> hi, cx<R> lo) {
   return hi;
 }
 
-// Register-cap variants: MINB resident CTAs of kGenMaxThreads per SM caps a
-// thread at 65536 / (256 MINB) registers.  Spilling part of the long
-// straight-line body to L1 in exchange for two or three times the resident
-// warps wins for the 3-jet bodies (measured on 2^20 events: gg>ggg 14.4 ms at
-// 255 registers, 11.3 ms at 128; uu>uug 2.6 ms at 128, 2.25 ms at 85), so the
-// FP32 bodies come in a 128- and an 85-register variant (the autotuner picks)
-// and the FP64 bodies in the 128-register one.  A module that also held
-// uncapped FP32 variants measured 25-45 % slower on the same 128-register
-// kernel, so none is built.
-template <typename R, typename Body, int MINB>
-__global__ void __launch_bounds__(kGenMaxThreads, MINB) gen_kernel(const DevProgram P, const AmpLaunch A,
+// Register-cap variants: MINB resident CTAs of MAXT threads per SM cap a
+// thread at 65536 / (MAXT MINB) registers.  Spilling part of the long
+// straight-line body to L1 in exchange for more resident warps wins for the
+// 3-jet bodies (measured on 2^20 events: gg>ggg 14.4 ms at 255 registers,
+// 11.3 ms at 128; uu>uug 2.6 ms at 128, 2.25 ms at 85), so the FP32 bodies
+// come at 128 (256 threads, MINB 2), 85 (256, 3) and 168 (192, 2) registers --
+// the last halves the gg>ggg spill footprint (640 against 936 bytes per
+// thread) so that it stays in L1 with 10 resident warps -- and the autotuner
+// picks; the FP64 bodies come at 128.  A module that also held uncapped FP32
+// variants measured 25-45 % slower on the same 128-register kernel, so none
+// is built.
+template <typename R, typename Body, int MINB, int MAXT>
+__global__ void __launch_bounds__(MAXT, MINB) gen_kernel(const DevProgram P, const AmpLaunch A,
                                                                    const AmpConfig C) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr bool F32 = std::is_same<R, float>::value;
@@ -128,11 +130,12 @@ __global__ void __launch_bounds__(kGenMaxThreads, MINB) gen_kernel(const DevProg
   }
 }
 
-template <typename R, typename Body, int MINB>
+template <typename R, typename Body, int MINB, int MAXT>
 void gen_launch_v(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
-  cudaFuncSetAttribute(gen_kernel<R, Body, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-  cudaFuncSetAttribute(gen_kernel<R, Body, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_percent(c));
-  gen_kernel<R, Body, MINB><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
+  auto k = gen_kernel<R, Body, MINB, MAXT>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_percent(c));
+  k<<<c.grid, c.threads, c.smem, s>>>(p, a, c);
 }
 
 // Each kernel variant of a process -- FP32 body with vertex partials at 128 /

@@ -16,13 +16,15 @@ struct AmpLaunch;
 // A straight-line per-process kernel emitted by codegen.cpp at build time.
 struct GenEntry {
   const char* key;  // PDG codes joined by commas
-  // regvar: variant of the FP32 kernel -- 0 / 1 body with vertex partials at
-  // 128 / 85 registers per thread, 2 / 3 body with one vertex call per diagram
-  // at 128 / 85; the FP64 kernel has one variant (partials, 128)
+  // regvar: variant of the FP32 kernel, 2 * cap + body -- cap 0 / 1 / 2 =
+  // 128 / 85 / 168 registers per thread, body 0 with vertex partials, 1 with
+  // one vertex call per diagram; the FP64 kernel has one variant (partials, 128)
   void (*launch)(bool fp64, int regvar, const DevProgram&, const AmpConfig&, const AmpLaunch&, cudaStream_t);
   const void* (*kernel)(bool fp64, int regvar);
 };
-constexpr int kGenRegVariants = 4;
+constexpr int kGenCaps = 3;
+constexpr int kGenRegVariants = 2 * kGenCaps;
+constexpr int kGenCapRegisters[kGenCaps] = {128, 85, 168};
 const GenEntry* generated_table(int* n);
 const GenEntry* find_generated(const int* pdg, int n_ext);
 
@@ -45,6 +47,7 @@ struct DevProgram {
   const int8_t* hel_all = nullptr;    // [2^n_ext][n_ext]
   double g = 0;                       // g_s
   const GenEntry* gen = nullptr;      // straight-line kernel of this process, if emitted
+  int gen_forced = -1;                // FP32 variant pinned by mea_options.kernel_variant (-1: free)
   const float* amp_w = nullptr;       // [n_diagrams] sum_alpha |c_alpha d| (amplitude-output mode)
 };
 
