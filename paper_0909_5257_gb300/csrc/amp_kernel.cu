@@ -464,7 +464,7 @@ static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n
   best.slots_in_smem = true;
   const int tab_stride = event_table_stride(p.n_ext, p.n_masks);
   double best_score = -1;
-  // default: the 128-register variant (mea_autotune also tries 85 registers)
+  // default: the 128-register variant (mea_autotune also tries 85 and 168 registers)
   const int regvar = fp64 ? 0 : (p.gen_forced >= 0 ? p.gen_forced : gen_body_variant(p, 0));
   const void* k = p.gen->kernel(fp64, regvar);
   cudaFuncAttributes fa;

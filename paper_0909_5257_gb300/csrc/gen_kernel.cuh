@@ -138,13 +138,11 @@ void gen_launch_v(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, c
   k<<<c.grid, c.threads, c.smem, s>>>(p, a, c);
 }
 
-// Each kernel variant of a process -- FP32 body with vertex partials at 128 /
-// 85 registers (regvar 0 / 1), FP32 body with one vertex call per diagram at
-// 128 / 85 (regvar 2 / 3), FP64 body with partials at 128 -- is instantiated
-// in a translation unit (device module) of its own by codegen.cpp, behind two
-// plain functions: gen_launch_v and the kernel's address.  One variant's code
-// then does not change where another's lands: the 3-jet straight-line kernels
-// are instruction-fetch bound, and their speed moved by up to 20 % with the
-// other code around them in a shared module.
+// Each kernel variant of a process -- the FP32 bodies (with vertex partials
+// or one vertex call per diagram) at 128, 85 and 168 registers, numbered
+// 2 * cap + body (kernels.h), and the FP64 body with partials at 128 -- is
+// instantiated in a translation unit (device module) of its own by
+// codegen.cpp, behind two plain functions: gen_launch_v and the kernel's
+// address.  Separate units compile in parallel.
 }  // namespace
 }  // namespace mea

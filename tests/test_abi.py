@@ -96,3 +96,26 @@ def test_host_only_handle_refuses_evaluation():
     with pytest.raises(mea.MeaError) as e:
         P.evaluate(0, 0, n_events=1)
     assert e.value.status == -2
+
+
+def test_kernel_variant_out_of_range_is_an_argument_error():
+    """mea_options.kernel_variant is checked before any device work."""
+    from paper_0909_5257_gb300 import mea
+    for v in (-1, 7):
+        with pytest.raises(mea.MeaError) as e:
+            mea.Process([21] * 5, kernel_variant=v)
+        assert e.value.status == -1
+
+
+def test_vertex_partials_reduce_the_flop_count():
+    """The program shares vertex partials (fewer FLOPs than one vertex call
+    per diagram) where diagrams share all amplitude-vertex inputs but one; the
+    2 -> 2 processes have no such groups.  Counts from the op costs of
+    heget.cuh: gg>ggg 13 098 -> 9 514, gg>gggg 147 957 -> 85 107 per helicity."""
+    from paper_0909_5257_gb300 import mea
+    for pdg, plain, part in (([21] * 5, 13098, 9514), ([21] * 6, 147957, 85107)):
+        info = mea.Process(pdg, host_only=True).info
+        assert info["flops_per_hel_plain"] == plain
+        assert info["flops_per_hel"] == part
+    info = mea.Process([21] * 4, host_only=True).info
+    assert info["flops_per_hel"] == info["flops_per_hel_plain"]
