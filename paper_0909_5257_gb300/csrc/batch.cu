@@ -94,11 +94,19 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
       mea::candidate_configs(dp, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
   mea::AmpConfig def = mea::plan_amp(dp, fp64, H, n, P->num_sms, P->smem_optin, P->smem_per_sm);
   cands.insert(cands.begin(), def);
-  cudaStream_t s;
-  MEA_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-  cudaEvent_t e0, e1;
-  MEA_CK(cudaEventCreate(&e0));
-  MEA_CK(cudaEventCreate(&e1));
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  {
+    cudaError_t ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {  // release what this call holds before reporting
+      if (e0) cudaEventDestroy(e0);
+      if (s) cudaStreamDestroy(s);
+      abuf.release(); rowmax.release(); pairk.release(); evf.release();
+      return mea::set_error(MEA_E_CUDA, std::string("mea_autotune: ") + cudaGetErrorString(ce));
+    }
+  }
   // Every timed launch starts with a cold L2 (a buffer of twice the L2 is
   // written before it), as in an evaluation that follows other work: a
   // kernel timed back to back on its own input finds that input and its own
