@@ -75,6 +75,21 @@ def outgoing_helicities(hel_index, n_ext):
 
 
 # ------------------------------------------------------------- Parke-Taylor
+def quark_line_mhv_sq(k, order, q_minus, q_plus, g_minus):
+    """|A(order)|^2 of the colour-ordered MHV amplitude with one quark line:
+    all-outgoing antiquark/quark legs q_minus (helicity -) and q_plus (+), one
+    negative-helicity gluon g_minus, the rest positive:
+    |s_{q- g-}|^3 |s_{q+ g-}| / |s_12 s_23 ... s_n1| over the cyclic order
+    (quark pair adjacent), normalisation Tr(T^a T^b) = delta^{ab}."""
+    def s(a, b):
+        return abs(mdot(k[a] + k[b], k[a] + k[b]))
+    den = 1.0
+    n = len(order)
+    for a in range(n):
+        den *= s(order[a], order[(a + 1) % n])
+    return s(q_minus, g_minus) ** 3 * s(q_plus, g_minus) / den
+
+
 def parke_taylor_sq(k, order, neg):
     """|A(order)|^2 for the MHV configuration whose two negative-helicity legs
     (all-outgoing convention) are `neg`: s_ij^4 / |s_12 s_23 ... s_n1|,

@@ -1,7 +1,7 @@
 """The pins catch plausible mistakes: each test builds a copy of the oracle
 with one deliberate mistake planted (OQ_MUTATION in qcd_oracle.cpp) and checks
-that the battery of pins -- closed forms, Parke-Taylor, Ward identities, Bose
-symmetry -- rejects it, while the unmutated copy passes the same battery.
+that the battery of pins -- closed forms, Parke-Taylor (gluons and one quark line),
+Ward identities, Bose symmetry -- rejects it, while the unmutated copy passes the same battery.
 
 Mutations: 1 a dropped term of the ggg vertex, 2 a flipped sign of one gggg
 colour structure, 3 the metric dropped from the gluon propagator (index slip),
@@ -54,6 +54,25 @@ def _battery(lib):
                     bad = True
         if bad:
             failed.append(f"Ward identity {pdg}")
+    P = oracle.OracleProcess([2, -2, 21, 21, 21], lib=lib)
+    g = ref.g_s()
+    orders = [P.basis(a)[0][3] for a in range(P.n_colour)]
+    k = ref.all_outgoing(mom3[0])
+    bad = False
+    for hel in range(32):
+        ho = ref.outgoing_helicities(hel, 5)
+        neg = [i for i in range(5) if ho[i] < 0]
+        if len(neg) != 2 or ho[0] == ho[1]:
+            continue
+        qm = 0 if ho[0] < 0 else 1
+        gm = [i for i in neg if i >= 2][0]
+        J = P.jamp(mom3[0], hel)
+        for a, gl in enumerate(orders):
+            a2 = ref.quark_line_mhv_sq(k, [0, 1] + gl, qm, 1 - qm, gm)
+            if not abs(abs(J[a]) ** 2 / (g ** 6 * 8 * a2) - 1.0) < 1e-10:
+                bad = True
+    if bad:
+        failed.append("quark-line MHV uu~>ggg")
     P = oracle.OracleProcess([21] * 5, lib=lib)
     base = P.me2(mom3)
     if not np.allclose(P.me2(mom3[:, [0, 1, 4, 2, 3]]), base, rtol=1e-12, atol=0):

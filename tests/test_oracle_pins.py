@@ -183,6 +183,39 @@ def test_mhv_partial_amplitudes(n_ext):
                 assert abs(abs(J[a]) ** 2 / (g ** (2 * n_ext - 4) * 2 ** n_ext * pt) - 1.0) < 1e-10
 
 
+@pytest.mark.parametrize("n_ext", [5, 6, 7])
+def test_quark_line_mhv_partial_amplitudes(n_ext):
+    """u u~ -> (n-2) g: for every string-basis ordering (T^{a_s1}...T^{a_sk})
+    and every MHV helicity configuration with the negative helicities on one
+    quark and one gluon, |J_alpha|^2 = g^{2n-4} 2^{n-2} |A|^2 with A the
+    colour-ordered one-quark-line MHV amplitude in the cyclic order
+    (leg 0, leg 1, s1, ..., sk) of the crossed momenta (textbook closed form;
+    2^{n-2} from Tr(T^a T^b) = delta/2 on the n-2 gluon generators).  Pins
+    the qqg vertex, the spinors and quark propagators, and the colour strings,
+    for every diagram of the process."""
+    pdg = [2, -2] + [21] * (n_ext - 2)
+    P = proc(pdg)
+    mom = events(n_ext - 2, 2 if n_ext < 7 else 1, lo=300.0, hi=3000.0, seed=ps.SEED_BASE + 5)
+    g = ref.g_s()
+    orders = [P.basis(a)[0][3] for a in range(P.n_colour)]
+    checked = 0
+    for m in mom:
+        k = ref.all_outgoing(m)
+        for hel in range(1 << n_ext):
+            ho = ref.outgoing_helicities(hel, n_ext)
+            neg = [i for i in range(n_ext) if ho[i] < 0]
+            if len(neg) != 2 or ho[0] == ho[1]:
+                continue
+            q_minus = 0 if ho[0] < 0 else 1
+            g_minus = [i for i in neg if i >= 2][0]
+            J = P.jamp(m, hel)
+            for a, gl in enumerate(orders):
+                a2 = ref.quark_line_mhv_sq(k, [0, 1] + gl, q_minus, 1 - q_minus, g_minus)
+                assert abs(abs(J[a]) ** 2 / (g ** (2 * n_ext - 4) * 2 ** (n_ext - 2) * a2) - 1.0) < 1e-10
+                checked += 1
+    assert checked >= P.n_colour * 2 * (n_ext - 2)
+
+
 # ------------------------------------------------------------ helicity zeros
 def _allowed(pdg, hel):
     n = len(pdg)
