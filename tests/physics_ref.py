@@ -192,6 +192,86 @@ def bg_amplitude(k, eps, order):
     return mdot(vertices(0, n - 2), eps[order[-1]])
 
 
+# -------------------------------------------- Berends-Giele, one quark line
+# Dirac matrices in the chiral representation (upper two components
+# left-handed), built here independently of the oracle.
+_SIG = [np.array([[0, 1], [1, 0]], dtype=complex), np.array([[0, -1j], [1j, 0]], dtype=complex),
+        np.array([[1, 0], [0, -1]], dtype=complex)]
+_Z2 = np.zeros((2, 2), dtype=complex)
+_GAMMA = [np.block([[_Z2, np.eye(2)], [np.eye(2), _Z2]]).astype(complex)] + \
+         [np.block([[_Z2, s], [-s, _Z2]]) for s in _SIG]
+
+
+def slash(v):
+    """gamma^mu v_mu for an upper-index (complex) 4-vector v."""
+    return _GAMMA[0] * v[0] - _GAMMA[1] * v[1] - _GAMMA[2] * v[2] - _GAMMA[3] * v[3]
+
+
+def _helicity_spinor(pvec, lam):
+    """Two-component helicity eigenstate of sigma.p_hat with eigenvalue lam."""
+    p = np.linalg.norm(pvec)
+    th = math.acos(max(-1.0, min(1.0, pvec[2] / p)))
+    ph = math.atan2(pvec[1], pvec[0])
+    if lam > 0:
+        return np.array([math.cos(th / 2), np.exp(1j * ph) * math.sin(th / 2)])
+    return np.array([-np.exp(-1j * ph) * math.sin(th / 2), math.cos(th / 2)])
+
+
+def u_spinor(p, lam):
+    """Massless Dirac spinor u(p, lam): left-handed (upper) for lam = -1."""
+    r = math.sqrt(2.0 * p[0])
+    c = _helicity_spinor(p[1:], lam)
+    return r * np.concatenate([c, [0, 0]]) if lam < 0 else r * np.concatenate([[0, 0], c])
+
+
+def vbar_spinor(p, lam):
+    """v-bar(p, lam) = v^dagger gamma^0 with v(p, lam) = u(p, -lam) up to a phase."""
+    return u_spinor(p, -lam).conj() @ _GAMMA[0]
+
+
+def bg_quark_line_amplitude(mom, eps, gluons, ubar_left, u_right):
+    """Colour-ordered amplitude of one quark line with gluons attached in the
+    order `gluons` (the order of the generators in the colour string, read from
+    the barred end), by the Berends-Giele recursion with colour-ordered rules:
+    qqg vertex (i/sqrt2) gamma^mu, quark propagator i P-slash / P^2, the gluon
+    sub-currents of consecutive gluons as in bg_amplitude.  mom: physical
+    momenta [n, 4] (leg 0 the incoming quark, gluons outgoing); eps: outgoing
+    gluon polarisation vectors by leg; ubar_left / u_right: the external
+    spinors at the two ends of the line.  Normalisation Tr(T T) = delta."""
+    kg = len(gluons)
+
+    @lru_cache(maxsize=None)
+    def J(i, j):
+        if i == j:
+            return eps[gluons[i]]
+        P = sum(mom[gluons[x]] for x in range(i, j + 1))
+        acc = np.zeros(4, dtype=complex)
+        for m in range(i, j):
+            Pa = sum(mom[gluons[x]] for x in range(i, m + 1))
+            Pb = sum(mom[gluons[x]] for x in range(m + 1, j + 1))
+            acc = acc + _v3(Pa, Pb, J(i, m), J(m + 1, j))
+        for m in range(i, j):
+            for l in range(m + 1, j):
+                acc = acc + _v4(J(i, m), J(m + 1, l), J(l + 1, j))
+        return (-1j / mdot(P, P)) * acc
+
+    @lru_cache(maxsize=None)
+    def R(j):
+        """Column spinor of the line from gluon j to the unbarred end."""
+        if j == kg:
+            return u_right
+        acc = np.zeros(4, dtype=complex)
+        for m in range(j, kg):
+            rest = R(m + 1)
+            if m + 1 < kg:  # quark propagator between this block and the next
+                Pq = mom[0] - sum(mom[gluons[x]] for x in range(m + 1, kg))
+                rest = (1j * slash(Pq) / mdot(Pq, Pq)) @ rest
+            acc = acc + (1j / math.sqrt(2.0)) * (slash(J(j, m)) @ rest)
+        return acc
+
+    return ubar_left @ R(0)
+
+
 # --------------------------------------------------------------- Gell-Mann
 def gell_mann_T():
     l = np.zeros((8, 3, 3), dtype=complex)
