@@ -330,6 +330,8 @@ typedef struct {
   int n_final;          /* 2..8 */
   double rs_lo, rs_hi;  /* sqrt(s_hat) log-uniform range, GeV */
   double pt_min, eta_max, dr_min;
+  double ptij_min;      /* GeV: min(pT_i, pT_j) Delta R_ij > ptij_min for every pair
+                           (Eq. (cuts-ptjj)); <= 0 off */
 } mea_ps_config;
 
 /* momenta_dev[n][2 + n_final][4] <- events first_event .. first_event+n-1 of

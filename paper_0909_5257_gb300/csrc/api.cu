@@ -789,7 +789,8 @@ mea_status mea_generate_phase_space(const mea_ps_config* cfg, uint64_t first_eve
     return fail(MEA_E_ARG, "mea_generate_phase_space: bad configuration");
   if (n == 0) return MEA_OK;
   if (!mom) return fail(MEA_E_ARG, "mea_generate_phase_space: null momenta");
-  mea::PsConfigDev c{cfg->seed, cfg->n_final, cfg->rs_lo, cfg->rs_hi, cfg->pt_min, cfg->eta_max, cfg->dr_min};
+  mea::PsConfigDev c{cfg->seed, cfg->n_final, cfg->rs_lo, cfg->rs_hi, cfg->pt_min, cfg->eta_max, cfg->dr_min,
+                     cfg->ptij_min};
   MEA_CUDA(mea::launch_phase_space(c, first_event, n, mom, attempts, reinterpret_cast<cudaStream_t>(stream)));
   return MEA_OK;
 }
@@ -826,7 +827,7 @@ mea_status mea_partonic_cross_section(mea_process_t P, double sqrt_s, const mea_
   MEA_CUDA(pa.ensure(sizeof(long long) * 2 * kBlocks));
   cudaStream_t s;
   MEA_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-  mea::PsConfigDev c{cuts->seed, nf, sqrt_s, sqrt_s, cuts->pt_min, cuts->eta_max, cuts->dr_min};
+  mea::PsConfigDev c{cuts->seed, nf, sqrt_s, sqrt_s, cuts->pt_min, cuts->eta_max, cuts->dr_min, cuts->ptij_min};
   double sum_f = 0.0, sum_f2 = 0.0;
   long long drawn = 0, accepted = 0;
   std::vector<double> hf(kBlocks), hf2(kBlocks);

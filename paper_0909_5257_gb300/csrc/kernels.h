@@ -116,7 +116,7 @@ cudaError_t launch_finish(const AmpLaunch& a, int H, const double* pairval, cons
 struct PsConfigDev {
   uint64_t seed;
   int n_final;
-  double rs_lo, rs_hi, pt_min, eta_max, dr_min;
+  double rs_lo, rs_hi, pt_min, eta_max, dr_min, ptij_min;
 };
 cudaError_t launch_phase_space(const PsConfigDev& cfg, uint64_t first_event, int64_t n,
                                double* mom, int32_t* attempts, cudaStream_t s);

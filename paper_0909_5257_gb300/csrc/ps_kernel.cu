@@ -79,6 +79,7 @@ cudaError_t launch_phase_space(const PsConfigDev& c, uint64_t first_event, int64
   cfg.pt_min = c.pt_min;
   cfg.eta_max = c.eta_max;
   cfg.dr_min = c.dr_min;
+  cfg.ptij_min = c.ptij_min;
   const int threads = 128;
   int64_t blocks = (n + threads - 1) / threads;
   ps_kernel<<<(unsigned)blocks, threads, 0, s>>>(cfg, first_event, n, mom, attempts);

@@ -70,7 +70,7 @@ class ServerStats(ctypes.Structure):
 class PsConfig(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("n_final", ctypes.c_int), ("rs_lo", ctypes.c_double),
                 ("rs_hi", ctypes.c_double), ("pt_min", ctypes.c_double), ("eta_max", ctypes.c_double),
-                ("dr_min", ctypes.c_double)]
+                ("dr_min", ctypes.c_double), ("ptij_min", ctypes.c_double)]
 
 
 def load(path: str | None = None):
@@ -238,10 +238,11 @@ class Process:
                                            _ptr(flags), _stream(stream)))
 
     def partonic_cross_section(self, sqrt_s, n_events, seed=0x09095257, first_event=0, pt_min=20.0,
-                               eta_max=2.5, dr_min=0.4, precision=PREC_FP64):
+                               eta_max=2.5, dr_min=0.4, precision=PREC_FP64, ptij_min=0.0):
         """sigma_hat at fixed sqrt(s_hat) in pb with its statistical error
-        (mea_partonic_cross_section): generator events first_event .. + n_events."""
-        cfg = PsConfig(seed, self.n_ext - 2, sqrt_s, sqrt_s, pt_min, eta_max, dr_min)
+        (mea_partonic_cross_section): generator events first_event .. + n_events.
+        ptij_min > 0 adds the paper's relative-pT cut min(pT_i, pT_j) Delta R_ij."""
+        cfg = PsConfig(seed, self.n_ext - 2, sqrt_s, sqrt_s, pt_min, eta_max, dr_min, ptij_min)
         r = XsecResult()
         _check(load().mea_partonic_cross_section(self._h, ctypes.c_double(sqrt_s), ctypes.byref(cfg),
                                                  ctypes.c_uint64(first_event), n_events, precision,
@@ -272,8 +273,8 @@ class Process:
 
 def generate_phase_space(n_final, n, momenta, first_event=0, seed=0x09095257, rs_lo=200.0,
                          rs_hi=2000.0, pt_min=20.0, eta_max=2.5, dr_min=0.4, attempts=None,
-                         stream=None):
-    cfg = PsConfig(seed, n_final, rs_lo, rs_hi, pt_min, eta_max, dr_min)
+                         stream=None, ptij_min=0.0):
+    cfg = PsConfig(seed, n_final, rs_lo, rs_hi, pt_min, eta_max, dr_min, ptij_min)
     _check(load().mea_generate_phase_space(ctypes.byref(cfg), first_event, n, _ptr(momenta),
                                            _ptr(attempts), _stream(stream)))
 

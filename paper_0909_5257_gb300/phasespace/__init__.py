@@ -32,14 +32,14 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("n_final", ctypes.c_int),
                 ("rs_lo", ctypes.c_double), ("rs_hi", ctypes.c_double),
                 ("pt_min", ctypes.c_double), ("eta_max", ctypes.c_double),
-                ("dr_min", ctypes.c_double)]
+                ("dr_min", ctypes.c_double), ("ptij_min", ctypes.c_double)]
 
 
 @dataclass(frozen=True)
 class PhaseSpaceConfig:
     """Synthetic partonic workload: n_final massless partons, sqrt(s_hat) in
     [rs_lo, rs_hi] GeV log-uniform, cuts pT > pt_min, |eta| < eta_max,
-    Delta R > dr_min."""
+    Delta R > dr_min and, if ptij_min > 0, min(pT_i, pT_j) Delta R_ij > ptij_min."""
     n_final: int
     rs_lo: float = 200.0
     rs_hi: float = 2000.0
@@ -47,10 +47,11 @@ class PhaseSpaceConfig:
     pt_min: float = 20.0
     eta_max: float = 2.5
     dr_min: float = 0.4
+    ptij_min: float = 0.0
 
     def as_c(self) -> _Cfg:
         return _Cfg(self.seed, self.n_final, self.rs_lo, self.rs_hi,
-                    self.pt_min, self.eta_max, self.dr_min)
+                    self.pt_min, self.eta_max, self.dr_min, self.ptij_min)
 
 
 def build(force: bool = False) -> str:

@@ -16,10 +16,11 @@
  *     (n = 2: a uniform direction, the same distribution drawn directly).
  *   - sqrt(s_hat) drawn log-uniform in [rs_lo, rs_hi]; incoming partons along
  *     +z / -z with energy sqrt(s_hat)/2 each.
- *   - Jet cuts pT > pt_min, |eta| < eta_max, Delta R > dr_min between every
- *     pair of final-state partons (the paper's Eq. (cuts) with the pT_ij cut
- *     replaced by a Delta R cut in the partonic frame).  A rejected point is
- *     redrawn completely with the next attempt counter.
+ *   - Jet cuts pT > pt_min, |eta| < eta_max and, between every pair of
+ *     final-state partons, Delta R > dr_min and (when ptij_min > 0) the
+ *     relative transverse momentum min(pT_i, pT_j) Delta R_ij > ptij_min of
+ *     the paper's Eq. (cuts-ptjj) -- Eq. (cuts) in the partonic frame.  A
+ *     rejected point is redrawn completely with the next attempt counter.
  *
  * Momentum layout: mom[leg][4] = (E, px, py, pz) in GeV, legs ordered
  * (incoming a, incoming b, outgoing 1..n).
@@ -47,6 +48,7 @@ typedef struct {
   double pt_min;     /* GeV */
   double eta_max;
   double dr_min;
+  double ptij_min;   /* GeV, <= 0: no relative-pT cut */
 } ps_config;
 
 /* ---- Philox4x32-10 ---------------------------------------------------- */
@@ -178,10 +180,11 @@ PS_HD void ps_rambo_massless(ps_stream *s, int n, double rs, double (*mom)[4]) {
 /* ---- cuts ---------------------------------------------------------------- */
 PS_HD int ps_pass_cuts(const ps_config *cfg, int n, double (*p)[4]) {
   const double pi = 3.14159265358979323846264338328;
-  double eta[PS_MAX_FINAL], phi[PS_MAX_FINAL];
+  double eta[PS_MAX_FINAL], phi[PS_MAX_FINAL], pts[PS_MAX_FINAL];
   for (int i = 0; i < n; ++i) {
     double pt = sqrt(p[i][1] * p[i][1] + p[i][2] * p[i][2]);
     if (!(pt > cfg->pt_min)) return 0;
+    pts[i] = pt;
     eta[i] = asinh(p[i][3] / pt);
     if (!(fabs(eta[i]) < cfg->eta_max)) return 0;
     phi[i] = atan2(p[i][2], p[i][1]);
@@ -192,7 +195,9 @@ PS_HD int ps_pass_cuts(const ps_config *cfg, int n, double (*p)[4]) {
       while (dphi > pi) dphi -= 2.0 * pi;
       while (dphi <= -pi) dphi += 2.0 * pi;
       double deta = eta[i] - eta[j];
-      if (!(deta * deta + dphi * dphi > cfg->dr_min * cfg->dr_min)) return 0;
+      double dr2 = deta * deta + dphi * dphi;
+      if (!(dr2 > cfg->dr_min * cfg->dr_min)) return 0;
+      if (cfg->ptij_min > 0.0 && !(fmin(pts[i], pts[j]) * sqrt(dr2) > cfg->ptij_min)) return 0;
     }
   return 1;
 }

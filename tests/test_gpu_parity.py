@@ -194,14 +194,15 @@ def test_empty_and_single_event():
 
 def test_device_generator_matches_host_generator():
     mea = _mea()
-    for nf, (lo, hi) in [(2, (200.0, 2000.0)), (3, (200.0, 2000.0)), (5, (500.0, 5000.0))]:
+    for nf, (lo, hi), dr, ptij in [(2, (200.0, 2000.0), 0.4, 0.0), (3, (200.0, 2000.0), 0.4, 0.0),
+                                   (5, (500.0, 5000.0), 0.4, 0.0), (4, (100.0, 1000.0), 0.0, 20.0)]:
         n = 4096
-        cfg = ps.PhaseSpaceConfig(nf, rs_lo=lo, rs_hi=hi, seed=ps.SEED_BASE + 3)
+        cfg = ps.PhaseSpaceConfig(nf, rs_lo=lo, rs_hi=hi, seed=ps.SEED_BASE + 3, dr_min=dr, ptij_min=ptij)
         host, att_h = ps.generate(cfg, n, first_event=1000, return_attempts=True)
         dev = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
         att = torch.empty(n, dtype=torch.int32, device="cuda")
         mea.generate_phase_space(nf, n, dev, first_event=1000, seed=cfg.seed, rs_lo=lo, rs_hi=hi,
-                                 attempts=att)
+                                 dr_min=dr, ptij_min=ptij, attempts=att)
         torch.cuda.synchronize()
         d = dev.cpu().numpy()
         same = att.cpu().numpy() == att_h

@@ -57,3 +57,31 @@ def test_sqrt_s_log_uniform():
     u = np.log((mom[att == 0, 0, 0] * 2) / 200.0) / np.log(10.0)
     hist, _ = np.histogram(u, bins=10, range=(0, 1))
     assert hist.min() > 0.85 * hist.mean()
+
+
+@pytest.mark.parametrize("n_final", [3, 4])
+def test_relative_pt_cut(n_final):
+    """The paper's Eq. (cuts-ptjj): with ptij_min every accepted event has
+    min(pT_i, pT_j) Delta R_ij > ptij_min for every pair; events whose first
+    draw already passes both cut sets are the same draw with and without it;
+    the cut removes points (more redraws)."""
+    base = ps.PhaseSpaceConfig(n_final, rs_lo=100.0, rs_hi=1000.0, dr_min=0.0)
+    cut = ps.PhaseSpaceConfig(n_final, rs_lo=100.0, rs_hi=1000.0, dr_min=0.0, ptij_min=20.0)
+    a, att_a = ps.generate(base, 4000, return_attempts=True)
+    b, att_b = ps.generate(cut, 4000, return_attempts=True)
+    assert (att_b >= 0).all()
+    fin = b[:, 2:]
+    pt = np.hypot(fin[..., 1], fin[..., 2])
+    eta = np.arcsinh(fin[..., 3] / pt)
+    phi = np.arctan2(fin[..., 2], fin[..., 1])
+    for i in range(n_final):
+        for j in range(i + 1, n_final):
+            dphi = np.angle(np.exp(1j * (phi[:, i] - phi[:, j])))
+            ptij = np.minimum(pt[:, i], pt[:, j]) * np.hypot(eta[:, i] - eta[:, j], dphi)
+            assert (ptij > 20.0).all()
+    both0 = (att_a == 0) & (att_b == 0)
+    assert both0.any() and np.array_equal(a[both0], b[both0])
+    assert att_b.sum() > att_a.sum()
+    # ptij_min <= 0 is no cut: the stream equals the default one
+    off = ps.generate(ps.PhaseSpaceConfig(n_final, rs_lo=100.0, rs_hi=1000.0, dr_min=0.0, ptij_min=0.0), 4000)
+    assert np.array_equal(off, a)

@@ -55,10 +55,11 @@ def closed_form_sigma(fn, pdg, rs, pt_min=20.0, eta_max=2.5):
     return _symmetry(pdg) / (2 * s) * integral * 2 * math.pi / (32 * math.pi ** 2) * GEV2_PB
 
 
-def oracle_sigma(pdg, rs, n, first=0, pt_min=20.0, eta_max=2.5, dr_min=0.4):
+def oracle_sigma(pdg, rs, n, first=0, pt_min=20.0, eta_max=2.5, dr_min=0.4, ptij_min=0.0):
     """The estimator on the host generator's events with the oracle's |M|^2."""
     nf = len(pdg) - 2
-    cfg = ps.PhaseSpaceConfig(nf, rs_lo=rs, rs_hi=rs, seed=SEED, pt_min=pt_min, eta_max=eta_max, dr_min=dr_min)
+    cfg = ps.PhaseSpaceConfig(nf, rs_lo=rs, rs_hi=rs, seed=SEED, pt_min=pt_min, eta_max=eta_max, dr_min=dr_min,
+                              ptij_min=ptij_min)
     mom, att = ps.generate(cfg, n, first_event=first, return_attempts=True)
     me2 = oracle.OracleProcess(pdg).me2(mom)
     ok = att >= 0
@@ -113,3 +114,18 @@ def test_gpu_cross_section_converges_to_closed_form():
     want = closed_form_sigma(ref.me2_gg_gg, [21] * 4, rs)
     assert abs(r["sigma_pb"] - want) < 5 * r["error_pb"]
     assert r["error_pb"] < 5e-3 * want
+
+
+@pytest.mark.gpu
+def test_gpu_cross_section_with_the_papers_relative_pt_cut():
+    """Eq. (cuts) as printed: pT > 20 GeV, |eta| < 2.5 and the relative
+    transverse momentum min(pT_i, pT_j) Delta R_ij > 20 GeV (no Delta R cut)."""
+    from paper_0909_5257_gb300 import mea
+    pdg, rs, n = [21] * 5, 500.0, 1 << 12
+    P = mea.Process(pdg)
+    r = P.partonic_cross_section(rs, n, seed=SEED, precision=mea.PREC_FP64, dr_min=0.0, ptij_min=20.0)
+    want, err, acc, drawn = oracle_sigma(pdg, rs, n, dr_min=0.0, ptij_min=20.0)
+    assert r["n_accepted"] == acc and r["n_drawn"] == drawn
+    assert abs(r["sigma_pb"] / want - 1.0) < 1e-10
+    loose = P.partonic_cross_section(rs, n, seed=SEED, precision=mea.PREC_FP64, dr_min=0.0)
+    assert loose["n_drawn"] < r["n_drawn"]  # the cut removes points
