@@ -367,6 +367,39 @@ mea_status mea_partonic_cross_section(mea_process_t proc, double sqrt_s, const m
                                       uint64_t first_event, int64_t n_events, mea_prec_mode prec,
                                       mea_xsec_result *out);
 
+/* The same sigma_hat by adaptive importance sampling (VEGAS, G. P. Lepage,
+ * J. Comput. Phys. 27 (1978) 192) over RAMBO's uniforms: a grid of `bins`
+ * intervals per dimension maps each uniform, points that fail the cuts weigh
+ * 0, and after every iteration each dimension's grid is refined from the sums
+ * of (weight |M|^2)^2 per interval (smoothed over neighbours, compressed with
+ * exponent alpha).  Iteration k uses generator events first_event + k *
+ * points_per_iteration onwards (the VEGAS counter range, distinct from the
+ * flat generator's); the iterations are combined with inverse-variance
+ * weights.  Points are made and |M|^2 evaluated on the device; the grid lives
+ * on the host.  Synchronous.  bins in [1, 64] (1: flat sampling without
+ * redraws), iterations >= 1, points_per_iteration >= 2, alpha >= 0;
+ * otherwise MEA_E_ARG. */
+typedef struct {
+  int iterations;
+  int64_t points_per_iteration;
+  int bins;
+  double alpha;          /* grid compression exponent; 1.5 is customary */
+} mea_vegas_config;
+
+typedef struct {
+  double sigma_pb;       /* inverse-variance weighted over the iterations */
+  double error_pb;
+  double chi2_per_dof;   /* consistency of the iterations (0 for one) */
+  double last_sigma_pb;  /* the last iteration alone */
+  double last_error_pb;
+  int64_t n_points;      /* all iterations */
+  int64_t n_accepted;    /* points that passed the cuts */
+} mea_vegas_result;
+
+mea_status mea_partonic_cross_section_vegas(mea_process_t proc, double sqrt_s, const mea_ps_config *cuts,
+                                            uint64_t first_event, const mea_vegas_config *vc,
+                                            mea_prec_mode prec, mea_vegas_result *out);
+
 /* ---- diagnostics ------------------------------------------------------------ */
 
 const char *mea_last_error(void);

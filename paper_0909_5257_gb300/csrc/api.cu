@@ -5,6 +5,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "../phasespace/phasespace.h"
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -874,3 +876,159 @@ mea_status mea_partonic_cross_section(mea_process_t P, double sqrt_s, const mea_
 }
 
 }  // extern "C"
+
+namespace {
+// One VEGAS grid refinement of one dimension (Lepage 1978): d[i] is the sum
+// of (weight f)^2 over the iteration's points in interval i; the sums are
+// smoothed over neighbours, compressed to r_i = ((1 - x_i) / ln(1 / x_i))^alpha
+// with x_i the smoothed share, and the new edges give every interval an equal
+// share of sum r, each old interval's r spread uniformly over its width.
+void vegas_refine(std::vector<double>& e, const std::vector<double>& d, double alpha) {
+  const int nb = (int)d.size();
+  if (nb < 2) return;
+  std::vector<double> ds(nb);
+  ds[0] = 0.5 * (d[0] + d[1]);
+  ds[nb - 1] = 0.5 * (d[nb - 2] + d[nb - 1]);
+  for (int i = 1; i < nb - 1; ++i) ds[i] = (d[i - 1] + d[i] + d[i + 1]) / 3.0;
+  double D = 0.0;
+  for (double v : ds) D += v;
+  if (!(D > 0.0)) return;
+  std::vector<double> r(nb);
+  double R = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    const double x = ds[i] / D;
+    r[i] = (x > 0.0) ? (x < 1.0 ? std::pow((1.0 - x) / -std::log(x), alpha) : 1.0) : 0.0;
+    R += r[i];
+  }
+  if (!(R > 0.0)) return;
+  std::vector<double> ne(nb + 1);
+  ne[0] = 0.0;
+  ne[nb] = 1.0;
+  double acc = 0.0;
+  int i = 0;
+  for (int j = 1; j < nb; ++j) {
+    const double need = R * (double)j / (double)nb;
+    while (i < nb - 1 && acc + r[i] < need) acc += r[i++];
+    const double frac = r[i] > 0.0 ? std::min(1.0, std::max(0.0, (need - acc) / r[i])) : 0.0;
+    ne[j] = e[i] + frac * (e[i + 1] - e[i]);
+  }
+  e = ne;
+}
+}  // namespace
+
+extern "C" {
+
+mea_status mea_partonic_cross_section_vegas(mea_process_t P, double sqrt_s, const mea_ps_config* cuts,
+                                            uint64_t first_event, const mea_vegas_config* vc, mea_prec_mode prec,
+                                            mea_vegas_result* out) {
+  if (!P || !cuts || !vc || !out || !(sqrt_s > 0) || !std::isfinite(sqrt_s))
+    return fail(MEA_E_ARG, "mea_partonic_cross_section_vegas: bad arguments");
+  if (vc->iterations < 1 || vc->points_per_iteration < 2 || vc->bins < 1 || vc->bins > PS_VEGAS_MAX_BINS ||
+      !(vc->alpha >= 0.0))
+    return fail(MEA_E_ARG, "mea_partonic_cross_section_vegas: bad VEGAS configuration");
+  if (P->host_only) return fail(MEA_E_UNSUPPORTED, "mea_partonic_cross_section_vegas: host-only process handle");
+  if (prec != MEA_PREC_FP64 && prec != MEA_PREC_MIXED)
+    return fail(MEA_E_ARG, "mea_partonic_cross_section_vegas: bad precision");
+  const mea::Program& G = P->prog;
+  const int n_ext = G.n_ext, nf = n_ext - 2;
+  if (cuts->n_final != nf) return fail(MEA_E_ARG, "mea_partonic_cross_section_vegas: cuts->n_final != n_ext - 2");
+  const double s_hat = sqrt_s * sqrt_s;
+  double fact_n1 = 1.0, fact_n2 = 1.0;
+  for (int k = 2; k <= nf - 1; ++k) fact_n1 *= k;
+  for (int k = 2; k <= nf - 2; ++k) fact_n2 *= k;
+  const double phi = std::pow(2.0 * M_PI, 4.0 - 3.0 * nf) * std::pow(M_PI / 2.0, nf - 1) * std::pow(s_hat, nf - 2) /
+                     (fact_n1 * fact_n2);
+  std::map<int, int> count;
+  for (int l = 2; l < n_ext; ++l) count[G.pdg[l]]++;
+  double sym = 1.0;
+  for (auto& kv : count)
+    for (int k = 2; k <= kv.second; ++k) sym /= k;
+  const double pre = sym * phi / (2.0 * s_hat) * 0.3893794e9;
+  const int nb = vc->bins, dims = ps_rambo_dims(nf);
+  const int64_t N = vc->points_per_iteration;
+  const int64_t chunk = std::min<int64_t>(N, 1 << 20);
+  mea::DevBuf mom, me2, wgt, bins, edges_d;
+  MEA_CUDA(mom.ensure(sizeof(double) * 4 * n_ext * chunk));
+  MEA_CUDA(me2.ensure(sizeof(double) * chunk));
+  MEA_CUDA(wgt.ensure(sizeof(double) * chunk));
+  MEA_CUDA(bins.ensure((size_t)dims * chunk));
+  MEA_CUDA(edges_d.ensure(sizeof(double) * dims * (nb + 1)));
+  std::vector<double> edges((size_t)dims * (nb + 1));
+  for (int d = 0; d < dims; ++d)
+    for (int b = 0; b <= nb; ++b) edges[(size_t)d * (nb + 1) + b] = (double)b / nb;
+  std::vector<double> hw(chunk), hm(chunk);
+  std::vector<unsigned char> hb((size_t)dims * chunk);
+  mea::PsConfigDev c{cuts->seed, nf, sqrt_s, sqrt_s, cuts->pt_min, cuts->eta_max, cuts->dr_min, cuts->ptij_min};
+  cudaStream_t s;
+  MEA_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  double sum_w = 0.0, sum_wi = 0.0, sum_chi = 0.0;
+  std::vector<double> Ik, Vk;
+  int64_t accepted = 0;
+  mea_status st = MEA_OK;
+  {
+    std::lock_guard<std::mutex> lk(P->mu);
+    for (int k = 0; k < vc->iterations && st == MEA_OK; ++k) {
+      std::vector<double> dsum((size_t)dims * nb, 0.0);
+      double f1 = 0.0, f2 = 0.0;
+      cudaError_t e = cudaMemcpyAsync(edges_d.p, edges.data(), sizeof(double) * edges.size(), cudaMemcpyHostToDevice, s);
+      for (int64_t c0 = 0; c0 < N && st == MEA_OK; c0 += chunk) {
+        const int64_t cn = std::min(chunk, N - c0);
+        const uint64_t ev0 = first_event + (uint64_t)k * (uint64_t)N + (uint64_t)c0;
+        if (e == cudaSuccess)
+          e = mea::launch_vegas_points(c, reinterpret_cast<const double*>(edges_d.p), nb, ev0, cn,
+                                       reinterpret_cast<double*>(mom.p), reinterpret_cast<double*>(wgt.p),
+                                       reinterpret_cast<unsigned char*>(bins.p), s);
+        if (e != cudaSuccess) { st = fail(MEA_E_CUDA, cudaGetErrorString(e)); break; }
+        st = do_evaluate(P, P->scr[0], reinterpret_cast<const double*>(mom.p), cn, MEA_HEL_SUM_NONZERO, nullptr, prec,
+                         reinterpret_cast<double*>(me2.p), nullptr, s);
+        if (st != MEA_OK) break;
+        e = cudaMemcpyAsync(hw.data(), wgt.p, sizeof(double) * cn, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), me2.p, sizeof(double) * cn, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), bins.p, (size_t)dims * cn, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { st = fail(MEA_E_CUDA, cudaGetErrorString(e)); break; }
+        // host sums in event order (reproducible)
+        for (int64_t i = 0; i < cn; ++i) {
+          const double f = hw[i] > 0.0 ? hw[i] * hm[i] : 0.0;
+          if (hw[i] > 0.0) ++accepted;
+          f1 += f;
+          f2 += f * f;
+          for (int d = 0; d < dims; ++d) dsum[(size_t)d * nb + hb[(size_t)i * dims + d]] += f * f;
+        }
+      }
+      if (st != MEA_OK) break;
+      const double mean = f1 / (double)N;
+      const double var = std::max(0.0, (f2 / (double)N - mean * mean) / (double)(N - 1));
+      Ik.push_back(pre * mean);
+      Vk.push_back(pre * pre * var);
+      if (k + 1 < vc->iterations)
+        for (int d = 0; d < dims; ++d) {
+          std::vector<double> ed(edges.begin() + (size_t)d * (nb + 1), edges.begin() + (size_t)(d + 1) * (nb + 1));
+          std::vector<double> dd(dsum.begin() + (size_t)d * nb, dsum.begin() + (size_t)(d + 1) * nb);
+          vegas_refine(ed, dd, vc->alpha);
+          std::copy(ed.begin(), ed.end(), edges.begin() + (size_t)d * (nb + 1));
+        }
+    }
+  }
+  cudaStreamDestroy(s);
+  if (st != MEA_OK) return st;
+  for (size_t k = 0; k < Ik.size(); ++k) {
+    const double wk = Vk[k] > 0.0 ? 1.0 / Vk[k] : 0.0;
+    sum_w += wk;
+    sum_wi += wk * Ik[k];
+  }
+  const double I = sum_w > 0.0 ? sum_wi / sum_w : Ik.back();
+  for (size_t k = 0; k < Ik.size(); ++k)
+    if (Vk[k] > 0.0) sum_chi += (Ik[k] - I) * (Ik[k] - I) / Vk[k];
+  out->sigma_pb = I;
+  out->error_pb = sum_w > 0.0 ? 1.0 / std::sqrt(sum_w) : 0.0;
+  out->chi2_per_dof = Ik.size() > 1 ? sum_chi / (double)(Ik.size() - 1) : 0.0;
+  out->last_sigma_pb = Ik.back();
+  out->last_error_pb = std::sqrt(Vk.back());
+  out->n_points = (int64_t)vc->iterations * N;
+  out->n_accepted = accepted;
+  return MEA_OK;
+}
+
+}  // extern "C"
+

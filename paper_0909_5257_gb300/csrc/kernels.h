@@ -120,6 +120,9 @@ struct PsConfigDev {
 };
 cudaError_t launch_phase_space(const PsConfigDev& cfg, uint64_t first_event, int64_t n,
                                double* mom, int32_t* attempts, cudaStream_t s);
+// VEGAS points at fixed sqrt(s_hat) = cfg.rs_lo (edges: device [dims][nb + 1]).
+cudaError_t launch_vegas_points(const PsConfigDev& cfg, const double* edges, int nb, uint64_t first_event,
+                                int64_t n, double* mom, double* weight, unsigned char* bins, cudaStream_t s);
 // Per-block sums for the partonic cross section (blocks x 256 threads);
 // part_a[2b], part_a[2b+1] = points drawn, points accepted.
 cudaError_t launch_xsec_sums(const double* me2, const int32_t* att, int64_t n, double* part_f, double* part_f2,

@@ -19,6 +19,17 @@ __global__ void ps_kernel(ps_config cfg, uint64_t first, int64_t n, double* mom,
   if (att) att[i] = a;
 }
 
+// VEGAS points of events first .. first + n - 1 (ps_vegas_event).
+__global__ void vegas_kernel(ps_config cfg, const double* edges, int nb, uint64_t first, int64_t n, double* mom,
+                             double* weight, unsigned char* bins) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int n_ext = 2 + cfg.n_final;
+  const int dims = ps_rambo_dims(cfg.n_final);
+  double (*m)[4] = reinterpret_cast<double (*)[4]>(mom + (size_t)i * n_ext * 4);
+  weight[i] = ps_vegas_event(&cfg, edges, nb, first + (uint64_t)i, m, bins + (size_t)i * dims);
+}
+
 // Partonic cross-section sums over a chunk: per block, in a fixed order, the
 // sums of f and f^2 with f = me2 for accepted points (attempt index >= 0) and
 // 0 otherwise, and the number of phase-space points drawn (attempt index + 1,
@@ -83,6 +94,26 @@ cudaError_t launch_phase_space(const PsConfigDev& c, uint64_t first_event, int64
   const int threads = 128;
   int64_t blocks = (n + threads - 1) / threads;
   ps_kernel<<<(unsigned)blocks, threads, 0, s>>>(cfg, first_event, n, mom, attempts);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) ++launch_counter();
+  return e;
+}
+
+cudaError_t launch_vegas_points(const PsConfigDev& c, const double* edges, int nb, uint64_t first_event, int64_t n,
+                                double* mom, double* weight, unsigned char* bins, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ps_config cfg;
+  cfg.seed = c.seed;
+  cfg.n_final = c.n_final;
+  cfg.rs_lo = c.rs_lo;
+  cfg.rs_hi = c.rs_hi;
+  cfg.pt_min = c.pt_min;
+  cfg.eta_max = c.eta_max;
+  cfg.dr_min = c.dr_min;
+  cfg.ptij_min = c.ptij_min;
+  const int threads = 128;
+  const int64_t blocks = (n + threads - 1) / threads;
+  vegas_kernel<<<(unsigned)blocks, threads, 0, s>>>(cfg, edges, nb, first_event, n, mom, weight, bins);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) ++launch_counter();
   return e;

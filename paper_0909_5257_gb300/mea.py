@@ -98,6 +98,7 @@ def load(path: str | None = None):
             lib.mea_evaluate_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp]
             lib.mea_generate_phase_space.argtypes = [vp, ctypes.c_uint64, i64, vp, vp, vp]
             lib.mea_partonic_cross_section.argtypes = [vp, ctypes.c_double, vp, ctypes.c_uint64, i64, i32, vp]
+            lib.mea_partonic_cross_section_vegas.argtypes = [vp, ctypes.c_double, vp, ctypes.c_uint64, vp, i32, vp]
             lib.mea_autotune.argtypes = [vp, vp, i64, i32, vp, vp]
             lib.mea_batch_create.argtypes = [vp, i32, i32, vp]
             lib.mea_batch_launch.argtypes = [vp, vp]
@@ -249,6 +250,19 @@ class Process:
                                                  ctypes.byref(r)))
         return {k: getattr(r, k) for k, _ in XsecResult._fields_}
 
+    def partonic_cross_section_vegas(self, sqrt_s, iterations, points_per_iteration, bins=32, alpha=1.5,
+                                     seed=0x09095257, first_event=0, pt_min=20.0, eta_max=2.5, dr_min=0.4,
+                                     ptij_min=0.0, precision=PREC_FP64):
+        """sigma_hat at fixed sqrt(s_hat) in pb by VEGAS over RAMBO's uniforms
+        (mea_partonic_cross_section_vegas)."""
+        cfg = PsConfig(seed, self.n_ext - 2, sqrt_s, sqrt_s, pt_min, eta_max, dr_min, ptij_min)
+        vc = VegasConfig(iterations, points_per_iteration, bins, alpha)
+        r = VegasResult()
+        _check(load().mea_partonic_cross_section_vegas(self._h, ctypes.c_double(sqrt_s), ctypes.byref(cfg),
+                                                       ctypes.c_uint64(first_event), ctypes.byref(vc), precision,
+                                                       ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _ in VegasResult._fields_}
+
     def evaluate_host(self, momenta: np.ndarray, precision=PREC_MIXED, with_flags=False, out=None, flags=None):
         """|M|^2 of host momenta through the library's pipelined copies.
 
@@ -277,6 +291,17 @@ def generate_phase_space(n_final, n, momenta, first_event=0, seed=0x09095257, rs
     cfg = PsConfig(seed, n_final, rs_lo, rs_hi, pt_min, eta_max, dr_min, ptij_min)
     _check(load().mea_generate_phase_space(ctypes.byref(cfg), first_event, n, _ptr(momenta),
                                            _ptr(attempts), _stream(stream)))
+
+
+class VegasConfig(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("points_per_iteration", ctypes.c_int64), ("bins", ctypes.c_int),
+                ("alpha", ctypes.c_double)]
+
+
+class VegasResult(ctypes.Structure):
+    _fields_ = [("sigma_pb", ctypes.c_double), ("error_pb", ctypes.c_double), ("chi2_per_dof", ctypes.c_double),
+                ("last_sigma_pb", ctypes.c_double), ("last_error_pb", ctypes.c_double),
+                ("n_points", ctypes.c_int64), ("n_accepted", ctypes.c_int64)]
 
 
 class XsecResult(ctypes.Structure):

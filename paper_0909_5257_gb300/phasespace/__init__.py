@@ -74,6 +74,9 @@ def _load():
                                              ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
             lib.ps_generate_host.restype = ctypes.c_int
             lib.ps_philox_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            lib.ps_vegas_host.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            lib.ps_vegas_host.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -90,6 +93,28 @@ def generate(cfg: PhaseSpaceConfig, n_events: int, first_event: int = 0,
     if rc != 0:
         raise ValueError("phase-space generator rejected its configuration")
     return (out, att) if return_attempts else out
+
+
+def vegas_points(cfg: PhaseSpaceConfig, edges: np.ndarray, first_event: int, n_events: int):
+    """VEGAS points at sqrt(s_hat) = cfg.rs_lo (ps_vegas_event): momenta
+    [n, 2 + n_final, 4], weights [n] (0 where the cuts reject), bins
+    [n, dims] uint8.  edges: [dims, nb + 1] float64."""
+    lib = _load()
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    nb = e.shape[1] - 1
+    out = np.zeros((n_events, 2 + cfg.n_final, 4), dtype=np.float64)
+    w = np.zeros(n_events, dtype=np.float64)
+    b = np.zeros((n_events, e.shape[0]), dtype=np.uint8)
+    c = cfg.as_c()
+    rc = lib.ps_vegas_host(ctypes.byref(c), e.ctypes.data, nb, ctypes.c_uint64(first_event), ctypes.c_int64(n_events),
+                           out.ctypes.data, w.ctypes.data, b.ctypes.data)
+    if rc != 0:
+        raise ValueError("VEGAS point generator rejected its configuration")
+    return out, w, b
+
+
+def rambo_dims(n_final: int) -> int:
+    return 2 if n_final == 2 else 4 * n_final
 
 
 def philox4x32_10(ctr, key):

@@ -117,17 +117,22 @@ PS_HD double ps_next(ps_stream *s) {
 }
 
 /* ---- RAMBO, massless ---------------------------------------------------- */
-/* Writes n massless momenta with total momentum (rs, 0, 0, 0) into mom. */
-PS_HD void ps_rambo_massless(ps_stream *s, int n, double rs, double (*mom)[4]) {
+/* Uniforms RAMBO consumes for n partons: 2 for n = 2 (cos theta, phi), else 4
+ * per parton (cos theta, phi, and two for the energy -log(r1 r2)). */
+PS_HD int ps_rambo_dims(int n) { return n == 2 ? 2 : 4 * n; }
+
+/* Writes n massless momenta with total momentum (rs, 0, 0, 0) into mom from
+ * the ps_rambo_dims(n) uniforms u in (0, 1), in the order listed above. */
+PS_HD void ps_rambo_massless_u(const double *u, int n, double rs, double (*mom)[4]) {
   const double twopi = 6.283185307179586476925286766559;
   if (n == 2) {
     /* Flat two-body massless phase space is a uniform direction in the
      * centre-of-mass frame; drawing it directly keeps both momenta exactly
      * back to back and on shell (RAMBO's conformal boost loses digits when
      * its two random vectors are nearly parallel). */
-    double c = 2.0 * ps_next(s) - 1.0;
+    double c = 2.0 * u[0] - 1.0;
     double sn = sqrt(1.0 - c * c);
-    double f = twopi * ps_next(s);
+    double f = twopi * u[1];
     double e = 0.5 * rs;
     mom[0][0] = e; mom[0][1] = e * sn * cos(f); mom[0][2] = e * sn * sin(f); mom[0][3] = e * c;
     mom[1][0] = e; mom[1][1] = -mom[0][1]; mom[1][2] = -mom[0][2]; mom[1][3] = -mom[0][3];
@@ -136,11 +141,11 @@ PS_HD void ps_rambo_massless(ps_stream *s, int n, double rs, double (*mom)[4]) {
   double q[PS_MAX_FINAL][4];
   double Q[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = 0; i < n; ++i) {
-    double c = 2.0 * ps_next(s) - 1.0;
+    double c = 2.0 * u[4 * i] - 1.0;
     double sn = sqrt(1.0 - c * c);
-    double f = twopi * ps_next(s);
-    double r1 = ps_next(s);
-    double r2 = ps_next(s);
+    double f = twopi * u[4 * i + 1];
+    double r1 = u[4 * i + 2];
+    double r2 = u[4 * i + 3];
     double e = -log(r1 * r2);
     q[i][0] = e;
     q[i][3] = e * c;
@@ -175,6 +180,14 @@ PS_HD void ps_rambo_massless(ps_stream *s, int n, double rs, double (*mom)[4]) {
   double f = rs / esum;
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < 4; ++k) mom[i][k] *= f;
+}
+
+/* RAMBO drawing its uniforms from the stream. */
+PS_HD void ps_rambo_massless(ps_stream *s, int n, double rs, double (*mom)[4]) {
+  double u[4 * PS_MAX_FINAL];
+  const int d = ps_rambo_dims(n);
+  for (int k = 0; k < d; ++k) u[k] = ps_next(s);
+  ps_rambo_massless_u(u, n, rs, mom);
 }
 
 /* ---- cuts ---------------------------------------------------------------- */
@@ -221,6 +234,49 @@ PS_HD int ps_generate_event(const ps_config *cfg, uint64_t event,
     if (ps_pass_cuts(cfg, n, mom + 2)) { accepted = (int)att; break; }
   }
   return accepted;
+}
+
+/* ---- VEGAS points at fixed sqrt(s_hat) ------------------------------------ *
+ * Adaptive importance sampling (G. P. Lepage, J. Comput. Phys. 27 (1978) 192)
+ * over RAMBO's uniforms: dimension d has nb bins with edges
+ * e[d][0] = 0 < e[d][1] < ... < e[d][nb] = 1; a uniform x lands in bin
+ * i = floor(x nb) and maps linearly into [e[d][i], e[d][i+1]], with Jacobian
+ * nb (e[d][i+1] - e[d][i]).  A point that fails the cuts has weight 0 (no
+ * redraw).  The uniforms are those of attempt PS_VEGAS_ATTEMPT of the event,
+ * a counter range the flat generator never reaches. */
+#define PS_VEGAS_MAX_BINS 64
+#define PS_VEGAS_ATTEMPT 0xFFFFFFFFu
+
+/* mom[2 + n_final][4] <- the point of `event` (incoming legs along +-z at
+ * sqrt(s_hat) = cfg->rs_lo); bins[d] <- its bin per dimension; returns the
+ * weight (product of the Jacobians) or 0 when the cuts reject the point.
+ * edges: [ps_rambo_dims(n_final)][nb + 1]. */
+PS_HD double ps_vegas_event(const ps_config *cfg, const double *edges, int nb, uint64_t event,
+                            double (*mom)[4], unsigned char *bins) {
+  const int n = cfg->n_final;
+  const int dims = ps_rambo_dims(n);
+  ps_stream s;
+  ps_stream_init(&s, cfg->seed, event, PS_VEGAS_ATTEMPT);
+  double u[4 * PS_MAX_FINAL];
+  double w = 1.0;
+  for (int d = 0; d < dims; ++d) {
+    const double x = ps_next(&s) * (double)nb;
+    int b = (int)x;
+    if (b > nb - 1) b = nb - 1;
+    const double *e = edges + (size_t)d * (size_t)(nb + 1);
+    const double width = e[b + 1] - e[b];
+    double y = e[b] + (x - (double)b) * width;
+    if (!(y > 0.0)) y = 0x1p-60;
+    if (!(y < 1.0)) y = 1.0 - 0x1p-53;
+    u[d] = y;
+    w *= (double)nb * width;
+    bins[d] = (unsigned char)b;
+  }
+  const double rs = cfg->rs_lo, half = 0.5 * rs;
+  mom[0][0] = half; mom[0][1] = 0.0; mom[0][2] = 0.0; mom[0][3] = half;
+  mom[1][0] = half; mom[1][1] = 0.0; mom[1][2] = 0.0; mom[1][3] = -half;
+  ps_rambo_massless_u(u, n, rs, mom + 2);
+  return ps_pass_cuts(cfg, n, mom + 2) ? w : 0.0;
 }
 
 #endif /* PS_PHASESPACE_H */
