@@ -138,6 +138,43 @@ def test_mc_colour_statistics_gg4g():
     assert abs(frac_zero - want["all_zero_config_fraction"]) < 0.01
 
 
+def test_mc_colour_variance_inflation_gg3g():
+    """Sec. 3.3's alternative -- one uniformly drawn colour assignment per event
+    instead of the colour sum -- measured: for gg -> ggg the estimator
+    8^5 sum_h |sum_alpha J_h,alpha Tr_alpha(c)|^2 has, per event, a colour
+    variance about 40 times the square of the exact sum, so it needs tens of
+    times more events than the exact colour sum for the same precision; the
+    colour sum it would save is a fraction of the per-event cost.  (Its mean
+    over all assignments is the exact colour sum: checked.)"""
+    n = 5
+    T = ref.gell_mann_T()
+    letters, inner = "abcde", "ijklm"
+    subs = ",".join(letters[k] + inner[k] + inner[(k + 1) % n] for k in range(n))
+    X = np.einsum(subs + "->" + letters, *([T] * n), optimize=True)
+    P = proc([21] * n)
+    Y = np.array([np.moveaxis(X, list(range(n)), P.basis(a)[0][3]).reshape(-1) for a in range(P.n_colour)])
+    N = P.colour_matrix()
+    mom = events(n - 2, 60, lo=300.0, hi=3000.0, seed=ps.SEED_BASE + 31)
+    exact, var_c = [], []
+    for m in mom:
+        S = np.zeros(Y.shape[1])
+        tot = 0.0
+        for h in range(1 << n):
+            J = P.jamp(m, h)
+            if not np.any(J):
+                continue
+            S += np.abs(J @ Y) ** 2
+            tot += float(np.real(np.conj(J) @ N @ J)) * 64.0  # N carries 1/(n_a n_b)
+        assert abs(S.sum() / tot - 1.0) < 1e-10  # the mean over assignments is the colour sum
+        exact.append(S.sum())
+        var_c.append(np.mean((8.0 ** n * S) ** 2) - S.sum() ** 2)
+    exact, var_c = np.array(exact), np.array(var_c)
+    per_event = float(np.mean(var_c / exact ** 2))
+    inflation = 1.0 + var_c.mean() / exact.var()
+    assert 20.0 < per_event < 80.0
+    assert inflation > 10.0
+
+
 # ------------------------------------------------------------ closed forms
 @pytest.mark.parametrize("pdg,fn", [([21] * 4, ref.me2_gg_gg),
                                     ([2, -2, 21, 21], ref.me2_uubar_gg),
