@@ -82,7 +82,7 @@ struct AmpConfig {
   size_t smem = 0;
   bool jamp_in_smem = true;
   bool slots_in_smem = true;
-  int regvar = 0;  // straight-line kernels: register-cap variant (see GenEntry)
+  int regvar = 0;  // straight-line kernels: variant, 2 * cap + body (see GenEntry)
   int per_sm = 1;  // CTAs meant to be resident per SM (sets the shared-memory carveout)
 };
 
