@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <new>
@@ -585,6 +586,22 @@ mea_status mea_evaluate(mea_process_t P, const double* mom, int64_t n, mea_hel_m
 }  // extern "C"
 
 namespace {
+// Releases device buffers local to one call when the call returns, on every
+// path (mea::DevBuf itself is a plain record that longer-lived holders copy,
+// so it has no destructor).
+class ScopedBufs {
+ public:
+  ScopedBufs(std::initializer_list<mea::DevBuf*> bufs) : bufs_(bufs) {}
+  ScopedBufs(const ScopedBufs&) = delete;
+  ScopedBufs& operator=(const ScopedBufs&) = delete;
+  ~ScopedBufs() {
+    for (mea::DevBuf* b : bufs_) b->release();
+  }
+
+ private:
+  std::vector<mea::DevBuf*> bufs_;
+};
+
 // Host copy into / out of the pinned staging buffers, split over host threads
 // for large blocks (one core's memcpy bandwidth would bound the pipeline).
 void host_copy(void* dst, const void* src, size_t bytes) {
@@ -821,6 +838,7 @@ mea_status mea_partonic_cross_section(mea_process_t P, double sqrt_s, const mea_
   const int64_t chunk = std::min<int64_t>(n, 1 << 20);
   constexpr int kBlocks = 256;
   mea::DevBuf mom, me2, att, pf, pf2, pa;
+  const ScopedBufs held{&mom, &me2, &att, &pf, &pf2, &pa};
   MEA_CUDA(mom.ensure(sizeof(double) * 4 * n_ext * chunk));
   MEA_CUDA(me2.ensure(sizeof(double) * chunk));
   MEA_CUDA(att.ensure(sizeof(int32_t) * chunk));
@@ -948,6 +966,7 @@ mea_status mea_partonic_cross_section_vegas(mea_process_t P, double sqrt_s, cons
   const int64_t N = vc->points_per_iteration;
   const int64_t chunk = std::min<int64_t>(N, 1 << 20);
   mea::DevBuf mom, me2, wgt, bins, edges_d;
+  const ScopedBufs held{&mom, &me2, &wgt, &bins, &edges_d};
   MEA_CUDA(mom.ensure(sizeof(double) * 4 * n_ext * chunk));
   MEA_CUDA(me2.ensure(sizeof(double) * chunk));
   MEA_CUDA(wgt.ensure(sizeof(double) * chunk));
