@@ -342,6 +342,9 @@ mea_status mea_generate_phase_space(const mea_ps_config *cfg, uint64_t first_eve
                                     double *momenta_dev, int32_t *attempts_dev, void *stream);
 
 /* ---- partonic cross section ------------------------------------------------ *
+ * The subprocess cross section of Sec. 2.1 (the leading-order d sigma_hat with
+ * the invariant phase space of Eq. (phase-space) and the statistical factor on
+ * it):
  * sigma_hat(s_hat) = 1/(2 s_hat) * S * integral over the cut region of
  * dPhi_n |M|^2, with |M|^2 as mea_evaluate returns it (initial helicities and
  * colours averaged), S = 1 / prod k! over identical final-state partons, and
