@@ -38,7 +38,8 @@ def test_schedules_compute_the_same_colour_amplitudes(tmp_path):
                     os.path.join(HERE, "native", "program_variants_check.cpp"),
                     os.path.join(CSRC, "generator.cpp")], check=True)
     procs = ["21,21,21,21,21", "2,-2,21,21,21", "2,2,2,2,21", "21,21,21,21,21,21",
-             "2,-2,21,21,21,21", "2,2,2,2,21,21", "2,2,2,2,21,21,21", "2,21,2,21,21", "2,-2,1,-1,21"]
+             "2,-2,21,21,21,21", "2,2,2,2,21,21", "2,2,2,2,21,21,21", "2,21,2,21,21", "2,-2,1,-1,21",
+             "2,-2,21,21,21,21,21", "21,21,21,21,21,21,21"]
     r = subprocess.run([exe] + procs, capture_output=True, text=True)
     assert r.returncode == 0, "mask tables differ between build options"
     lines = r.stdout.split()
@@ -46,3 +47,4 @@ def test_schedules_compute_the_same_colour_amplitudes(tmp_path):
         name, worst, n_part = lines[3 * k], float(lines[3 * k + 1]), int(lines[3 * k + 2])
         assert worst < 1e-13, (name, worst)
     assert int(lines[3 * 3 + 2]) > 0  # gg > gggg shares partials
+    assert int(lines[3 * 10 + 2]) == 81 + 225  # gg > ggggg: vvv and gggg groups
