@@ -140,6 +140,22 @@ def _ptr(x):
     raise TypeError(f"cannot take the address of {type(x)}")
 
 
+def _check_device_tensor(t, name, dtype, min_numel, device_only=True):
+    """Reject (MeaError MEA_E_ARG), before any device access, a torch tensor
+    the kernels would misread: wrong dtype, strided, on the host, or too
+    small.  Raw addresses (ints) and None pass to the library unchecked."""
+    if t is None or isinstance(t, int) or not hasattr(t, "data_ptr"):
+        return
+    if t.dtype != dtype:
+        raise MeaError(-1, f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise MeaError(-1, f"{name}: must be contiguous")
+    if device_only and t.device.type != "cuda":
+        raise MeaError(-1, f"{name}: must be a CUDA tensor")
+    if t.numel() < min_numel:
+        raise MeaError(-1, f"{name}: {t.numel()} elements, need at least {min_numel}")
+
+
 def _stream(s):
     if s is None:
         return None
@@ -209,13 +225,22 @@ class Process:
         """Enqueue |M|^2 of device momenta [N, n_ext, 4] (float64) into device me2 [N]."""
         if n_events is None:
             n_events = int(momenta.shape[0])
+        self._check_args(momenta, me2, n_events, flags, hel if hel_mode == HEL_GIVEN else None)
         _check(load().mea_evaluate(self._h, _ptr(momenta), n_events, hel_mode, _ptr(hel), precision,
                                    _ptr(me2), _ptr(flags), _stream(stream)))
+
+    def _check_args(self, momenta, me2, n_events, flags=None, hel=None):
+        import torch
+        _check_device_tensor(momenta, "momenta", torch.float64, n_events * self.n_ext * 4)
+        _check_device_tensor(me2, "me2", torch.float64, n_events)
+        _check_device_tensor(flags, "flags", torch.uint8, n_events)
+        _check_device_tensor(hel, "hel", torch.int8, n_events * self.n_ext)
 
     def autotune(self, momenta, scratch_me2, n_sample=None, precision=PREC_MIXED):
         """Time the candidate tile shapes on a device sample and keep the fastest."""
         if n_sample is None:
             n_sample = int(momenta.shape[0])
+        self._check_args(momenta, scratch_me2, n_sample)
         r = TuneResult()
         _check(load().mea_autotune(self._h, _ptr(momenta), n_sample, precision, _ptr(scratch_me2),
                                    ctypes.byref(r)))

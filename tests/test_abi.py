@@ -119,3 +119,22 @@ def test_vertex_partials_reduce_the_flop_count():
         assert info["flops_per_hel"] == part
     info = mea.Process([21] * 4, host_only=True).info
     assert info["flops_per_hel"] == info["flops_per_hel_plain"]
+
+
+def test_binding_rejects_tensors_the_kernels_would_misread():
+    """The Python binding checks dtype, contiguity, device and size of torch
+    arguments before handing their addresses to the library (MEA_E_ARG)."""
+    torch = pytest.importorskip("torch")
+    from paper_0909_5257_gb300 import mea
+    P = mea.Process([21] * 5, host_only=True)
+    n = 8
+    cases = [
+        (torch.zeros((n, 5, 4), dtype=torch.float32), torch.zeros(n, dtype=torch.float64), "float64"),
+        (torch.zeros((n, 5, 4), dtype=torch.float64), torch.zeros(n, dtype=torch.float64), "CUDA"),
+        (torch.zeros((n, 4, 5), dtype=torch.float64).transpose(1, 2), torch.zeros(n, dtype=torch.float64),
+         "contiguous"),
+    ]
+    for mom, me2, word in cases:
+        with pytest.raises(mea.MeaError) as e:
+            P.evaluate(mom, me2)
+        assert e.value.status == -1 and word in str(e.value)
