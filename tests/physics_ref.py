@@ -272,6 +272,82 @@ def bg_quark_line_amplitude(mom, eps, gluons, ubar_left, u_right):
     return ubar_left @ R(0)
 
 
+# ------------------------------- two quark lines by explicit Feynman diagrams
+def _ubar(p, lam):
+    return u_spinor(p, lam).conj() @ _GAMMA[0]
+
+
+_METRIC = np.diag([1.0, -1.0, -1.0, -1.0])
+
+
+def _mu_vec(bar, ket, mid=None):
+    """bar gamma^mu [mid] ket for mu = 0..3 (upper index)."""
+    m = np.eye(4) if mid is None else mid
+    return np.array([bar @ _GAMMA[k] @ m @ ket for k in range(4)])
+
+
+def quark_quark_gluon_diagrams(m, lam, g, ward=False):
+    """Lorentz values (couplings, propagators and i's included) of the five
+    tree diagrams of q(p0) Q(p1) -> q(p2) Q(p3) g(p4) for distinct quark
+    lines q and Q, from the textbook Feynman-gauge rules (Peskin-Schroeder
+    conventions: qqg vertex i g gamma^mu t^a, three-gluon vertex
+    g f^{abc}[g^{mu nu}(k-p)^rho + g^{nu rho}(p-q)^mu + g^{rho mu}(q-k)^nu]
+    with incoming momenta, gluon propagator -i g_{mu nu}/k^2, quark
+    propagator i k-slash/k^2), in the order: gluon from incoming q, outgoing q,
+    incoming Q, outgoing Q, and from the exchanged gluon.  ward=True replaces
+    the gluon's polarisation by its momentum."""
+    p0, p1, p2, p3, p4 = m
+    u0, u1 = u_spinor(p0, lam[0]), u_spinor(p1, lam[1])
+    b2, b3 = _ubar(p2, lam[2]), _ubar(p3, lam[3])
+    eps = p4.astype(complex) if ward else polarisation(p4, lam[4], outgoing=True)
+    es = slash(eps)
+    ig = 1j * g
+    J1, J2 = _mu_vec(b2, u0), _mu_vec(b3, u1)
+    q1, q2 = p0 - p2, p1 - p3
+
+    def prop_q(k):
+        return 1j * slash(k) / mdot(k, k)
+
+    def dot(a, b):
+        return a @ _METRIC @ b
+
+    L = np.zeros(5, dtype=complex)
+    for d, (bar, ket, k, outgoing, other, q) in enumerate(
+            ((b2, u0, p0 - p4, False, J2, q2), (b2, u0, p2 + p4, True, J2, q2),
+             (b3, u1, p1 - p4, False, J1, q1), (b3, u1, p3 + p4, True, J1, q1))):
+        S = prop_q(k)
+        if outgoing:  # gluon off the outgoing quark: next to the barred spinor
+            A = np.array([bar @ es @ S @ _GAMMA[mu] @ ket for mu in range(4)])
+        else:         # gluon off the incoming quark
+            A = np.array([bar @ _GAMMA[mu] @ S @ es @ ket for mu in range(4)])
+        L[d] = ig ** 3 * (-1j / mdot(q, q)) * dot(A, other)
+    X1 = ig * J1 * (-1j / mdot(q1, q1))
+    X2 = ig * J2 * (-1j / mdot(q2, q2))
+    k4 = -p4
+    L[4] = g * (dot(eps, X1) * dot(k4 - q1, X2) + dot(X1, X2) * dot(q1 - q2, eps) + dot(X2, eps) * dot(q2 - k4, X1))
+    return L
+
+
+def quark_quark_gluon_colours():
+    """Colour tensors C_d[i_out q, i_in q, j_out Q, j_in Q, a] of the five
+    diagrams, explicit SU(3) generators t = lambda/2 and
+    f^{abc} = -2i Tr([t^a, t^b] t^c)."""
+    T = gell_mann_T()
+    f = np.zeros((8, 8, 8))
+    for a in range(8):
+        for b in range(8):
+            comm = T[a] @ T[b] - T[b] @ T[a]
+            for c in range(8):
+                f[a, b, c] = np.real(-2j * np.trace(comm @ T[c]))
+    C = np.zeros((5, 3, 3, 3, 3, 8), dtype=complex)
+    C[0] = np.einsum("bxy,ayz,bwv->xzwva", T, T, T)
+    C[1] = np.einsum("axy,byz,bwv->xzwva", T, T, T)
+    C[2] = np.einsum("bxz,bwy,ayv->xzwva", T, T, T)
+    C[3] = np.einsum("bxz,awy,byv->xzwva", T, T, T)
+    C[4] = np.einsum("abc,bxz,cwv->xzwva", f, T, T)
+    return C
+
+
 # --------------------------------------------------------------- Gell-Mann
 def gell_mann_T():
     l = np.zeros((8, 3, 3), dtype=complex)
