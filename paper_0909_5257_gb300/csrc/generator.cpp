@@ -822,13 +822,13 @@ bool helicity_allowed(const Builder& B, const std::vector<int>& lam) {
 double op_flops(int type) {
   switch (type) {
     case OP_EXT: return 12;
-    case OP_JVV: return 159;
-    case OP_JGGG: return 125;
+    case OP_JVV: return 160;  // the ggg partial (148), the open momentum and 1/q^2
+    case OP_JGGG: return 128;  // the gggg partial (120) and 1/q^2
     case OP_FVI: return 115;
     case OP_FVO: return 115;
     case OP_JIO: return 129;
-    case OP_AVVV: return 204;
-    case OP_AGGGG: return 136;
+    case OP_AVVV: return 178;  // the ggg partial closed with the third wavefunction
+    case OP_AGGGG: return 150;  // the gggg partial closed with the fourth
     case OP_AIOV: return 96;
     case OP_ADOT: return 30;
     case OP_PVVV: return 148;

@@ -64,64 +64,92 @@ MEA_HD cx<R> dot(const R* p, const W4<R>& a) {
   return p[0] * a.c[0] - p[1] * a.c[1] - p[2] * a.c[2] - p[3] * a.c[3];
 }
 
-// ---------------------------------------------------------------- VVV
-// vvvxxx: amplitude of the ggg vertex from three gluon wavefunctions with
-// flowing-out momenta pa, pb, pc (Appendix A, listing vvvxxx):
-//   -g [ (ga.gb)(pa-pb).gc + (gb.gc)(pb-pc).ga + (gc.ga)(pc-pa).gb ]
-template <typename R>
-MEA_HD cx<R> vvv_amp(const W4<R>& ga, const W4<R>& gb, const W4<R>& gc,
-                                         const R* pa, const R* pb, const R* pc, R g) {
-  cx<R> v12 = dot(ga, gb), v23 = dot(gb, gc), v31 = dot(gc, ga);
-  cx<R> p12 = dot(pa, gb), p13 = dot(pa, gc);
-  cx<R> p21 = dot(pb, ga), p23 = dot(pb, gc);
-  cx<R> p31 = dot(pc, ga), p32 = dot(pc, gb);
-  cx<R> v = v12 * (p13 - p23) + v23 * (p21 - p31) + v31 * (p32 - p12);
-  return (-g) * v;
-}
+// ---------------------------------------------------------------- ggg vertex
+// Feynman rule of the three-gluon term of the Lagrangian (Sec. 4.1) with the
+// colour factor i f^{abc} taken off and all three momenta k1, k2, k3 flowing
+// into the vertex:
+//   Gamma^{mu nu rho}(k1, k2, k3) = g^{mu nu} (k1 - k2)^rho + g^{nu rho} (k2 - k3)^mu
+//                                 + g^{rho mu} (k3 - k1)^nu,
+// unchanged by a cyclic shift of its (index, momentum) pairs.  Contracting the
+// nu and rho slots with wavefunctions y and z leaves a vector in mu:
+//   O^mu(y, z) = y^mu (k1 - k2).z + (k2 - k3)^mu (y.z) + z^mu (k3 - k1).y .
+// HEGET normalisation (Sec. 4.1): an amplitude is -g times the full
+// contraction, an off-shell current -g O / q^2.  Everything below is built on
+// the one open contraction, so vertex, current and vertex partial share it.
 
-// jvvxx0 (listing name jggxxx): off-shell gluon from two gluons, Feynman-gauge
-// propagator.  inv_q2 = 1/q^2 with q = -(pa+pb), supplied from the FP64 prep.
+// -g O^mu(y, z): the ggg vertex with the slot of momentum k1 left open (also
+// the vertex partial of a diagram whose free wavefunction sits in that slot)
 template <typename R>
-MEA_HD W4<R> jvv(const W4<R>& ga, const W4<R>& gb, const R* pa,
-                                     const R* pb, R inv_q2, R g) {
-  // q = -(pa+pb):  (pb - q) = pa + 2 pb,  (pa - q) = 2 pa + pb
-  R s1[4], s2[4], d[4];
+MEA_HD W4<R> vvv_part(const W4<R>& y, const W4<R>& z, const R* k1, const R* k2, const R* k3, R g) {
+  R d12[4], d23[4], d31[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    s1[m] = pa[m] + R(2) * pb[m];
-    s2[m] = R(2) * pa[m] + pb[m];
-    d[m] = pa[m] - pb[m];
+    d12[m] = k1[m] - k2[m];
+    d23[m] = k2[m] - k3[m];
+    d31[m] = k3[m] - k1[m];
   }
-  cx<R> gab = dot(ga, gb);
-  cx<R> sga = dot(s1, ga);
-  cx<R> sgb = -dot(s2, gb);
-  R gs = -g * inv_q2;
-  W4<R> j;
+  const R ng = -g;
+  const cx<R> along_y = ng * dot(d12, z);
+  const cx<R> along_z = ng * dot(d31, y);
+  const cx<R> along_d = ng * dot(y, z);
+  W4<R> o;
 #pragma unroll
-  for (int m = 0; m < 4; ++m) j.c[m] = gs * (d[m] * gab + sga * gb.c[m] + sgb * ga.c[m]);
-  return j;
+  for (int m = 0; m < 4; ++m) o.c[m] = along_y * y.c[m] + along_z * z.c[m] + d23[m] * along_d;
+  return o;
 }
 
-// ---------------------------------------------------------------- VVVV
-// ggggxx: one colour structure of the gggg amplitude,
-//   gg [ (ga.gd)(gb.gc) - (ga.gc)(gb.gd) ],  gg = g_s^2   (listing ggggxx)
+// Amplitude of three gluon wavefunctions x, y, z with momenta kx, ky, kz into
+// the vertex (vvvxxx): the open slot of -g O(y, z) closed with x.
 template <typename R>
-MEA_HD cx<R> gggg_amp(const W4<R>& ga, const W4<R>& gb, const W4<R>& gc,
-                                          const W4<R>& gd, R gg) {
-  return gg * (dot(ga, gd) * dot(gb, gc) - dot(ga, gc) * dot(gb, gd));
+MEA_HD cx<R> vvv_amp(const W4<R>& x, const W4<R>& y, const W4<R>& z, const R* kx, const R* ky, const R* kz, R g) {
+  return dot(x, vvv_part(y, z, kx, ky, kz, g));
 }
 
-// jgggx0: off-shell gluon of one gggg colour structure,
-//   (gg/q^2) [ ga (gc.gb) - gb (ga.gc) ]                  (listing jgggx0)
+// Off-shell gluon from two gluon wavefunctions (jvvxx0, listed as jggxxx):
+// the open slot carries the current's momentum into the vertex, -(kx + ky),
+// times the Feynman-gauge propagator factor 1/q^2 (inv_q2, from the prep).
 template <typename R>
-MEA_HD W4<R> jggg(const W4<R>& ga, const W4<R>& gb, const W4<R>& gc,
-                                      R inv_q2, R gg) {
-  R f = gg * inv_q2;
-  cx<R> gcb = dot(gc, gb), gac = dot(ga, gc);
-  W4<R> j;
+MEA_HD W4<R> jvv(const W4<R>& x, const W4<R>& y, const R* kx, const R* ky, R inv_q2, R g) {
+  R k_open[4];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) j.c[m] = f * (ga.c[m] * gcb - gb.c[m] * gac);
-  return j;
+  for (int m = 0; m < 4; ++m) k_open[m] = -(kx[m] + ky[m]);
+  W4<R> o = vvv_part(x, y, k_open, kx, ky, g);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) o.c[m] = inv_q2 * o.c[m];
+  return o;
+}
+
+// ---------------------------------------------------------------- gggg vertex
+// One colour structure of the four-gluon term (Sec. 4.2; the three structures
+// f^{abe}f^{cde}, f^{ace}f^{dbe}, f^{ade}f^{bce} are three calls with the
+// wavefunctions permuted), coupling gg = g_s^2.  With one slot open the
+// structure is the vector
+//   G(x, y, z) = gg [ z (x.y) - y (x.z) ]   (so G(x, y, z) = -G(x, z, y)),
+// and the amplitude of four wavefunctions is
+//   a . G(b, c, d) = gg [ (a.d)(b.c) - (a.c)(b.d) ] = b.G(a, d, c) = c.G(d, a, b) = d.G(c, b, a).
+template <typename R>
+MEA_HD W4<R> gggg_part(const W4<R>& x, const W4<R>& y, const W4<R>& z, R gg) {
+  const cx<R> xy = gg * dot(x, y), xz = gg * dot(x, z);
+  W4<R> o;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) o.c[m] = xy * z.c[m] - xz * y.c[m];
+  return o;
+}
+
+// Amplitude of one gggg colour structure (ggggxx).
+template <typename R>
+MEA_HD cx<R> gggg_amp(const W4<R>& a, const W4<R>& b, const W4<R>& c, const W4<R>& d, R gg) {
+  return dot(a, gggg_part(b, c, d, gg));
+}
+
+// Off-shell gluon of one gggg colour structure (jgggx0): the open first slot
+// of ggggxx(open, c, b, a), G(c, b, a) = gg [ a (c.b) - b (c.a) ], times 1/q^2.
+template <typename R>
+MEA_HD W4<R> jggg(const W4<R>& a, const W4<R>& b, const W4<R>& c, R inv_q2, R gg) {
+  W4<R> o = gggg_part(c, b, a, gg);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) o.c[m] = inv_q2 * o.c[m];
+  return o;
 }
 
 // ---------------------------------------------------------------- qqg
@@ -231,38 +259,9 @@ MEA_HD W4<R> jio(const W4<R>& fi, const W4<R>& fo, R inv_q2, R g) {
 // summed into the colour amplitudes on its own; only the common factor of the
 // vertex is computed once.
 
-// vvvxxx with the first wavefunction free:  vvv_amp(ga, gb, gc) = ga . U
-//   U = -g [ gb (pa-pb).gc + (pb-pc) (gb.gc) + gc (pc-pa).gb ]
-// (vvv_amp is invariant under a cyclic shift of (wavefunction, momentum), so
-// any of its three arguments can be the free one).
-template <typename R>
-MEA_HD W4<R> vvv_part(const W4<R>& gb, const W4<R>& gc, const R* pa, const R* pb, const R* pc, R g) {
-  R d1[4], d2[4], d3[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    d1[m] = pa[m] - pb[m];
-    d2[m] = pb[m] - pc[m];
-    d3[m] = pc[m] - pa[m];
-  }
-  const R ng = -g;
-  const cx<R> s1 = ng * dot(d1, gc), s3 = ng * dot(d3, gb), bc = ng * dot(gb, gc);
-  W4<R> u;
-#pragma unroll
-  for (int m = 0; m < 4; ++m) u.c[m] = s1 * gb.c[m] + d2[m] * bc + s3 * gc.c[m];
-  return u;
-}
-
-// ggggxx with one wavefunction free, written as free . G(x, y, z) with
-//   G(x, y, z) = gg [ z (x.y) - y (x.z) ]
-// ggggxx(a, b, c, d) = a.G(b, c, d) = b.G(a, d, c) = c.G(d, a, b) = d.G(c, b, a).
-template <typename R>
-MEA_HD W4<R> gggg_part(const W4<R>& x, const W4<R>& y, const W4<R>& z, R gg) {
-  const cx<R> xy = gg * dot(x, y), xz = gg * dot(x, z);
-  W4<R> o;
-#pragma unroll
-  for (int m = 0; m < 4; ++m) o.c[m] = xy * z.c[m] - xz * y.c[m];
-  return o;
-}
+// vvv_part and gggg_part above are the partials of vvvxxx and ggggxx: any
+// slot of either can be the free one (cyclic shift of vvvxxx; the four slot
+// orders of ggggxx listed with G).
 
 // iovxx0 = g fo slash(V) fi with V free: the vector g fo gamma^mu fi, so that
 // iov_amp = V . P (metric contraction).

@@ -111,9 +111,9 @@ def test_vertex_partials_reduce_the_flop_count():
     """The program shares vertex partials (fewer FLOPs than one vertex call
     per diagram) where diagrams share all amplitude-vertex inputs but one; the
     2 -> 2 processes have no such groups.  Counts from the op costs of
-    heget.cuh: gg>ggg 13 098 -> 9 514, gg>gggg 147 957 -> 85 107 per helicity."""
+    heget.cuh: gg>ggg 12 702 -> 9 742, gg>gggg 144 232 -> 86 272 per helicity."""
     from paper_0909_5257_gb300 import mea
-    for pdg, plain, part in (([21] * 5, 13098, 9514), ([21] * 6, 147957, 85107)):
+    for pdg, plain, part in (([21] * 5, 12702, 9742), ([21] * 6, 144232, 86272)):
         info = mea.Process(pdg, host_only=True).info
         assert info["flops_per_hel_plain"] == plain
         assert info["flops_per_hel"] == part
@@ -135,6 +135,15 @@ def test_binding_rejects_tensors_the_kernels_would_misread():
          "contiguous"),
     ]
     for mom, me2, word in cases:
+        for call in (P.evaluate, P.evaluate_noalloc, P.autotune):
+            with pytest.raises(mea.MeaError) as e:
+                call(mom, me2)
+            assert e.value.status == -1 and word in str(e.value)
+    # mistyped outputs of the allocation-free entry point (the other arguments
+    # given as raw addresses, which pass to the library unchecked; the check
+    # raises before the call)
+    for me2, flags, word in ((torch.zeros(n, dtype=torch.float32), None, "float64"),
+                             (0, torch.zeros(n, dtype=torch.int32), "uint8")):
         with pytest.raises(mea.MeaError) as e:
-            P.evaluate(mom, me2)
+            P.evaluate_noalloc(0, me2, n_events=n, flags=flags)
         assert e.value.status == -1 and word in str(e.value)
