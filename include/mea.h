@@ -105,10 +105,13 @@ typedef struct {
                             values -> MEA_E_ARG */
 } mea_options;
 
-/* Per-event flag bits written to flags_dev. */
+/* Per-event flag bits written to flags_dev.  An event re-evaluated in FP64
+ * keeps the bits that sent it there (MEA_FLAG_CANCEL, MEA_FLAG_QGUARD) and
+ * gains MEA_FLAG_REEVALUATED; MEA_FLAG_NONFINITE then describes the FP64
+ * result. */
 #define MEA_FLAG_REEVALUATED 0x01u  /* result comes from the FP64 re-evaluation */
 #define MEA_FLAG_NONFINITE   0x02u  /* a non-finite value was met */
-#define MEA_FLAG_CANCEL      0x04u  /* error indicator above flag_threshold */
+#define MEA_FLAG_CANCEL      0x04u  /* error indicator of the mixed path above flag_threshold */
 #define MEA_FLAG_QGUARD      0x08u  /* a propagator invariant |q^2| is below 1e-10 of the
                                        squared energy flowing through it (near-singular
                                        kinematics; re-evaluated in FP64 on the mixed path) */
@@ -136,6 +139,9 @@ typedef struct {
   double colour_flops_per_hel; /* 4 n_colour_amplitudes^2: FLOPs of the colour quadratic form */
   double flops_per_hel_plain;  /* flops_per_hel when every diagram amplitude is its own
                                   vertex call (no shared vertex partials) */
+  int64_t n_colour_entries;    /* non-zero diagram -> colour-amplitude coefficients c_{alpha d}
+                                  of Eq. (color-amplitude) over the accumulated colour
+                                  amplitudes; flops_per_hel holds 4 FLOPs for each */
 } mea_process_info_t;
 
 /* ---- process handles ---------------------------------------------------- */
@@ -179,6 +185,35 @@ mea_status mea_check_status(mea_process_t proc, void *stream);
  * the tests) exercise the timeout path without a hung or faulted GPU; the
  * context stays usable.  MEA_E_ARG for a limit out of range. */
 mea_status mea_probe_bounded_wait(mea_process_t proc, uint32_t spin_limit, void *stream);
+
+/* Diagnostics, no counterpart in the paper: per-stage device time of this
+ * process's evaluations.  With timing enabled, every evaluation records a
+ * pair of CUDA events on its stream around the kernel launches of each stage
+ * (amplitudes; colour amplitudes and colour sum of the tensor-core path; the
+ * helicity sum of that path; the FP64 re-evaluation of flagged events).
+ * mea_get_stage_times synchronises with the recorded events, returns the
+ * summed milliseconds and launch counts per stage since the previous query
+ * (or since timing was enabled) and starts a new count.  Stages that ran
+ * concurrently on several streams are each counted in full; launches made
+ * during stream capture are not timed.  Timing costs two event records per
+ * stage launch; off by default.  The straight-line kernels
+ * of small processes fuse amplitudes, colour amplitudes, colour sum and
+ * helicity sum into one launch, counted as MEA_STAGE_AMPLITUDES. */
+enum {
+  MEA_STAGE_AMPLITUDES = 0,        /* amplitude kernel (fused kernel for small processes) */
+  MEA_STAGE_COLOUR_AMPLITUDES = 1, /* tensor-core colour amplitudes J = C A */
+  MEA_STAGE_COLOUR_SUM = 2,        /* tensor-core colour sum J^+ K J */
+  MEA_STAGE_FINISH = 3,            /* helicity sum and flags after the tensor-core stages */
+  MEA_STAGE_REEVALUATION = 4,      /* FP64 re-evaluation of flagged events */
+  MEA_N_STAGES = 5
+};
+typedef struct {
+  double ms[MEA_N_STAGES];
+  int64_t launches[MEA_N_STAGES];
+} mea_stage_times;
+
+mea_status mea_set_stage_timing(mea_process_t proc, int enable);
+mea_status mea_get_stage_times(mea_process_t proc, mea_stage_times *out);
 
 /* ---- evaluation ----------------------------------------------------------- */
 
@@ -299,19 +334,26 @@ mea_status mea_server_destroy(mea_server_t srv);
  * variant never calls cudaMalloc, cudaFree or any allocating routine.
  *
  * Same result as mea_evaluate(proc, momenta_dev, n_events, MEA_HEL_SUM_NONZERO,
- * NULL, prec, me2_dev, flags_dev, stream), except that the colour sum always
- * runs on CUDA cores: where mea_evaluate would use the tensor-core colour stage
- * (MEA_PREC_MIXED with a colour basis of 96 or more, or colour_mode 2) the two
- * agree within the mixed-path tolerance instead of bitwise.  Its scratch (the flagged-event list
- * and, for large processes, wavefunction and colour-amplitude work space) is a
- * fixed array of MEA_NOALLOC_SCRATCH_BYTES in the library's device image,
- * which every GPU that loads the library holds until the process exits.
+ * NULL, prec, me2_dev, flags_dev, stream), bit for bit -- with the same launch
+ * configuration, the one mea_autotune chose if it has run -- except that the
+ * colour sum always runs on CUDA cores: where mea_evaluate would use the
+ * tensor-core colour stages (MEA_PREC_MIXED for processes of six or more
+ * partons, or colour_mode 2) the two agree within the mixed-path tolerance
+ * (median 1e-6, max 1e-4 relative) instead of bitwise.  Events flagged on the
+ * mixed path are re-evaluated in FP64 as in mea_evaluate.  Its scratch (the
+ * flagged-event list and, for processes without a straight-line kernel,
+ * wavefunction and colour-amplitude work space) is a fixed array of
+ * MEA_NOALLOC_SCRATCH_BYTES in the library's device image, which every GPU
+ * that loads the library holds until the process exits.
  *   - A request whose scratch would exceed that size is rejected with
  *     MEA_E_ARG before anything is enqueued (mea_last_error() gives the bytes
  *     needed); for gg -> ggg the flagged-event list limits n_events to about
- *     8.38 million per call.
- *   - The first call on each device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     8.38 million per call, for gg -> gggg the work space to a few hundred
+ *     events.
+ *   - The first call on each device (and the first after its CUDA context was
+ *     recreated, e.g. by cudaDeviceReset) looks up the array's device address
+ *     with that device current; make that first call before any stream
+ *     capture.
  *   - All calls share the one array and it keeps the last call's contents
  *     (the event-count word is cleared on the stream at the start of every
  *     call).  Calls whose GPU work overlaps -- on different streams, or from
@@ -406,6 +448,16 @@ mea_status mea_partonic_cross_section_vegas(mea_process_t proc, double sqrt_s, c
 /* ---- diagnostics ------------------------------------------------------------ */
 
 const char *mea_last_error(void);
+
+/* Measured arithmetic peak of the FP32 (fp64 = 0) or FP64 (fp64 = 1) pipe of
+ * the current device, the denominator of the amplitude kernels' rooflines (no
+ * counterpart in the paper): a kernel of independent fused multiply-add
+ * chains, every SM several CTAs deep, timed with CUDA events after a warm-up
+ * launch, the timed launch sized for about `seconds` (0 < seconds <= 10).
+ * *tflops receives 2 FLOP per FMA over the launch's duration, *ms that
+ * duration.  Changes no clock or power setting: the result holds at whatever
+ * SM clock the GPU ran (sample it alongside to normalise).  Synchronous. */
+mea_status mea_measure_alu_peak(int fp64, double seconds, double *tflops, double *ms);
 
 /* Number of kernels this library has launched in this process (all devices). */
 uint64_t mea_kernel_launch_count(void);

@@ -237,7 +237,9 @@ __device__ __forceinline__ void tile_finish(const AmpLaunch& A, int t, int E, in
         }
         if (A.flags) {
           if (A.write_flags_mode == 0) A.flags[gev] = fl;
-          else A.flags[gev] = (uint8_t)((A.flags[gev] & ~MEA_FLAG_CANCEL) | MEA_FLAG_REEVALUATED | fl);
+          // re-evaluation: keep why the event was flagged (cancellation, input
+          // checks), take finiteness from the FP64 result
+          else A.flags[gev] = (uint8_t)((A.flags[gev] & ~MEA_FLAG_NONFINITE) | MEA_FLAG_REEVALUATED | fl);
         }
         if (A.flag_list && (fl & (MEA_FLAG_CANCEL | MEA_FLAG_NONFINITE | MEA_FLAG_QGUARD))) {
           int slot = atomicAdd(A.flag_count, 1);

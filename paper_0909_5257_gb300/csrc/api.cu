@@ -60,6 +60,7 @@ cudaError_t upload(mea_process_s* P, const std::vector<T>& v, const T** out) {
 
 void destroy(mea_process_s* P) {
   if (!P) return;
+  for (cudaEvent_t e : P->st_events) cudaEventDestroy(e);
   for (void* d : P->owned) cudaFree(d);
   for (auto& x : P->scr) x.release();
   for (int i = 0; i < 2; ++i) {
@@ -85,6 +86,48 @@ cudaError_t place_scratch(mea::DevBuf& buf, const mea::DevProgram& d, bool fp64,
   a.slot_scratch = reinterpret_cast<float*>(reinterpret_cast<char*>(buf.p) + jb);
   return cudaSuccess;
 }
+
+// Stage timing: CUDA events on the launching stream around one stage's
+// launches, when the process has stage timing enabled (off by default; the
+// pool of events only grows).
+class StageTimer {
+ public:
+  StageTimer(mea_process_s* P, cudaStream_t s, int stage) : P_(P), s_(s) {
+    if (!P->stage_timing) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    std::lock_guard<std::mutex> lk(P->st_mu);
+    const size_t k = P->st_used;
+    while (P->st_events.size() < 2 * (k + 1)) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+      }
+      P->st_events.push_back(e);
+    }
+    if (P->st_stage.size() < k + 1) P->st_stage.resize(k + 1);
+    P->st_stage[k] = stage;
+    if (cudaEventRecord(P->st_events[2 * k], s) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    pair_ = (long)k;
+    P->st_used = k + 1;
+  }
+  ~StageTimer() {
+    if (pair_ < 0) return;
+    std::lock_guard<std::mutex> lk(P_->st_mu);
+    if (cudaEventRecord(P_->st_events[2 * pair_ + 1], s_) != cudaSuccess) cudaGetLastError();
+  }
+  StageTimer(const StageTimer&) = delete;
+  StageTimer& operator=(const StageTimer&) = delete;
+
+ private:
+  mea_process_s* P_;
+  cudaStream_t s_;
+  long pair_ = -1;
+};
 
 // Mixed path with both colour stages on the tensor cores: the interpreter
 // writes every diagram amplitude (no colour accumulators), the colour
@@ -192,11 +235,20 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
     a.pair_kappa = reinterpret_cast<float*>(S.pairk.p);
     a.ev_flags = reinterpret_cast<uint8_t*>(S.evf.p);
     MEA_CUDA(place_scratch(S.s32, dp, false, c, a));
-    MEA_CUDA(mea::launch_amp(dp, false, c, a, s));
+    {
+      StageTimer tm(P, s, MEA_STAGE_AMPLITUDES);
+      MEA_CUDA(mea::launch_amp(dp, false, c, a, s));
+    }
     jg.n_pairs = cn * H;
-    MEA_CUDA(mea::launch_jamp_gemm(jg, P->num_sms, s));
+    {
+      StageTimer tm(P, s, MEA_STAGE_COLOUR_AMPLITUDES);
+      MEA_CUDA(mea::launch_jamp_gemm(jg, P->num_sms, s));
+    }
     cg.n_pairs = cn * H;
-    MEA_CUDA(mea::launch_colour_gemm(cg, P->num_sms, s));
+    {
+      StageTimer tm(P, s, MEA_STAGE_COLOUR_SUM);
+      MEA_CUDA(mea::launch_colour_gemm(cg, P->num_sms, s));
+    }
     mea::AmpLaunch f = a;
     f.amp_out = nullptr;
     bool reeval = P->opts.reeval_fp64 != 0;
@@ -205,9 +257,12 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
       f.flag_list = reinterpret_cast<int32_t*>(S.flag_list.p);
       f.flag_count = reinterpret_cast<int32_t*>(S.flag_count.p);
     }
-    MEA_CUDA(mea::launch_finish(f, H, reinterpret_cast<const double*>(S.pairval.p),
-                                reinterpret_cast<const float*>(S.pairk.p), s,
-                                reinterpret_cast<const float*>(S.jabs.p), JM.n_splits));
+    {
+      StageTimer tm(P, s, MEA_STAGE_FINISH);
+      MEA_CUDA(mea::launch_finish(f, H, reinterpret_cast<const double*>(S.pairval.p),
+                                  reinterpret_cast<const float*>(S.pairk.p), s,
+                                  reinterpret_cast<const float*>(S.jabs.p), JM.n_splits));
+    }
     if (reeval) {
       mea::AmpConfig c2 = mea::cached_plan(P, P->dev, true, false, H, cn);
       mea::AmpLaunch b = f;
@@ -217,6 +272,7 @@ mea_status do_evaluate_tc(mea_process_s* P, mea::EvalScratch& S, const double* m
       b.flag_count = nullptr;
       b.write_flags_mode = 1;
       MEA_CUDA(place_scratch(S.s64, P->dev, true, c2, b));
+      StageTimer tm(P, s, MEA_STAGE_REEVALUATION);
       MEA_CUDA(mea::launch_amp(P->dev, true, c2, b, s));
     }
   }
@@ -281,7 +337,10 @@ mea_status do_evaluate(mea_process_s* P, mea::EvalScratch& S, const double* mom,
     a.flag_list = reinterpret_cast<int32_t*>(S.flag_list.p);
     a.flag_count = reinterpret_cast<int32_t*>(S.flag_count.p);
   }
-  MEA_CUDA(mea::launch_amp(P->dev, fp64, c, a, s));
+  {
+    StageTimer tm(P, s, MEA_STAGE_AMPLITUDES);
+    MEA_CUDA(mea::launch_amp(P->dev, fp64, c, a, s));
+  }
   if (reeval) {
     // FP64 re-evaluation of the flagged events; their count is read on the device
     mea::AmpConfig c2 = mea::cached_plan(P, P->dev, true, false, H, n);
@@ -292,6 +351,7 @@ mea_status do_evaluate(mea_process_s* P, mea::EvalScratch& S, const double* mom,
     b.flag_count = nullptr;
     b.write_flags_mode = 1;
     MEA_CUDA(place_scratch(S.s64, P->dev, true, c2, b));
+    StageTimer tm(P, s, MEA_STAGE_REEVALUATION);
     MEA_CUDA(mea::launch_amp(P->dev, true, c2, b, s));
   }
   return MEA_OK;
@@ -518,6 +578,10 @@ mea_status mea_process_info(mea_process_t P, mea_process_info_t* info) {
   info->flops_per_hel = G.flops_per_hel;
   info->colour_flops_per_hel = 4.0 * (double)G.n_jamp * (double)G.n_jamp;
   info->flops_per_hel_plain = G.flops_per_hel_plain;
+  int64_t nnz = 0;
+  for (const mea::Op& op : G.ops)
+    if (mea::is_amp_op(op.type)) nnz += op.col_count;
+  info->n_colour_entries = nnz;
   return MEA_OK;
 }
 
@@ -558,6 +622,34 @@ mea_status mea_probe_bounded_wait(mea_process_t P, uint32_t spin_limit, void* st
   if (P->host_only) return fail(MEA_E_UNSUPPORTED, "mea_probe_bounded_wait: host-only process handle");
   if (spin_limit < 1 || spin_limit > (1u << 20)) return fail(MEA_E_ARG, "mea_probe_bounded_wait: limit out of range");
   MEA_CUDA(mea::launch_wait_probe(P->status, spin_limit, reinterpret_cast<cudaStream_t>(stream)));
+  return MEA_OK;
+}
+
+mea_status mea_set_stage_timing(mea_process_t P, int enable) {
+  if (!P) return fail(MEA_E_ARG, "mea_set_stage_timing: null process");
+  if (P->host_only) return fail(MEA_E_UNSUPPORTED, "mea_set_stage_timing: host-only process handle");
+  std::lock_guard<std::mutex> lk(P->st_mu);
+  P->stage_timing = enable != 0;
+  P->st_used = 0;
+  return MEA_OK;
+}
+
+mea_status mea_get_stage_times(mea_process_t P, mea_stage_times* out) {
+  if (!P || !out) return fail(MEA_E_ARG, "mea_get_stage_times: null argument");
+  std::memset(out, 0, sizeof(*out));
+  if (P->host_only) return MEA_OK;
+  std::lock_guard<std::mutex> lk(P->st_mu);
+  for (size_t k = 0; k < P->st_used; ++k) {
+    MEA_CUDA(cudaEventSynchronize(P->st_events[2 * k + 1]));
+    float ms = 0.f;
+    MEA_CUDA(cudaEventElapsedTime(&ms, P->st_events[2 * k], P->st_events[2 * k + 1]));
+    const int st = P->st_stage[k];
+    if (st >= 0 && st < MEA_N_STAGES) {
+      out->ms[st] += ms;
+      out->launches[st] += 1;
+    }
+  }
+  P->st_used = 0;
   return MEA_OK;
 }
 
@@ -712,13 +804,44 @@ mea_status mea_evaluate_host(mea_process_t P, const double* mom_h, int64_t n, me
 
 // ---- evaluation without allocation ------------------------------------------
 // Scratch for mea_evaluate_noalloc: one fixed array in the device image.  Host
-// code must not use its name as a device address; the address is looked up
-// once per device with cudaGetSymbolAddress.
+// code must not use its name as a device address: the address is looked up
+// with cudaGetSymbolAddress, with the device current, once per device and CUDA
+// context (a context created after cudaDeviceReset reloads the module, so the
+// lookup is repeated when the context's unique id changes).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MEA_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[64] = {nullptr};
+struct NoallocSlot {
+  void* ptr = nullptr;
+  unsigned long long ctx_id = 0;
+};
+NoallocSlot g_noalloc[64];
+
+// Unique id of the calling thread's current CUDA context (driver entry points
+// resolved through the runtime, so the library does not link libcuda).
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    resolved = true;
+  }
+  void* ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
 }  // namespace
 
 mea_status mea_evaluate_noalloc(mea_process_t P, const double* mom, int64_t n, mea_prec_mode prec, double* me2,
@@ -735,21 +858,35 @@ mea_status mea_evaluate_noalloc(mea_process_t P, const double* mom, int64_t n, m
   if (dev != P->device) return fail(MEA_E_ARG, "mea_evaluate_noalloc: process belongs to another device");
   void* base = nullptr;
   {
+    // set-up: the array's device address for this device and context
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    unsigned long long ctx = 0;
+    const bool have_ctx = current_context_id(&ctx);
+    NoallocSlot& slot = g_noalloc[dev];
+    if (!slot.ptr || !have_ctx || slot.ctx_id != ctx) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p)
         return fail(MEA_E_CUDA, std::string("mea_evaluate_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_noalloc_ptr[dev] = p;
+      slot.ptr = p;
+      slot.ctx_id = have_ctx ? ctx : 0;
     }
-    base = g_noalloc_ptr[dev];
+    base = slot.ptr;
   }
   const mea::Program& G = P->prog;
   const int H = G.n_hel;
   const bool fp64 = prec == MEA_PREC_FP64;
   const bool reeval = !fp64 && P->opts.reeval_fp64;
+  const int ti = fp64 ? 1 : 0;
+  std::lock_guard<std::mutex> lk(P->mu);
+  // the launch configuration mea_evaluate uses: the tuned one when mea_autotune
+  // (explicit or on first use) has chosen one for this helicity count
   mea::AmpConfig c = mea::cached_plan(P, P->dev, fp64, false, H, n);
+  if (P->tuned[ti].grid > 0 && P->tuned_H[ti] == H && !mea::uses_tensor_path(P, prec, MEA_HEL_SUM_NONZERO)) {
+    c = P->tuned[ti];
+    const int64_t tiles = (n + c.E_cta - 1) / c.E_cta;
+    if (tiles < c.grid) c.grid = (int)std::max<int64_t>(tiles, 1);
+  }
   mea::AmpConfig c2 = mea::cached_plan(P, P->dev, true, false, H, n);
   auto work_bytes = [&](bool f64, const mea::AmpConfig& cc) {
     size_t jb = (mea::jamp_scratch_bytes_needed(P->dev, f64, cc) + 255) & ~size_t(255);
@@ -773,7 +910,6 @@ mea_status mea_evaluate_noalloc(mea_process_t P, const double* mom, int64_t n, m
     a.jamp_scratch = reinterpret_cast<float*>(b + work_off);
     a.slot_scratch = reinterpret_cast<float*>(b + work_off + jb);
   };
-  std::lock_guard<std::mutex> lk(P->mu);
   mea::AmpLaunch a;
   a.mom = mom;
   a.n_events = n;

@@ -87,6 +87,13 @@ struct mea_process_s {
   cudaEvent_t done[2] = {nullptr, nullptr};
   int64_t pipe_chunk = 0;
   bool host_only = false;
+  // stage timing (mea_set_stage_timing): a pair of CUDA events recorded on the
+  // evaluation's stream around every kernel launch, resolved by mea_get_stage_times
+  bool stage_timing = false;
+  std::mutex st_mu;
+  std::vector<cudaEvent_t> st_events;  // pool: 2 per recorded launch
+  std::vector<int> st_stage;           // stage of each recorded pair
+  size_t st_used = 0;                  // pairs recorded since the last query
 };
 
 namespace mea {

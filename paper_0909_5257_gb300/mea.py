@@ -46,7 +46,7 @@ class ProcessInfo(ctypes.Structure):
                 ("n_slots", ctypes.c_int), ("n_colour_amplitudes", ctypes.c_int),
                 ("cf_denominator", ctypes.c_int64), ("cf_max_abs_numerator", ctypes.c_int64),
                 ("flops_per_hel", ctypes.c_double), ("colour_flops_per_hel", ctypes.c_double),
-                ("flops_per_hel_plain", ctypes.c_double)]
+                ("flops_per_hel_plain", ctypes.c_double), ("n_colour_entries", ctypes.c_int64)]
 
 
 class TuneResult(ctypes.Structure):
@@ -65,6 +65,13 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("events_completed", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("busy_seconds", ctypes.c_double), ("reserved_bytes", ctypes.c_size_t)]
+
+
+STAGES = ("amplitudes", "colour_amplitudes", "colour_sum", "finish", "reevaluation")
+
+
+class StageTimes(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5)]
 
 
 class PsConfig(ctypes.Structure):
@@ -93,6 +100,9 @@ def load(path: str | None = None):
             lib.mea_destroy_process.argtypes = [vp]
             lib.mea_check_status.argtypes = [vp, vp]
             lib.mea_probe_bounded_wait.argtypes = [vp, ctypes.c_uint32, vp]
+            lib.mea_set_stage_timing.argtypes = [vp, i32]
+            lib.mea_measure_alu_peak.argtypes = [i32, ctypes.c_double, vp, vp]
+            lib.mea_get_stage_times.argtypes = [vp, vp]
             lib.mea_evaluate.argtypes = [vp, vp, i64, i32, vp, i32, vp, vp, vp]
             lib.mea_evaluate_host.argtypes = [vp, vp, i64, i32, vp, vp]
             lib.mea_evaluate_noalloc.argtypes = [vp, vp, i64, i32, vp, vp, vp]
@@ -116,7 +126,9 @@ def load(path: str | None = None):
                          "mea_evaluate_host", "mea_evaluate_noalloc", "mea_generate_phase_space",
                          "mea_check_status", "mea_autotune", "mea_batch_create", "mea_batch_launch",
                          "mea_batch_info", "mea_batch_destroy", "mea_server_create", "mea_server_submit",
-                         "mea_server_wait", "mea_server_stats", "mea_server_destroy"):
+                         "mea_server_wait", "mea_server_stats", "mea_server_destroy", "mea_set_stage_timing",
+                         "mea_get_stage_times", "mea_probe_bounded_wait", "mea_measure_alu_peak", "mea_partonic_cross_section",
+                         "mea_partonic_cross_section_vegas"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -166,6 +178,14 @@ def _stream(s):
 
 def kernel_launch_count() -> int:
     return int(load().mea_kernel_launch_count())
+
+
+def measure_alu_peak(fp64=False, seconds=0.2):
+    """(TFLOP/s, ms) of an FMA-chain kernel on the current device
+    (mea_measure_alu_peak): the measured FP32 or FP64 pipe peak."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().mea_measure_alu_peak(1 if fp64 else 0, ctypes.c_double(seconds), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 class Process:
@@ -251,6 +271,16 @@ class Process:
         check_status raises MeaError(MEA_E_TIMEOUT)."""
         _check(load().mea_probe_bounded_wait(self._h, ctypes.c_uint32(spin_limit), _stream(stream)))
 
+    def set_stage_timing(self, enable=True):
+        """Record CUDA events around every stage's kernel launches (mea_set_stage_timing)."""
+        _check(load().mea_set_stage_timing(self._h, 1 if enable else 0))
+
+    def stage_times(self):
+        """{stage: (milliseconds, launches)} since the previous call (synchronises)."""
+        st = StageTimes()
+        _check(load().mea_get_stage_times(self._h, ctypes.byref(st)))
+        return {name: (st.ms[i], st.launches[i]) for i, name in enumerate(STAGES)}
+
     def check_status(self, stream=None):
         """Synchronise and raise MeaError(MEA_E_TIMEOUT) if a bounded device wait expired."""
         _check(load().mea_check_status(self._h, _stream(stream)))
@@ -260,6 +290,7 @@ class Process:
         using only the library's fixed device scratch array (no allocation)."""
         if n_events is None:
             n_events = int(momenta.shape[0])
+        self._check_args(momenta, me2, n_events, flags)
         _check(load().mea_evaluate_noalloc(self._h, _ptr(momenta), n_events, precision, _ptr(me2),
                                            _ptr(flags), _stream(stream)))
 
