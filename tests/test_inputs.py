@@ -85,3 +85,76 @@ def test_relative_pt_cut(n_final):
     # ptij_min <= 0 is no cut: the stream equals the default one
     off = ps.generate(ps.PhaseSpaceConfig(n_final, rs_lo=100.0, rs_hi=1000.0, dr_min=0.0, ptij_min=0.0), 4000)
     assert np.array_equal(off, a)
+
+
+def _uncut(n_final, rs=1000.0):
+    """The generator with every cut open (pT > 0, |eta| < 1e9, no Delta R):
+    RAMBO's flat massless n-body phase space at fixed sqrt(s)."""
+    return ps.PhaseSpaceConfig(n_final, rs_lo=rs, rs_hi=rs, pt_min=0.0, eta_max=1e9, dr_min=0.0,
+                               seed=ps.SEED_BASE + 71)
+
+
+@pytest.mark.parametrize("n_final", [3, 4, 5])
+def test_rambo_is_flat_single_parton_energy(n_final):
+    """Flatness of Eq. (phase-space) for n >= 3, pinned by a closed form: in
+    flat massless n-body phase space the energy fraction x = 2E/sqrt(s) of
+    any one parton has the density (n-1)(n-2) x (1-x)^(n-3) on [0, 1]
+    (integrate the other n-1 momenta out: Phi_{n-1} of the recoil system of
+    squared mass s(1-x) grows as (1-x)^(n-3), times x from d^3p/E), i.e.
+    Beta(2, n-2).  Kolmogorov-Smirnov on 60 000 events per parton; a RAMBO
+    map with a wrong Jacobian or conformal boost fails it by orders of
+    magnitude."""
+    stats = pytest.importorskip("scipy.stats")
+    rs = 1000.0
+    mom = ps.generate(_uncut(n_final, rs), 60000)
+    x = 2.0 * mom[:, 2:, 0] / rs
+    for i in range(n_final):
+        p = stats.kstest(x[:, i], stats.beta(2, n_final - 2).cdf).pvalue
+        assert p > 1e-4, (i, p)
+    # the first and second moments of Beta(2, n-2)
+    assert abs(x.mean() - 2.0 / n_final) < 3e-3
+    assert abs((x ** 2).mean() - 6.0 / (n_final * (n_final + 1))) < 3e-3
+
+
+def test_rambo_three_body_dalitz_plot_is_uniform():
+    """n = 3: the Dalitz variables (x1, x2) are uniform over the triangle
+    x1 + x2 > 1, x1 < 1, x2 < 1 (constant matrix element of flat phase
+    space); chi-square over a 10 x 10 grid of the unit square restricted to
+    the triangle (cells cut by the diagonal carry their area fraction)."""
+    stats = pytest.importorskip("scipy.stats")
+    rs = 1000.0
+    n = 200000
+    mom = ps.generate(_uncut(3, rs), n)
+    x1 = 2.0 * mom[:, 2, 0] / rs
+    x2 = 2.0 * mom[:, 3, 0] / rs
+    assert np.all(x1 + x2 >= 1.0 - 1e-12)
+    k = 10
+    h, _, _ = np.histogram2d(x1, x2, bins=k, range=[[0, 1], [0, 1]])
+    # area of each cell inside the triangle (exact: the diagonal crosses cells (i, k-1-i))
+    area = np.zeros((k, k))
+    for i in range(k):
+        for j in range(k):
+            if i + j >= k:
+                area[i, j] = 1.0
+            elif i + j == k - 1:
+                area[i, j] = 0.5
+    expect = n * area / area.sum()
+    m = expect > 0
+    chi2 = float((((h - expect) ** 2)[m] / expect[m]).sum())
+    dof = int(m.sum()) - 1
+    assert stats.chi2.sf(chi2, dof) > 1e-4, (chi2, dof)
+    assert h[~m].sum() == 0
+
+
+@pytest.mark.parametrize("n_final", [3, 5])
+def test_rambo_is_isotropic(n_final):
+    """Flat phase space has no preferred direction: cos(theta) of every
+    parton is uniform on [-1, 1] and phi uniform on (-pi, pi]."""
+    stats = pytest.importorskip("scipy.stats")
+    mom = ps.generate(_uncut(n_final), 40000)
+    fin = mom[:, 2:]
+    cth = fin[..., 3] / np.linalg.norm(fin[..., 1:], axis=-1)
+    phi = np.arctan2(fin[..., 2], fin[..., 1])
+    for i in range(n_final):
+        assert stats.kstest(cth[:, i], stats.uniform(-1, 2).cdf).pvalue > 1e-4
+        assert stats.kstest(phi[:, i], stats.uniform(-np.pi, 2 * np.pi).cdf).pvalue > 1e-4

@@ -1,7 +1,8 @@
 """The pins catch plausible mistakes: each test builds a copy of the oracle
 with one deliberate mistake planted (OQ_MUTATION in qcd_oracle.cpp) and checks
 that the battery of pins -- closed forms, Parke-Taylor (gluons and one quark line),
-Ward identities, Bose symmetry -- rejects it, while the unmutated copy passes the same battery.
+Ward identities, Bose symmetry, the collinear limit of u u -> u u g g --
+rejects it, while the unmutated copy passes the same battery.
 
 Mutations: 1 a dropped term of the ggg vertex, 2 a flipped sign of one gggg
 colour structure, 3 the metric dropped from the gluon propagator (index slip),
@@ -18,6 +19,7 @@ import pytest
 import oracle
 from paper_0909_5257_gb300 import phasespace as ps
 from tests import physics_ref as ref
+from tests import test_oracle_collinear as coll
 
 
 def _events(n_final, n, lo=300.0, hi=3000.0):
@@ -77,6 +79,11 @@ def _battery(lib):
     base = P.me2(mom3)
     if not np.allclose(P.me2(mom3[:, [0, 1, 4, 2, 3]]), base, rtol=1e-12, atol=0):
         failed.append("Bose symmetry gg>ggg")
+    small, big, leg, kernel, n_phi, z = coll.CASES[0]
+    ev = coll._events(small, 2, ps.SEED_BASE + 63)
+    r = coll._ratio(small, big, ev, leg, z, 1e-5, kernel, n_phi, lib=lib)
+    if not np.all(np.abs(r - 1.0) < 5e-4):
+        failed.append("collinear limit uu>uugg")
     return failed
 
 
