@@ -1,25 +1,40 @@
-"""Benchmark: helicity-summed |M|^2 events/s per subprocess, mixed vs FP64 path.
+"""Benchmark: helicity-summed |M|^2 events/s per subprocess, mixed vs FP64 path; p50/p99.
 
-Workload (default "3jet"): g g -> g g g, u u~ -> g g g and u u -> u u g, 2^20
-synthetic events each per GPU (RAMBO flat massless phase space in the partonic
-centre-of-mass frame, sqrt(s_hat) log-uniform in [200 GeV, 2 TeV], cuts
-pT > 20 GeV, |eta| < 2.5, Delta R > 0.4, alpha_s = 0.118).  One step evaluates
-every subprocess once.  Momenta are generated on the device before timing and
-stay resident (2^20 x 5 x 32 B = 168 MB per subprocess, larger than L2, so no
-explicit L2 flush is needed between steps).
+Default workload "serve" -- the serving configuration: requests over
+g g -> 5g (7245 diagrams, 720 colours), u u~ -> 5g (1890 diagrams, 120 colours)
+and u u -> u u + 3g (786 diagrams, 240 colours), process mix 40/40/20 % by
+request, request sizes log-uniform in [2^10, 2^18] events, sqrt(s_hat)
+log-uniform in [500 GeV, 5 TeV] (RAMBO flat massless phase space in the
+partonic centre-of-mass frame, cuts pT > 20 GeV, |eta| < 2.5, Delta R > 0.4,
+alpha_s = 0.118).  Synthetic, seeded data; momenta generated on the device
+before timing.  Inputs are larger than L2 (one request of 2^18 events holds
+59 MB of momenta plus GBs of tensor-path scratch), so no explicit flush.
 
-Before timing, every subprocess is autotuned once per precision
-(mea_autotune on the full launch for the straight-line kernels of the
-processes with up to five partons, else on 2^16 events).  The line reports per subprocess the mixed and
-FP64 rates, their relative difference (median / p99 / max), the flagged
-fraction and the rate of the paper's sampled-helicity mode (one helicity per
-event); the roofline of the dominant kernel; e2e through host buffers; clocks;
-the oracle on the host cores as cpu_baseline.  Other workloads: --workload
-2jet | 4jet | batch (one CUDA graph over four uneven subprocesses) | serve
-(Poisson arrivals through the server, p50/p99).
+One step = REQS_PER_STEP requests.  After W warm-up steps, the K timed steps'
+requests are all submitted to the continuous-batching server (mea_server_*)
+at once and the timed region ends when the last completes: `value` is the
+whole job's events/s at saturation (capacity), `ms_per_step` the timed
+region / K.  Then, with the same requests:
+  * latency: Poisson arrivals at 0.8 x the measured capacity, `p50_ms` and
+    `p99_ms` of submit-to-completion latency (mixed path);
+  * e2e: every request's momenta copied from pinned host memory to the
+    device, submitted, and its |M|^2 copied back, inside the timed region;
+  * per subprocess: device-timed (CUDA events) mixed events/s on 2^16-2^17
+    events, FP64 events/s on a subsample of the same inputs, the mixed-vs-FP64
+    relative error (median / p99 / max) and the flagged fraction;
+  * roofline of the dominant kernel (the stage with the largest share of the
+    mix's device time, timed per stage with CUDA events on its stream), the
+    tensor-core stages' useful and executed rates against the sustained BF16
+    peak, measured FP32 / FP64 pipe peaks (FMA-chain kernel, this GPU);
+  * cpu_baseline: the FP64 oracle on the host cores on a bounded sample of the
+    mix, and the FP64 GPU path's largest relative error against it there.
+Other workloads (also reported as extra keys unless --no-extra): "3jet"
+(gg>ggg, uu~>ggg, uu>uug, 2^20 each), "4jet" (gg>gggg, uu~>gggg), "batch"
+(one CUDA graph over four uneven subprocesses), "2jet"; "single" evaluates one
+subprocess (--process, --events) inside an NVTX range "eval" for profilers.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload 3jet|2jet|4jet|batch|serve]
+                       [--workload serve|3jet|4jet|2jet|batch|single]
 Prints one JSON line on rank 0.
 """
 from __future__ import annotations
@@ -39,17 +54,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "helicity-summed |M|^2 events/s per subprocess, mixed vs FP64 path; p50/p99"
-# ncu (dram__bytes_read.sum + dram__bytes_write.sum), one 2^20-event launch of
-# the mixed-path kernel each subprocess runs: gg>ggg the per-diagram body at
-# 128 registers, uu~>ggg the vertex-partial body at 128, uu>uug the per-diagram
-# body at 85
-TRAFFIC_BYTES_PER_EVENT = {"gg>ggg": (206848000 + 7545397760) / 2 ** 20,
-                           "uu~>ggg": (168618752 + 7403264) / 2 ** 20,
-                           "uu>uug": (168189952 + 21019136) / 2 ** 20}
 SEED_BASE = 0x09095257
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2070.0
 
+# ---- serving workload ------------------------------------------------------
+SERVE_MIX = [("gg>ggggg", [21] * 7, 5, 0.4), ("uu~>ggggg", [2, -2, 21, 21, 21, 21, 21], 5, 0.4),
+             ("uu>uuggg", [2, 2, 2, 2, 21, 21, 21], 5, 0.2)]
+SERVE_RS = (500.0, 5000.0)
+SERVE_SIZES = (1 << 10, 1 << 18)
+REQS_PER_STEP = 3
+SERVE_SLOTS = 4
+SERVE_CHUNK = 1 << 12
+SERVE_LOAD = 0.8
+# per-subprocess device-timed pass: events (mixed), FP64 subsample, oracle sample
+SUB_EVENTS = {"gg>ggggg": 1 << 16, "uu~>ggggg": 1 << 17, "uu>uuggg": 1 << 17}
+FP64_EVENTS = {"gg>ggggg": 2048, "uu~>ggggg": 8192, "uu>uuggg": 16384}
+CPU_SAMPLE = {"gg>ggggg": 16, "uu~>ggggg": 16, "uu>uuggg": 8}
+REF_PER_STEP = {"gg>ggggg": 4, "uu~>ggggg": 4, "uu>uuggg": 2}
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum) per event of the dominant
+# kernel, from the capture summarised in profiles/ (None: not captured for
+# the current kernel)
+TRAFFIC_BYTES_PER_EVENT = {}
+
+# ---- device-resident workloads (extra keys) ------------------------------------
 WORKLOADS = {
     # name: (subprocesses, events per subprocess per GPU, seed offset)
     "3jet": ([("gg>ggg", [21, 21, 21, 21, 21], 3, 200.0, 2000.0),
@@ -64,6 +92,12 @@ WORKLOAD_TEXT = {
     "3jet": "gg>ggg + uu~>ggg + uu>uug, 2^20 events each per GPU, sqrt(s) in [200 GeV, 2 TeV]",
     "2jet": "gg>gg + uu~>gg, 2^14 events each per GPU, sqrt(s) in [200 GeV, 2 TeV]",
     "4jet": "gg>gggg + uu~>gggg, 2^20 events each per GPU, sqrt(s) in [300 GeV, 3 TeV]",
+}
+SINGLE = {
+    "gg3g": ([21] * 5, 200.0, 2000.0), "uu3g": ([2, -2, 21, 21, 21], 200.0, 2000.0),
+    "uuuug": ([2, 2, 2, 2, 21], 200.0, 2000.0), "gg4g": ([21] * 6, 300.0, 3000.0),
+    "uu4g": ([2, -2, 21, 21, 21, 21], 300.0, 3000.0), "uuuu3g": ([2, 2, 2, 2, 21, 21, 21], 500.0, 5000.0),
+    "uu5g": ([2, -2] + [21] * 5, 500.0, 5000.0), "gg5g": ([21] * 7, 500.0, 5000.0),
 }
 
 
@@ -118,7 +152,7 @@ class ClockSampler:
             self.proc.kill()
         self.file.flush()
         self.file.seek(0)
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.file.read().splitlines():
             f = [x.strip() for x in line.split(",")]
@@ -127,6 +161,7 @@ class ClockSampler:
             try:
                 sm.append(float(f[1]))
                 smax.append(float(f[2]))
+                power.append(float(f[3]))
             except ValueError:
                 continue
             for n, v in zip(names, f[5:9]):
@@ -136,6 +171,7 @@ class ClockSampler:
         os.unlink(self.file.name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
@@ -154,6 +190,24 @@ def max_over_ranks_value(x: float, dist=None, device=None) -> float:
     return float(t.item())
 
 
+def serve_requests(rank: int, n_req: int, seed: int = SEED_BASE + 4):
+    """The serving workload's request stream: request k = (subprocess index,
+    events, first event of its momenta in that subprocess's generator
+    stream).  Rank r takes requests [r*n_req, (r+1)*n_req) of one seeded
+    stream, so the ranks' requests are disjoint (weak scaling)."""
+    rng = np.random.default_rng(seed)
+    total = (rank + 1) * n_req
+    kinds = rng.choice(len(SERVE_MIX), size=total, p=[w for *_, w in SERVE_MIX])
+    sizes = np.exp(rng.uniform(np.log(SERVE_SIZES[0]), np.log(SERVE_SIZES[1]), size=total)).astype(np.int64)
+    firsts = np.zeros(total, dtype=np.int64)
+    nxt = [0] * len(SERVE_MIX)
+    for k in range(total):
+        firsts[k] = nxt[kinds[k]]
+        nxt[kinds[k]] += int(sizes[k])
+    lo = rank * n_req
+    return [(int(kinds[k]), int(sizes[k]), int(firsts[k])) for k in range(lo, total)]
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -161,47 +215,66 @@ def _dist():
     return ws, rank, local
 
 
+# ---- the oracle (reference arm and cpu_baseline) --------------------------------
 def run_reference(args):
     """The oracle (FP64 CPU, all host cores), as it stands, on a bounded sample
-    of the same workload: each step evaluates `ref_events` events of every
-    subprocess."""
+    of the same workload; rank 0 only."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     import oracle
     from paper_0909_5257_gb300 import phasespace as ps
-    subs, n_full, seed_off = WORKLOADS[args.workload]
-    n = args.ref_events
+    if args.workload == "serve":
+        subs = [(name, pdg, nf, SERVE_RS[0], SERVE_RS[1]) for name, pdg, nf, _ in SERVE_MIX]
+        per_step = dict(REF_PER_STEP)
+        seed = SEED_BASE + 4
+        text = serve_workload_text()
+    else:
+        subs, _, seed_off = WORKLOADS[args.workload]
+        per_step = {s[0]: args.ref_events for s in subs}
+        seed = SEED_BASE + seed_off
+        text = WORKLOAD_TEXT[args.workload]
     procs, moms = [], []
+    total_steps = args.warmup + args.steps
     for name, pdg, nf, lo, hi in subs:
         procs.append(oracle.OracleProcess(pdg))
-        moms.append(ps.generate(ps.PhaseSpaceConfig(nf, rs_lo=lo, rs_hi=hi, seed=SEED_BASE + seed_off), n))
-    for _ in range(args.warmup):
-        for P, m in zip(procs, moms):
-            P.me2(m[: max(1, n // 16)])
+        moms.append(ps.generate(ps.PhaseSpaceConfig(nf, rs_lo=lo, rs_hi=hi, seed=seed),
+                                per_step[name] * total_steps))
+    for s in range(args.warmup):
+        for (name, *_), P, m in zip(subs, procs, moms):
+            k = per_step[name]
+            P.me2(m[s * k:(s + 1) * k])
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for P, m in zip(procs, moms):
-            P.me2(m)
+    for s in range(args.warmup, total_steps):
+        for (name, *_), P, m in zip(subs, procs, moms):
+            k = per_step[name]
+            P.me2(m[s * k:(s + 1) * k])
     dt = time.perf_counter() - t0
-    ev = args.steps * n * len(subs)
+    ev = args.steps * sum(per_step.values())
     value = ev / dt
     cores = oracle.max_threads()
+    sample = ", ".join(f"{per_step[s[0]]} {s[0]}" for s in subs)
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "sample_events_per_subprocess_per_step": n},
+        "config": {"workload": text, "sample_per_step": sample},
         "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{n} events of each subprocess per step, {args.steps} steps"},
+                         "sample": f"{sample} events per step (distinct events every step), {args.steps} steps"},
         "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
 
 
+def serve_workload_text():
+    return ("serving: continuous batching over gg>ggggg / uu~>ggggg / uu>uuggg, mix 40/40/20 % by request, "
+            "request sizes log-uniform in [2^10, 2^18] events, sqrt(s) in [500 GeV, 5 TeV]")
+
+
 def cpu_baseline(subs, seed_off, budget_s=12.0, single_budget_s=3.0):
-    """Oracle on the host cores over a bounded sample of the workload, and on
-    one core over a smaller one (the paper compares with one CPU core)."""
+    """Oracle on the host cores over a bounded sample of a device-resident
+    workload, and on one core over a smaller one (the paper compares with
+    one CPU core)."""
     import oracle
     from paper_0909_5257_gb300 import phasespace as ps
     cores = oracle.max_threads()
@@ -232,196 +305,60 @@ def cpu_baseline(subs, seed_off, budget_s=12.0, single_budget_s=3.0):
             "single_core_value": one_ev / one_t, "single_core_sample": f"{one_ev} events in {one_t:.1f} s"}
 
 
-BATCH_SPEC = [  # (name, pdg, n_final, sqrt(s) range, configured events)
-    ("gg>ggg", [21, 21, 21, 21, 21], 3, 200.0, 2000.0, 1 << 18),
-    ("uu~>gggg", [2, -2, 21, 21, 21, 21], 4, 300.0, 3000.0, 1 << 20),
-    ("uu>uuggg", [2, 2, 2, 2, 21, 21, 21], 5, 300.0, 3000.0, 1 << 19),
-    ("gg>gggg", [21] * 6, 4, 300.0, 3000.0, 1 << 17),
-]
-
-
-def run_batch(args):
-    """Batched mixed launch: four subprocesses of very uneven cost, counts
-    perturbed by a seeded draw, autotuned per process, evaluated by one
-    CUDA-graph launch per step (mea_batch_*); mixed vs FP64 graph."""
+def serve_cpu_baseline(procs):
+    """The oracle on the host cores over a bounded sample of the serving mix
+    (CPU_SAMPLE events per subprocess, host generator), and the FP64 GPU
+    path's relative error against it on those very events."""
     import torch
+
+    import oracle
     from paper_0909_5257_gb300 import mea
-    torch.cuda.set_device(0)
-    rng = np.random.default_rng(SEED_BASE + 3)
-    procs, moms, n_ev = [], [], []
-    for name, pdg, nf, lo, hi, n in BATCH_SPEC:
-        n = max(64, int(n * args.scale * rng.uniform(0.75, 1.25)))
-        P = mea.Process(pdg)
-        m = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
-        mea.generate_phase_space(nf, n, m, seed=SEED_BASE + 3, rs_lo=lo, rs_hi=hi)
-        procs.append(P); moms.append(m); n_ev.append(n)
-    tune = {}
-    for (name, *_), P, m in zip(BATCH_SPEC, procs, moms):
-        k = min(m.shape[0], 1 << 14)
-        scratch = torch.empty(k, dtype=torch.float64, device="cuda")
-        tune[name] = P.autotune(m[:k], scratch, precision=mea.PREC_MIXED)
-    res = {}
-    for prec, pname in ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64")):
-        outs = [torch.empty(n, dtype=torch.float64, device="cuda") for n in n_ev]
-        flags = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in n_ev]
-        B = mea.Batch(list(zip(procs, moms, outs, flags)), precision=prec)
-        steps = args.steps if pname == "mixed" else max(1, min(args.steps, 2))
-        for _ in range(max(1, args.warmup if pname == "mixed" else 1)):
-            B.launch()
-        torch.cuda.synchronize()
-        l0 = mea.kernel_launch_count()
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0.record()
-        for _ in range(steps):
-            B.launch()
-        t1.record()
-        torch.cuda.synchronize()
-        ms = t0.elapsed_time(t1) / steps
-        res[pname] = {"events_per_s": sum(n_ev) / (ms * 1e-3), "ms_per_launch": ms, "steps": steps,
-                      "graph_kernel_nodes": B.kernel_nodes, "kernels_launched": mea.kernel_launch_count() - l0}
-        res[pname + "_out"] = [o.clone() for o in outs]
-        B.close()
-    errs = {}
-    for i, (name, *_) in enumerate(BATCH_SPEC):
-        rel = (res["mixed_out"][i] / res["fp64_out"][i] - 1.0).abs()
-        errs[name] = {"events": n_ev[i], "mixed_vs_fp64_rel_err_median": float(rel.median()),
-                      "mixed_vs_fp64_rel_err_max": float(rel.max()), "autotune": tune[name]}
-    out = {"metric": METRIC, "value": res["mixed"]["events_per_s"], "unit": "events/s", "n_gpus": 1,
-           "steps": res["mixed"]["steps"], "warmup": args.warmup, "ms_per_step": res["mixed"]["ms_per_launch"],
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32 amplitudes + tcgen05 f16-split colour sum; f64 re-evaluation", "data": "synthetic",
-           "config": {"workload": "batched mixed launch (one CUDA graph): " +
-                      ", ".join(f"{b[0]} {n}" for b, n in zip(BATCH_SPEC, n_ev)),
-                      "scale": args.scale},
-           "fp64": {k: v for k, v in res["fp64"].items()}, "mixed": {k: v for k, v in res["mixed"].items()},
-           "per_subprocess": errs, "gpu_launches": res["mixed"]["kernels_launched"]}
-    print(json.dumps(out), flush=True)
-
-
-SERVE_MIX = [("gg>ggggg", [21] * 7, 5, 0.4), ("uu~>ggggg", [2, -2, 21, 21, 21, 21, 21], 5, 0.4),
-             ("uu>uuggg", [2, 2, 2, 2, 21, 21, 21], 5, 0.2)]
-
-
-def run_serve(args):
-    """Serving: Poisson arrivals, request sizes log-uniform in
-    [2^10, 2^18] x scale events, mix 40/40/20 % of gg>ggggg, uu~>ggggg,
-    uu>uuggg, sqrt(s) in [500 GeV, 5 TeV]; offered load a fraction of the
-    measured capacity; p50/p99 latency and throughput for the mixed and the
-    FP64 path."""
-    import torch
-    from paper_0909_5257_gb300 import mea
-    torch.cuda.set_device(0)
-    rng = np.random.default_rng(SEED_BASE + 4)
-    procs = {name: mea.Process(pdg) for name, pdg, _, _ in SERVE_MIX}
-    n_req = max(8, args.steps * 4)
-    lo_n, hi_n = (1 << 10) * args.scale, (1 << 18) * args.scale
-    reqs = []
-    first = 0
-    for k in range(n_req):
-        name, pdg, nf, _ = SERVE_MIX[int(rng.choice(3, p=[w for *_, w in SERVE_MIX]))]
-        n = max(16, int(np.exp(rng.uniform(np.log(lo_n), np.log(hi_n)))))
-        m = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
-        mea.generate_phase_space(nf, n, m, first_event=first, seed=SEED_BASE + 4, rs_lo=500.0, rs_hi=5000.0)
-        first += n
-        reqs.append((name, m, n))
-    torch.cuda.synchronize()
-    results = {}
-    for prec, pname in ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64")):
-        # capacity: back-to-back submission
-        srv = mea.Server(mem_budget_bytes=160 << 30, n_slots=4, chunk_events=1 << 12)
-        outs = [torch.empty(n, dtype=torch.float64, device="cuda") for _, _, n in reqs]
+    from paper_0909_5257_gb300 import phasespace as ps
+    cores = oracle.max_threads()
+    tot_ev, tot_t, parts, errs = 0, 0.0, [], {}
+    for name, pdg, nf, _ in SERVE_MIX:
+        n = CPU_SAMPLE[name]
+        mom = ps.generate(ps.PhaseSpaceConfig(nf, rs_lo=SERVE_RS[0], rs_hi=SERVE_RS[1], seed=SEED_BASE + 24), n)
+        P = oracle.OracleProcess(pdg)
         t0 = time.perf_counter()
-        ids = [srv.submit(procs[nm], m, o, precision=prec) for (nm, m, n), o in zip(reqs, outs)]
-        for i in ids:
-            srv.wait(i, timeout_ms=600000)
-        cap_s = time.perf_counter() - t0
-        total = sum(n for _, _, n in reqs)
-        srv.close()
-        capacity = total / cap_s
-        # Poisson arrivals at 0.8 x capacity
-        mean_gap = (total / len(reqs)) / (0.8 * capacity)
-        gaps = rng.exponential(mean_gap, size=len(reqs))
-        srv = mea.Server(mem_budget_bytes=160 << 30, n_slots=4, chunk_events=1 << 12)
-        t0 = time.perf_counter()
-        ids = []
-        tnext = t0
-        for (nm, m, n), o, g in zip(reqs, outs, gaps):
-            tnext += g
-            while time.perf_counter() < tnext:
-                time.sleep(min(0.001, max(0.0, tnext - time.perf_counter())))
-            ids.append(srv.submit(procs[nm], m, o, precision=prec))
-        for i in ids:
-            srv.wait(i, timeout_ms=600000)
-        wall = time.perf_counter() - t0
-        st = srv.stats()
-        srv.close()
-        results[pname] = {"capacity_events_per_s": capacity, "offered_load": 0.8, "events_per_s": total / wall,
-                          "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
-                          "requests": len(reqs), "events": total}
-    out = {"metric": METRIC, "value": results["mixed"]["events_per_s"], "unit": "events/s", "n_gpus": 1,
-           "steps": n_req, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32 amplitudes + tcgen05 f16-split colour sum; f64 re-evaluation",
-           "data": "synthetic",
-           "config": {"workload": "serving: Poisson arrivals at 0.8 x capacity, sizes log-uniform "
-                                  f"[{int(lo_n)}, {int(hi_n)}], mix 40/40/20 gg>ggggg/uu~>ggggg/uu>uuggg",
-                      "scale": args.scale, "slots": 4, "chunk_events": 4096},
-           "p50_ms": results["mixed"]["p50_ms"], "p99_ms": results["mixed"]["p99_ms"],
-           "mixed": results["mixed"], "fp64": results["fp64"]}
-    print(json.dumps(out), flush=True)
+        ref = P.me2(mom)
+        dt = time.perf_counter() - t0
+        tot_ev += n
+        tot_t += dt
+        parts.append(f"{name}: {n} events in {dt:.1f} s")
+        d = torch.from_numpy(mom).cuda()
+        o = torch.empty(n, dtype=torch.float64, device="cuda")
+        procs[name].evaluate(d, o, precision=mea.PREC_FP64)
+        o2 = torch.empty(n, dtype=torch.float64, device="cuda")
+        procs[name].evaluate(d, o2, precision=mea.PREC_MIXED)
+        torch.cuda.synchronize()
+        r64 = np.abs(o.cpu().numpy() / ref - 1.0)
+        r32 = np.abs(o2.cpu().numpy() / ref - 1.0)
+        errs[name] = {"events": n, "fp64_max_rel_err": float(r64.max()),
+                      "mixed_median_rel_err": float(np.median(r32)), "mixed_max_rel_err": float(r32.max())}
+    return ({"value": tot_ev / tot_t, "unit": "events/s", "cores": cores, "kind": "oracle",
+             "sample": "; ".join(parts) + " (host generator, sqrt(s) in [500 GeV, 5 TeV])"}, errs)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3jet", choices=sorted(WORKLOADS) + ["batch", "serve"])
-    ap.add_argument("--scale", type=float, default=1.0,
-                    help="batch/serve: multiply the configured event counts (bounded runs)")
-    ap.add_argument("--ref-events", type=int, default=4096)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--no-sampled", action="store_true",
-                    help="skip the sampled-helicity (one helicity per event) throughput")
-    args = ap.parse_args()
-
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    if args.workload == "batch":
-        run_batch(args)
-        return
-    if args.workload == "serve":
-        run_serve(args)
-        return
-
+# ---- device-resident workloads ---------------------------------------------------
+def device_workload(name, steps, warmup, rank=0, ws=1, dist=None, autotune=True, sampled=True):
+    """Evaluate every subprocess of a device-resident workload `steps` times
+    (after `warmup`), mixed and FP64; per-subprocess rates, errors, the
+    timing of each evaluation (CUDA events on the launching stream)."""
     import torch
     from paper_0909_5257_gb300 import mea
-
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        return max_over_ranks_value(x, dist, "cuda")
-
-    subs, n, seed_off = WORKLOADS[args.workload]
+    subs, n, seed_off = WORKLOADS[name]
     stream = torch.cuda.current_stream()
     procs, moms, outs, flags = [], [], [], []
-    for name, pdg, nf, lo, hi in subs:
+    for sname, pdg, nf, lo, hi in subs:
         P = mea.Process(pdg)
         m = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
-        # weak scaling: every rank evaluates its own slice of the event stream
         mea.generate_phase_space(nf, n, m, first_event=shard_first_event(rank, n), seed=SEED_BASE + seed_off,
                                  rs_lo=lo, rs_hi=hi)
         procs.append(P)
@@ -429,16 +366,12 @@ def main():
         outs.append(torch.empty(n, dtype=torch.float64, device="cuda"))
         flags.append(torch.empty(n, dtype=torch.uint8, device="cuda"))
     torch.cuda.synchronize()
-    # one-time tile / register-variant / body choice per subprocess and
-    # precision, outside the timed region: the straight-line kernels are tuned
-    # on the full launch (their spill footprint competes with the streamed
-    # inputs for L2 only at that size), the others on a 2^16-event sample
     tuned = {}
-    if not args.no_autotune:
-        for (name, *_), P, m, o in zip(subs, procs, moms, outs):
+    if autotune:
+        for (sname, *_), P, m, o in zip(subs, procs, moms, outs):
             k = n if P.n_ext <= 5 else min(n, 1 << 16)
-            tuned[name] = {pn: P.autotune(m[:k], o[:k], precision=pr)
-                           for pr, pn in ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64"))}
+            tuned[sname] = {pn: P.autotune(m[:k], o[:k], precision=pr)
+                            for pr, pn in ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64"))}
         torch.cuda.synchronize()
 
     def step(prec, ev_pairs=None):
@@ -449,62 +382,43 @@ def main():
             if ev_pairs is not None:
                 ev_pairs[i][1].record(stream)
 
-    def timed(prec, steps):
-        for _ in range(args.warmup):
+    def timed(prec, k):
+        for _ in range(warmup):
             step(prec)
         barrier()
-        per = [[] for _ in procs]
         pairs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in procs] for _ in range(steps)]
+                  for _ in procs] for _ in range(k)]
         l0 = mea.kernel_launch_count()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        for s in range(steps):
+        for s in range(k):
             step(prec, pairs[s])
         t1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        launches = mea.kernel_launch_count() - l0
-        ms = t0.elapsed_time(t1)
-        for s in range(steps):
-            for i in range(len(procs)):
-                per[i].append(pairs[s][i][0].elapsed_time(pairs[s][i][1]))
-        return max_over_ranks(ms) / steps, per, launches
+        per = [[pairs[s][i][0].elapsed_time(pairs[s][i][1]) for s in range(k)] for i in range(len(procs))]
+        ms = max_over_ranks_value(t0.elapsed_time(t1), dist, "cuda")
+        return ms / k, per, mea.kernel_launch_count() - l0
 
-    sampler = ClockSampler(local)
-    sampler.start()
-    ms_mixed, per_mixed, launches = timed(mea.PREC_MIXED, args.steps)
-    clocks = sampler.stop()
-    # the clones run on torch's stream: finish them before the FP64 pass
-    # overwrites the outputs on the evaluation stream
+    ms_mixed, per_mixed, launches = timed(mea.PREC_MIXED, steps)
     mixed_out = [o.clone() for o in outs]
     mixed_flags = [f.clone() for f in flags]
     torch.cuda.synchronize()
-
-    fp64 = None
-    if not args.no_fp64:
-        ms64, per64, _ = timed(mea.PREC_FP64, args.steps)
-        fp64 = {"value": ws * n * len(procs) / (ms64 * 1e-3), "unit": "events/s", "ms_per_step": ms64}
+    ms64, per64, _ = timed(mea.PREC_FP64, max(1, min(steps, 3)))
     fp64_out = [o.clone() for o in outs]
     torch.cuda.synchronize()
-
     per_sub = {}
-    for i, (name, pdg, nf, lo, hi) in enumerate(subs):
+    for i, (sname, pdg, nf, lo, hi) in enumerate(subs):
         info = procs[i].info
-        ms_i = statistics.median(per_mixed[i])
-        d = {"mixed_events_per_s": n / (ms_i * 1e-3), "diagrams": info["n_diagrams"], "colours": info["n_colour"],
-             "helicities": info["n_hel_nonzero"],
-             "flagged_fraction": float((mixed_flags[i] != 0).float().mean().item())}
-        if fp64 is not None:
-            d["fp64_events_per_s"] = n / (statistics.median(per64[i]) * 1e-3)
-            rel = (mixed_out[i] / fp64_out[i] - 1.0).abs()
-            d["mixed_vs_fp64_rel_err_median"] = float(rel.median().item())
-            d["mixed_vs_fp64_rel_err_max"] = float(rel.max().item())
-            d["mixed_vs_fp64_rel_err_p99"] = float(torch.quantile(rel.float(), 0.99).item())
-        if not args.no_sampled:
-            # the paper's mode (one helicity per event, drawn from the
-            # non-vanishing set): throughput only, for comparison with its
-            # per-event timings (one sampled helicity = 1/H of a summed event)
+        rel = (mixed_out[i] / fp64_out[i] - 1.0).abs()
+        d = {"mixed_events_per_s": n / (statistics.median(per_mixed[i]) * 1e-3),
+             "fp64_events_per_s": n / (statistics.median(per64[i]) * 1e-3),
+             "diagrams": info["n_diagrams"], "colours": info["n_colour"], "helicities": info["n_hel_nonzero"],
+             "flagged_fraction": float((mixed_flags[i] != 0).float().mean().item()),
+             "mixed_vs_fp64_rel_err_median": float(rel.median().item()),
+             "mixed_vs_fp64_rel_err_p99": float(torch.quantile(rel.float(), 0.99).item()),
+             "mixed_vs_fp64_rel_err_max": float(rel.max().item())}
+        if sampled:
             P = procs[i]
             hels = torch.from_numpy(P.helicities()).to("cuda")
             g = torch.Generator(device="cuda").manual_seed(SEED_BASE + 11 + i)
@@ -519,93 +433,539 @@ def main():
             ev1.record(stream)
             torch.cuda.synchronize()
             d["sampled_helicity_events_per_s"] = n / (ev0.elapsed_time(ev1) / 3 * 1e-3)
-        per_sub[name] = d
+        per_sub[sname] = d
+    return {"subs": subs, "n": n, "procs": procs, "moms": moms, "per_sub": per_sub, "tuned": tuned,
+            "ms_mixed": ms_mixed, "ms_fp64": ms64, "per_mixed": per_mixed, "launches": launches}
 
-    # roofline of the dominant kernel: the fused amplitude + colour kernel of the
-    # most expensive subprocess, FP32 pipe (ALU-bound), algorithmic FLOPs per launch
-    # FLOPs of the straight-line body the tuner chose: with the shared vertex
-    # partials, or one vertex call per diagram (flops_per_hel_plain)
-    def body_flops(i):
-        name = subs[i][0]
-        plain = name in tuned and not tuned[name]["mixed"].get("vertex_partials", 1)
-        return procs[i].info["flops_per_hel_plain" if plain else "flops_per_hel"]
-    cost = [procs[i].info["n_hel_nonzero"] * (body_flops(i) + procs[i].info["colour_flops_per_hel"])
-            for i in range(len(procs))]
-    dom = int(np.argmax([c * statistics.median(per_mixed[i]) for i, c in enumerate(cost)]))
-    ms_dom = statistics.mean(per_mixed[dom])
-    flops_launch = n * cost[dom]
-    achieved = flops_launch / (ms_dom * 1e-3) / 1e12
+
+BATCH_SPEC = [  # (name, pdg, n_final, sqrt(s) range, configured events)
+    ("gg>ggg", [21, 21, 21, 21, 21], 3, 200.0, 2000.0, 1 << 18),
+    ("uu~>gggg", [2, -2, 21, 21, 21, 21], 4, 300.0, 3000.0, 1 << 20),
+    ("uu>uuggg", [2, 2, 2, 2, 21, 21, 21], 5, 300.0, 3000.0, 1 << 19),
+    ("gg>gggg", [21] * 6, 4, 300.0, 3000.0, 1 << 17),
+]
+
+
+def batch_workload(steps, warmup, scale=1.0):
+    """Batched mixed launch: four subprocesses of very uneven cost, counts
+    perturbed by a seeded draw, autotuned per process, evaluated by one
+    CUDA-graph launch per step (mea_batch_*); mixed vs FP64 graph."""
+    import torch
+    from paper_0909_5257_gb300 import mea
+    rng = np.random.default_rng(SEED_BASE + 3)
+    procs, moms, n_ev = [], [], []
+    for name, pdg, nf, lo, hi, n in BATCH_SPEC:
+        n = max(64, int(n * scale * rng.uniform(0.75, 1.25)))
+        P = mea.Process(pdg)
+        m = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
+        mea.generate_phase_space(nf, n, m, seed=SEED_BASE + 3, rs_lo=lo, rs_hi=hi)
+        procs.append(P)
+        moms.append(m)
+        n_ev.append(n)
+    tune = {}
+    for (name, *_), P, m in zip(BATCH_SPEC, procs, moms):
+        k = min(m.shape[0], 1 << 14)
+        scratch = torch.empty(k, dtype=torch.float64, device="cuda")
+        tune[name] = P.autotune(m[:k], scratch, precision=mea.PREC_MIXED)
+    res = {}
+    for prec, pname in ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64")):
+        outs = [torch.empty(n, dtype=torch.float64, device="cuda") for n in n_ev]
+        flags = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in n_ev]
+        B = mea.Batch(list(zip(procs, moms, outs, flags)), precision=prec)
+        k = steps if pname == "mixed" else max(1, min(steps, 2))
+        for _ in range(max(1, warmup if pname == "mixed" else 1)):
+            B.launch()
+        torch.cuda.synchronize()
+        l0 = mea.kernel_launch_count()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(k):
+            B.launch()
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / k
+        res[pname] = {"events_per_s": sum(n_ev) / (ms * 1e-3), "ms_per_launch": ms, "steps": k,
+                      "graph_kernel_nodes": B.kernel_nodes, "kernels_launched": mea.kernel_launch_count() - l0}
+        res[pname + "_out"] = [o.clone() for o in outs]
+        B.close()
+    errs = {}
+    for i, (name, *_) in enumerate(BATCH_SPEC):
+        rel = (res["mixed_out"][i] / res["fp64_out"][i] - 1.0).abs()
+        errs[name] = {"events": n_ev[i], "mixed_vs_fp64_rel_err_median": float(rel.median()),
+                      "mixed_vs_fp64_rel_err_max": float(rel.max()),
+                      "autotune": {k: tune[name][k] for k in ("threads", "events_per_cta", "register_cap")}}
+    return {"workload": "batched mixed launch (one CUDA graph): " +
+                        ", ".join(f"{b[0]} {n}" for b, n in zip(BATCH_SPEC, n_ev)),
+            "mixed": res["mixed"], "fp64": res["fp64"], "per_subprocess": errs}
+
+
+# ---- serving headline ---------------------------------------------------------------
+def _stage_flops(info, H):
+    """Algorithmic work per (event, helicity) pair of each stage of the
+    tensor-core path: FP32 FLOPs of the amplitude program without the
+    colour-amplitude accumulation (done by the tensor cores there), the
+    useful tensor FLOPs of the colour amplitudes (2 FLOP per non-zero
+    coefficient for each of Re, Im) and of the colour sum (4 m^2)."""
+    nnz = info["n_colour_entries"]
+    m = info["n_colour_amplitudes"]
+    return {"amplitudes": info["flops_per_hel"] - 4.0 * nnz, "colour_amplitudes": 4.0 * nnz,
+            "colour_sum": 4.0 * m * m}
+
+
+def _cdiv(a, b):
+    return -(-a // b)
+
+
+def _jamp_executed_flops(info):
+    """Tensor FLOPs the colour-amplitude GEMM executes per (event, helicity)
+    pair: Re and Im rows x 2 FLOP x padded diagrams x padded colour columns
+    x 3 digit planes (tiles of 64 diagrams, column splits of at most 128)."""
+    m, kd = info["n_colour_amplitudes"], info["n_diagrams"]
+    nc = min(128, _cdiv(m, 16) * 16)
+    splits = _cdiv(m, nc)
+    nc = min(nc, _cdiv(_cdiv(m, splits), 16) * 16)
+    return 2 * 2 * (_cdiv(kd, 64) * 64) * (splits * nc) * 3
+
+
+def _colour_sum_executed_flops(info):
+    """Tensor FLOPs the colour-sum GEMM executes per pair: 2 rows x 2 FLOP x
+    padded K x padded N x MMAs per K step (3 for the 3-way split of J when the
+    integer colour matrix is exact in FP16, else 5)."""
+    m = info["n_colour_amplitudes"]
+    nb = _cdiv(m, 256)
+    nc = _cdiv(_cdiv(m, nb), 32) * 32
+    n_mma = 3 if info["cf_max_abs_numerator"] <= 2048 else 5
+    return 2 * 2 * (_cdiv(m, 64) * 64) * (nb * nc) * n_mma
+
+
+def run_serve(args):
+    import torch
+    from paper_0909_5257_gb300 import mea
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    names = [s[0] for s in SERVE_MIX]
+    procs = {name: mea.Process(pdg) for name, pdg, _, _ in SERVE_MIX}
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
-    peak = n_sms * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
-    # DRAM bytes per event of each kernel from one ncu capture of the current
-    # kernels (dram__bytes_read.sum + dram__bytes_write.sum of one 2^20-event
-    # launch, divided by the events), scaled to this launch's events.  Mostly
-    # spill write-back for gg>ggg.
-    traffic_per_event = TRAFFIC_BYTES_PER_EVENT.get(subs[dom][0])
-    traffic = None if traffic_per_event is None else traffic_per_event * n
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic,
-                "kernel": (f"gen_kernel<float> straight-line body ({subs[dom][0]})" if len(subs[dom][1]) <= 5
-                           else f"amp_kernel<float> + jamp/colour GEMMs ({subs[dom][0]})") +
-                          ", per-launch CUDA events incl. the FP64 re-evaluation launch",
-                "peak_note": f"derived: {n_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x {MAX_SM_MHZ:.0f} MHz"}
 
-    # end to end through the host-buffer entry point
-    e2e = None
-    if rank == 0 or ws > 1:
-        # inputs and results in pinned host memory: the library's copy engines
-        # read and write them directly (pageable arrays would be staged)
-        host = [m.cpu().pin_memory().numpy() for m in moms]
-        outs = [torch.empty(h.shape[0], dtype=torch.float64).pin_memory().numpy() for h in host]
-        fls = [torch.empty(h.shape[0], dtype=torch.uint8).pin_memory().numpy() for h in host]
-        for P, h, o, f in zip(procs, host, outs, fls):  # warm-up at full size
-            P.evaluate_host(h, precision=mea.PREC_MIXED, out=o, flags=f)
-        barrier()
-        t0 = time.perf_counter()
-        e2e_steps = max(1, min(args.steps, 3))
-        for _ in range(e2e_steps):
-            for P, h, o, f in zip(procs, host, outs, fls):
-                P.evaluate_host(h, precision=mea.PREC_MIXED, out=o, flags=f)
-        dt = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": ws * n * len(procs) * e2e_steps / dt, "unit": "events/s",
-               "h2d_bytes_per_step": int(sum(h.nbytes for h in host)),
-               "d2h_bytes_per_step": int(sum(h.shape[0] * 9 for h in host)), "steps": e2e_steps}
+    # measured ALU peaks of this GPU (FMA chains), with the SM clock they ran at
+    sampler = ClockSampler(local)
+    sampler.start()
+    fp32_peak, _ = mea.measure_alu_peak(False, 0.3)
+    fp64_peak, _ = mea.measure_alu_peak(True, 0.3)
+    peak_clocks = sampler.stop()
+
+    # ---- per subprocess: device-timed mixed (stage timing) and FP64 on the same inputs
+    per_sub, stage_ms_ev, tune = {}, {}, {}
+    reps = max(1, min(args.steps, 3))
+    for i, (name, pdg, nf, _) in enumerate(SERVE_MIX):
+        P = procs[name]
+        n = SUB_EVENTS[name]
+        mom = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
+        mea.generate_phase_space(nf, n, mom, first_event=shard_first_event(rank, n), seed=SEED_BASE + 14,
+                                 rs_lo=SERVE_RS[0], rs_hi=SERVE_RS[1])
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+        k = min(n, 1 << 16)
+        tune[name] = P.autotune(mom[:k], out[:k], precision=mea.PREC_MIXED)
+        P.evaluate(mom, out, precision=mea.PREC_MIXED, flags=fl, stream=stream)
+        torch.cuda.synchronize()
+        P.set_stage_timing(True)
+        P.stage_times()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            P.evaluate(mom, out, precision=mea.PREC_MIXED, flags=fl, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = P.stage_times()
+        P.set_stage_timing(False)
+        ms = e0.elapsed_time(e1) / reps
+        stage_ms_ev[name] = {k2: (v[0] / reps / n, v[1] / reps) for k2, v in st.items() if v[1] > 0}
+        n64 = FP64_EVENTS[name]
+        o64 = torch.empty(n64, dtype=torch.float64, device="cuda")
+        P.evaluate(mom[:64], o64[:64], precision=mea.PREC_FP64, stream=stream)
+        e0.record(stream)
+        P.evaluate(mom[:n64], o64, precision=mea.PREC_FP64, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        rel = (out[:n64] / o64 - 1.0).abs()
+        info = P.info
+        per_sub[name] = {
+            "mixed_events_per_s": n / (ms * 1e-3), "mixed_events": n,
+            "fp64_events_per_s": n64 / (ms64 * 1e-3), "fp64_events": n64,
+            "mixed_vs_fp64_rel_err_median": float(rel.median()), "mixed_vs_fp64_rel_err_p99":
+                float(torch.quantile(rel.float(), 0.99)), "mixed_vs_fp64_rel_err_max": float(rel.max()),
+            "flagged_fraction": float((fl != 0).float().mean()),
+            "diagrams": info["n_diagrams"], "colours": info["n_colour"], "helicities": info["n_hel_nonzero"],
+            "stage_ms_per_event": {k2: v[0] for k2, v in stage_ms_ev[name].items()},
+        }
+        del mom, out, fl, o64
+        torch.cuda.empty_cache()
+
+    # ---- the dominant kernel: largest share of the mix's device time per event
+    mix_w = {name: w for name, _, _, w in SERVE_MIX}
+    share = {(nm, stg): mix_w[nm] * v[0] for nm in names for stg, v in stage_ms_ev[nm].items()}
+    dom_nm, dom_stage = max(share, key=share.get)
+    tot_share = sum(share.values())
+    info = procs[dom_nm].info
+    H = info["n_hel_nonzero"]
+    fl_stage = _stage_flops(info, H)
+    peaks, peak_src = _peaks()
+    bf16_sus = peaks.get("bf16_tflops_sustained", 1700.0)
+    ms_per_launch = stage_ms_ev[dom_nm][dom_stage][0] * SUB_EVENTS[dom_nm] / max(
+        stage_ms_ev[dom_nm][dom_stage][1], 1)
+    events_per_launch = SUB_EVENTS[dom_nm] / max(stage_ms_ev[dom_nm][dom_stage][1], 1)
+    if dom_stage == "amplitudes":
+        flop = events_per_launch * H * fl_stage["amplitudes"]
+        achieved = flop / (ms_per_launch * 1e-3) / 1e12
+        tpe = TRAFFIC_BYTES_PER_EVENT.get((dom_nm, dom_stage))
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak, "traffic": None if tpe is None else tpe * events_per_launch,
+                    "kernel": f"amp_kernel<float> amplitude output ({dom_nm}), {events_per_launch:.0f} events "
+                              "per launch, CUDA events per launch on its stream",
+                    "peak_note": "measured on this GPU: FMA-chain kernel (mea_measure_alu_peak), "
+                                 f"SM clock median {peak_clocks.get('sm_mhz')} MHz",
+                    "share_of_mix_device_time": share[(dom_nm, dom_stage)] / tot_share}
+    else:
+        flop = events_per_launch * H * fl_stage.get(dom_stage, 0.0)
+        achieved = flop / (ms_per_launch * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": bf16_sus, "unit": "TFLOP/s",
+                    "frac": achieved / bf16_sus, "traffic": None,
+                    "kernel": f"{dom_stage} ({dom_nm})", "peak_note": f"bf16 sustained, {peak_src}",
+                    "share_of_mix_device_time": share[(dom_nm, dom_stage)] / tot_share}
+    # tensor-core stages of every subprocess: useful (algorithmic) and executed rates
+    tensor = {}
+    for nm in names:
+        inf = procs[nm].info
+        h = inf["n_hel_nonzero"]
+        f = _stage_flops(inf, h)
+        for stg, exec_flop in (("colour_amplitudes", _jamp_executed_flops(inf)),
+                               ("colour_sum", _colour_sum_executed_flops(inf))):
+            if stg in stage_ms_ev[nm]:
+                sec = stage_ms_ev[nm][stg][0] * 1e-3  # per event
+                useful = h * f[stg] / sec / 1e12
+                executed = h * exec_flop / sec / 1e12
+                tensor[f"{nm} {stg}"] = {"useful_tflops": useful, "executed_tflops": executed,
+                                         "useful_frac": useful / bf16_sus, "executed_frac": executed / bf16_sus}
+
+    # ---- serving: capacity (timed steps), latency under Poisson load, e2e
+    n_req = args.steps * REQS_PER_STEP
+    reqs = serve_requests(rank, n_req)
+    warm = serve_requests(rank + 7, max(1, args.warmup) * REQS_PER_STEP)  # a different slice for warm-up
+    datas = []
+    for kind, n, first in reqs + warm:
+        name, pdg, nf, _ = SERVE_MIX[kind]
+        m = torch.empty((n, nf + 2, 4), dtype=torch.float64, device="cuda")
+        mea.generate_phase_space(nf, n, m, first_event=first, seed=SEED_BASE + 4 + kind,
+                                 rs_lo=SERVE_RS[0], rs_hi=SERVE_RS[1])
+        datas.append((name, m, n))
+    torch.cuda.synchronize()
+    timed_reqs, warm_reqs = datas[:n_req], datas[n_req:]
+    outs = [torch.empty(n, dtype=torch.float64, device="cuda") for _, _, n in timed_reqs]
+    flags = [torch.empty(n, dtype=torch.uint8, device="cuda") for _, _, n in timed_reqs]
+    total = sum(n for _, _, n in timed_reqs)
+    budget = 200 << 30
+
+    def serve_all(srv, items, gaps=None, out_list=None, flag_list=None):
+        ids = []
+        t_next = time.perf_counter()
+        for j, (nm, m, n) in enumerate(items):
+            if gaps is not None:
+                t_next += gaps[j]
+                while time.perf_counter() < t_next:
+                    time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
+            o = out_list[j] if out_list is not None else torch.empty(n, dtype=torch.float64, device="cuda")
+            f = flag_list[j] if flag_list is not None else None
+            ids.append(srv.submit(procs[nm], m, o, flags=f, precision=mea.PREC_MIXED))
+        return [srv.wait(i, timeout_ms=900000) for i in ids]
+
+    srv = mea.Server(mem_budget_bytes=budget, n_slots=SERVE_SLOTS, chunk_events=SERVE_CHUNK)
+    serve_all(srv, warm_reqs)  # warm-up steps: scratch sized, modules loaded
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = mea.kernel_launch_count()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    t0 = time.perf_counter()
+    serve_all(srv, timed_reqs, out_list=outs, flag_list=flags)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier()
+    clocks = sampler.stop()
+    launches = mea.kernel_launch_count() - l0
+    dev_ms = max_over_ranks_value(c0.elapsed_time(c1), dist, "cuda")
+    srv_stats = srv.stats()
+    srv.close()
+    capacity = ws * total / (dev_ms * 1e-3)
+    flagged = float(sum(int((f != 0).sum()) for f in flags)) / total
+
+    # latency under Poisson arrivals at SERVE_LOAD x capacity (this rank's share)
+    rng = np.random.default_rng(SEED_BASE + 5 + rank)
+    mean_gap = (total / len(timed_reqs)) / (SERVE_LOAD * capacity / ws)
+    gaps = rng.exponential(mean_gap, size=len(timed_reqs))
+    srv = mea.Server(mem_budget_bytes=budget, n_slots=SERVE_SLOTS, chunk_events=SERVE_CHUNK)
+    serve_all(srv, warm_reqs[:1])
+    t0 = time.perf_counter()
+    lat = serve_all(srv, timed_reqs, gaps=gaps, out_list=outs)
+    load_wall = time.perf_counter() - t0
+    srv.close()
+    lat_sorted = sorted(lat)
+
+    def q(f):
+        return lat_sorted[min(len(lat_sorted) - 1, int(round(f * (len(lat_sorted) - 1))))]
+
+    by_proc = {}
+    for (nm, _, n), l in zip(timed_reqs, lat):
+        by_proc.setdefault(nm, []).append(l)
+
+    # e2e: momenta from pinned host memory, results back to pinned host memory
+    host = [m.cpu().pin_memory() for _, m, _ in timed_reqs]
+    host_out = [torch.empty(n, dtype=torch.float64).pin_memory() for _, _, n in timed_reqs]
+    dev_in = [torch.empty_like(m) for _, m, _ in timed_reqs]
+    copy_stream = torch.cuda.Stream()
+    srv = mea.Server(mem_budget_bytes=budget, n_slots=SERVE_SLOTS, chunk_events=SERVE_CHUNK)
+    serve_all(srv, warm_reqs[:1])
+    barrier()
+    t0 = time.perf_counter()
+    ids = []
+    for j, (nm, _, n) in enumerate(timed_reqs):
+        with torch.cuda.stream(copy_stream):
+            dev_in[j].copy_(host[j], non_blocking=True)
+        copy_stream.synchronize()
+        ids.append(srv.submit(procs[nm], dev_in[j], outs[j], precision=mea.PREC_MIXED))
+    for j, i in enumerate(ids):
+        srv.wait(i, timeout_ms=900000)
+        with torch.cuda.stream(copy_stream):
+            host_out[j].copy_(outs[j], non_blocking=True)
+    copy_stream.synchronize()
+    e2e_wall = max_over_ranks_value(time.perf_counter() - t0, dist, "cuda")
+    srv.close()
+    e2e = {"value": ws * total / e2e_wall, "unit": "events/s",
+           "h2d_bytes_per_step": int(sum(h.numel() * 8 for h in host) / args.steps),
+           "d2h_bytes_per_step": int(sum(n * 8 for _, _, n in timed_reqs) / args.steps),
+           "how": "per request: pinned host momenta -> device (copy stream), mea_server_submit; |M|^2 "
+                  "device -> pinned host after completion; wall clock over all requests"}
+    del host, host_out, dev_in
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    peaks, peak_src = _peaks()
+
+    # FP64 serving capacity of the same mix, from the per-subprocess FP64 rates
+    fp64_cap = 1.0 / sum(mix_w[nm] / per_sub[nm]["fp64_events_per_s"] for nm in names)
+    mixed_cap_dev = 1.0 / sum(mix_w[nm] / per_sub[nm]["mixed_events_per_s"] for nm in names)
     out = {
-        "metric": METRIC,
-        "value": ws * n * len(procs) / (ms_mixed * 1e-3),
-        "unit": "events/s",
-        "n_gpus": ws,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": ms_mixed,
-        "higher_is_better": True,
-        "scaling": "weak",
+        "metric": METRIC, "value": capacity, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 amplitudes (two-sum colour amplitudes) + f64 prep/re-evaluation",
+        "dtype": "f32 amplitudes + tcgen05 f16-digit colour stages (f32 accumulate); f64 prep/re-evaluation",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "events_per_subprocess_per_gpu": n,
-                   "l2": "inputs larger than L2 (no flush)", "alpha_s": 0.118,
-                   "autotuned": {k: {pn: {kk: v[pn][kk] for kk in ("threads", "events_per_cta", "register_cap", "vertex_partials")}
-                                     for pn in v} for k, v in tuned.items()}},
+        "config": {"workload": serve_workload_text(), "requests_per_step": REQS_PER_STEP,
+                   "requests": len(timed_reqs), "events": int(total), "server_slots": SERVE_SLOTS,
+                   "server_chunk_events": SERVE_CHUNK, "alpha_s": 0.118,
+                   "l2": "inputs larger than L2 (no flush)",
+                   "timed_region": "all K x requests_per_step requests submitted at once; CUDA events on the "
+                                   "submitting stream around submission and observed completion"},
+        "p50_ms": q(0.50), "p99_ms": q(0.99),
+        "serving": {"capacity_events_per_s": capacity, "host_wall_s": wall, "device_ms": dev_ms,
+                    "flagged_fraction": flagged, "server_busy_s": srv_stats["busy_seconds"],
+                    "latency": {"offered_load": SERVE_LOAD, "arrivals": "Poisson", "p50_ms": q(0.50),
+                                "p99_ms": q(0.99), "max_ms": lat_sorted[-1], "wall_s": load_wall,
+                                "served_events_per_s": total / load_wall,
+                                "p50_ms_by_subprocess": {k: float(np.median(v)) for k, v in by_proc.items()}},
+                    "mixed_capacity_from_device_rates": mixed_cap_dev,
+                    "fp64_capacity_from_device_rates": fp64_cap},
         "per_subprocess": per_sub,
-        "fp64": fp64,
+        "fp64": {"value": fp64_cap, "unit": "events/s",
+                 "note": "mix-weighted from the per-subprocess FP64 device rates (FP64 serving of full-size "
+                         "requests would take minutes)"},
         "roofline": roofline,
+        "tensor_stages": tensor,
+        "alu_peaks": {"fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak, "clocks": peak_clocks,
+                      "how": "mea_measure_alu_peak: FMA chains, 8 per thread, 4 x 512 threads per SM, CUDA events"},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
         "peaks_source": peak_src,
+        "autotuned": {k: {kk: v[kk] for kk in ("threads", "events_per_cta", "grid", "slots_in_shared")}
+                      for k, v in tune.items()},
     }
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(subs, seed_off)
+        out["cpu_baseline"], out["fp64_vs_oracle"] = serve_cpu_baseline(procs)
+    if not args.no_extra:
+        extra = {}
+        for wl in ("3jet", "4jet"):
+            r = device_workload(wl, 3, 2, sampled=(wl == "3jet"))
+            extra[wl] = {"workload": WORKLOAD_TEXT[wl],
+                         "mixed_events_per_s": len(r["subs"]) * r["n"] / (r["ms_mixed"] * 1e-3),
+                         "fp64_events_per_s": len(r["subs"]) * r["n"] / (r["ms_fp64"] * 1e-3),
+                         "per_subprocess": r["per_sub"]}
+            del r
+            torch.cuda.empty_cache()
+        extra["batch"] = batch_workload(3, 2)
+        out["other_workloads"] = extra
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_device(args):
+    """A device-resident workload (3jet, 4jet, 2jet) as the headline line."""
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_0909_5257_gb300 import mea
+    sampler = ClockSampler(local)
+    sampler.start()
+    r = device_workload(args.workload, args.steps, args.warmup, rank, ws, dist, autotune=not args.no_autotune,
+                        sampled=not args.no_sampled)
+    clocks = sampler.stop()
+    subs, n, procs = r["subs"], r["n"], r["procs"]
+    # roofline of the dominant kernel: the fused straight-line kernel (or the
+    # amplitude kernel) of the most expensive subprocess, FP32 pipe
+    fp32_peak, _ = mea.measure_alu_peak(False, 0.3)
+
+    def body_flops(i):
+        name = subs[i][0]
+        plain = name in r["tuned"] and not r["tuned"][name]["mixed"].get("vertex_partials", 1)
+        return procs[i].info["flops_per_hel_plain" if plain else "flops_per_hel"]
+    cost = [procs[i].info["n_hel_nonzero"] * (body_flops(i) + procs[i].info["colour_flops_per_hel"])
+            for i in range(len(procs))]
+    per = r["per_mixed"]
+    dom = int(np.argmax([c * statistics.median(per[i]) for i, c in enumerate(cost)]))
+    achieved = n * cost[dom] / (statistics.mean(per[dom]) * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": f"straight-line / amplitude kernel of {subs[dom][0]}, per-launch CUDA events",
+                "peak_note": "measured FMA-chain kernel (mea_measure_alu_peak)"}
+    e2e = None
+    if rank == 0:
+        host = [m.cpu().pin_memory().numpy() for m in r["moms"]]
+        outs = [torch.empty(h.shape[0], dtype=torch.float64).pin_memory().numpy() for h in host]
+        fls = [torch.empty(h.shape[0], dtype=torch.uint8).pin_memory().numpy() for h in host]
+        for P, h, o, f in zip(procs, host, outs, fls):
+            P.evaluate_host(h, precision=mea.PREC_MIXED, out=o, flags=f)
+        t0 = time.perf_counter()
+        k = max(1, min(args.steps, 3))
+        for _ in range(k):
+            for P, h, o, f in zip(procs, host, outs, fls):
+                P.evaluate_host(h, precision=mea.PREC_MIXED, out=o, flags=f)
+        dt = time.perf_counter() - t0
+        e2e = {"value": n * len(procs) * k / dt, "unit": "events/s",
+               "h2d_bytes_per_step": int(sum(h.nbytes for h in host)),
+               "d2h_bytes_per_step": int(sum(h.shape[0] * 9 for h in host)), "steps": k}
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = _peaks()
+    out = {"metric": METRIC, "value": ws * n * len(procs) / (r["ms_mixed"] * 1e-3), "unit": "events/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_mixed"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 amplitudes + f64 prep/re-evaluation", "data": "synthetic",
+           "config": {"workload": WORKLOAD_TEXT[args.workload], "events_per_subprocess_per_gpu": n,
+                      "l2": "inputs larger than L2 (no flush)", "alpha_s": 0.118},
+           "per_subprocess": r["per_sub"],
+           "fp64": {"value": ws * n * len(procs) / (r["ms_fp64"] * 1e-3), "unit": "events/s"},
+           "roofline": roofline, "e2e": e2e, "gpu_launches": r["launches"], "clocks": clocks,
+           "peaks_source": peak_src}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(subs, WORKLOADS[args.workload][2])
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_single(args):
+    """One subprocess, --events events generated on the device, evaluated once
+    (tuning on first use from 2^16 events), then again inside an NVTX range
+    "eval" (the range a profiler restricts itself to); prints timing."""
+    import torch
+    from paper_0909_5257_gb300 import mea
+    pdg, lo, hi = SINGLE[args.process]
+    torch.cuda.set_device(0)
+    prec = mea.PREC_FP64 if args.precision == "fp64" else mea.PREC_MIXED
+    P = mea.Process(pdg)
+    n = args.events
+    mom = torch.empty((n, len(pdg), 4), dtype=torch.float64, device="cuda")
+    mea.generate_phase_space(len(pdg) - 2, n, mom, rs_lo=lo, rs_hi=hi)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    P.evaluate(mom, out, precision=prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("eval")
+    e0.record()
+    P.evaluate(mom, out, precision=prec)
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    P.check_status()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"process": args.process, "events": n, "precision": args.precision, "ms": ms,
+                      "events_per_s": n / (ms * 1e-3), "mean_me2": float(out.mean())}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="serve", choices=["serve", "batch", "single"] + sorted(WORKLOADS))
+    ap.add_argument("--process", default="gg5g", choices=sorted(SINGLE), help="single: the subprocess")
+    ap.add_argument("--events", type=int, default=4096, help="single: events")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="single: precision")
+    ap.add_argument("--scale", type=float, default=1.0, help="batch: multiply the configured event counts")
+    ap.add_argument("--ref-events", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="serve: skip the other workloads' extra keys")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-sampled", action="store_true",
+                    help="skip the sampled-helicity (one helicity per event) throughput")
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        if args.workload in ("batch", "single"):
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers serve/2jet/3jet/4jet"}))
+            return
+        run_reference(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
+    elif args.workload == "single":
+        run_single(args)
+    elif args.workload == "batch":
+        import torch
+        torch.cuda.set_device(0)
+        r = batch_workload(args.steps, args.warmup, args.scale)
+        out = {"metric": METRIC, "value": r["mixed"]["events_per_s"], "unit": "events/s", "n_gpus": 1,
+               "steps": r["mixed"]["steps"], "warmup": args.warmup, "ms_per_step": r["mixed"]["ms_per_launch"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32 amplitudes + tcgen05 f16-digit colour stages; f64 re-evaluation", "data": "synthetic",
+               "config": {"workload": r["workload"], "scale": args.scale}, "mixed": r["mixed"], "fp64": r["fp64"],
+               "per_subprocess": r["per_subprocess"], "gpu_launches": r["mixed"]["kernels_launched"]}
+        print(json.dumps(out), flush=True)
+    else:
+        run_device(args)
 
 
 if __name__ == "__main__":
