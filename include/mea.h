@@ -83,7 +83,13 @@ typedef enum {
 typedef struct {
   double alpha_s;        /* strong coupling, g = sqrt(4 pi alpha_s); <= 0 -> 0.118 */
   double flag_threshold; /* relative error indicator above which an event is
-                            flagged in MEA_PREC_MIXED; <= 0 -> 1e-5 */
+                            flagged in MEA_PREC_MIXED; <= 0 -> 1e-5.  The
+                            indicator is u (32 + kappa), u = 2^-24 the FP32
+                            roundoff and kappa the cancellation sum |c A| /
+                            sum |J| of the colour-amplitude sum averaged over
+                            the helicities with their |M_h|^2; it bounds the
+                            measured relative error of the mixed result for
+                            >= 99 % of the events */
   int reeval_fp64;       /* 1: re-evaluate flagged events in FP64 (default) */
   int colour_mode;       /* 0 auto, 1 CUDA-core colour sum, 2 tensor-core GEMM */
   int64_t chunk_events;  /* tensor-core path: events per chunk (bounds its device

@@ -279,15 +279,10 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
       float mx_re = 0.f, mx_im = 0.f;
       bool finite_amps = true;
 
-      for (int i = 0; i < P.n_ops; ++i) {
-        OpWords w;
-        w.v[0] = __ldg(&ops[i].v[0]);
-        w.v[1] = __ldg(&ops[i].v[1]);
-        const Op& op = w.op;
-        cx<R> amp;
-        const bool is_amp = eval_op<R>(op, P, slots, L, t, et, mt, lam_bits, g, gg, amp);
-        if (AOUT && is_amp) {
-          // hand the diagram amplitude to the tensor-core colour-amplitude stage
+      // one diagram amplitude: to the tensor-core stage (AOUT) or into the
+      // colour amplitudes through its colour entries
+      auto take_amp = [&](uint32_t col_begin, uint32_t col_count, const cx<R>& amp) {
+        if (AOUT) {
           float2* dst = reinterpret_cast<float2*>(A.amp_out + (size_t)d_amp * A.lda + 2 * pair);
           *dst = make_float2((float)amp.r, (float)amp.i);
           const float ar = fabsf((float)amp.r), ai = fabsf((float)amp.i);
@@ -296,9 +291,9 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
           mx_im = fmaxf(mx_im, ai);
           abs_mass += __ldg(P.amp_w + d_amp) * (ar + ai);
           ++d_amp;
-        } else if (is_amp) {
-          const ColEntry* ce = P.col + op.col_begin;
-          for (uint32_t k = 0; k < op.col_count; ++k) {
+        } else {
+          const ColEntry* ce = P.col + col_begin;
+          for (uint32_t k = 0; k < col_count; ++k) {
             ColEntry c = ce[k];
             R cr = (R)c.re, ci = (R)c.im;
             R xr = cr * amp.r - ci * amp.i;
@@ -319,6 +314,14 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
             }
           }
         }
+      };
+      for (int i = 0; i < P.n_ops; ++i) {
+        OpWords w;
+        w.v[0] = __ldg(&ops[i].v[0]);
+        w.v[1] = __ldg(&ops[i].v[1]);
+        cx<R> amp;
+        const bool is_amp = eval_op<R>(w.op, P, slots, L, t, et, mt, lam_bits, g, gg, amp);
+        if (is_amp) take_amp(w.op.col_begin, w.op.col_count, amp);
       }
       if (AOUT) {
         const float nan = __int_as_float(0x7fc00000);
@@ -404,7 +407,7 @@ __global__ void finish_kernel(const AmpLaunch A, int H, const double* pairval, c
   A.me2[e] = me;
   uint8_t fl = A.ev_flags ? A.ev_flags[e] : (uint8_t)0;
   if (!isfinite(me)) fl |= MEA_FLAG_NONFINITE;
-  double ind = (s > 0.0) ? 5.96e-8 * wk / s : 0.0;
+  const double ind = error_indicator(wk, s);
   if (!(ind <= (double)A.flag_threshold)) fl |= MEA_FLAG_CANCEL;
   if (A.flags) A.flags[e] = fl;
   if (A.flag_list && (fl & (MEA_FLAG_CANCEL | MEA_FLAG_NONFINITE | MEA_FLAG_QGUARD))) {
@@ -501,6 +504,32 @@ static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n
   return best;
 }
 
+// CTAs of the interpreter kernel of this placement that can be resident on
+// one SM (registers, shared memory, threads): the kernel is persistent (a
+// grid-stride loop over tiles), so a grid beyond what is resident at once
+// would leave the CTAs that start late to finish their share of the tiles
+// alone.
+static int interp_resident(bool fp64, bool jsm, bool ssm, bool aout, int threads, size_t smem) {
+  const void* k;
+  if (aout) k = ssm ? (const void*)amp_kernel<float, true, true, true> : (const void*)amp_kernel<float, true, false, true>;
+  else if (fp64)
+    k = jsm ? (ssm ? (const void*)amp_kernel<double, true, true, false> : (const void*)amp_kernel<double, true, false, false>)
+            : (ssm ? (const void*)amp_kernel<double, false, true, false> : (const void*)amp_kernel<double, false, false, false>);
+  else
+    k = jsm ? (ssm ? (const void*)amp_kernel<float, true, true, false> : (const void*)amp_kernel<float, true, false, false>)
+            : (ssm ? (const void*)amp_kernel<float, false, true, false> : (const void*)amp_kernel<float, false, false, false>);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms,
                    size_t max_smem, size_t smem_per_sm, int hint) {
   if (p.gen && hint == 0) return plan_generated(p, fp64, H, n_events, num_sms);
@@ -525,6 +554,8 @@ AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int 
       int per_sm = (int)std::min<size_t>(smem_per_sm / std::max<size_t>(sm, 1), 2048 / threads);
       per_sm = std::min(per_sm, 32);
       if (per_sm < 1) continue;
+      const int res = interp_resident(fp64, jsm, ssm, p.n_colour == 0 && !fp64, threads, sm);
+      if (res >= 1) per_sm = std::min(per_sm, res);
       double util = (double)(E * H) / threads;
       double lanes_sm = (double)per_sm * E * H;
       // enough lanes per SM to hide latency, then as few idle lanes as possible
@@ -607,6 +638,8 @@ std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, 
       int per_sm = (int)std::min<size_t>(smem_per_sm / std::max<size_t>(sm, 1), 2048 / threads);
       per_sm = std::min(per_sm, 32);
       if (per_sm < 1) continue;
+      const int res = interp_resident(fp64, pl[0] != 0, pl[1] != 0, p.n_colour == 0 && !fp64, threads, sm);
+      if (res >= 1) per_sm = std::min(per_sm, res);
       AmpConfig c;
       c.H = H; c.E_cta = E; c.threads = threads; c.smem = sm;
       c.jamp_in_smem = pl[0] != 0; c.slots_in_smem = pl[1] != 0;
