@@ -689,7 +689,12 @@ def run_serve(args):
             o = out_list[j] if out_list is not None else torch.empty(n, dtype=torch.float64, device="cuda")
             f = flag_list[j] if flag_list is not None else None
             ids.append(srv.submit(procs[nm], m, o, flags=f, precision=mea.PREC_MIXED))
-        return [srv.wait(i, timeout_ms=900000) for i in ids]
+        try:
+            return [srv.wait(i, timeout_ms=900000) for i in ids]
+        except mea.MeaError as err:
+            free, tot = torch.cuda.mem_get_info()
+            raise RuntimeError(f"serving failed ({err}); device memory free {free / 2**30:.1f} of "
+                               f"{tot / 2**30:.1f} GiB") from err
 
     srv = mea.Server(mem_budget_bytes=budget, n_slots=SERVE_SLOTS, chunk_events=SERVE_CHUNK)
     serve_all(srv, warm_reqs)  # warm-up steps: scratch sized, modules loaded
@@ -766,6 +771,10 @@ def run_serve(args):
             dist.destroy_process_group()
         return
 
+    # the capacity the per-subprocess device rates predict for these very
+    # requests (their own mix of sizes): the server's efficiency is value / this
+    expect_s = sum(n / per_sub[nm]["mixed_events_per_s"] for nm, _, n in timed_reqs)
+    expected_capacity = ws * total / expect_s
     # FP64 serving capacity of the same mix, from the per-subprocess FP64 rates
     fp64_cap = 1.0 / sum(mix_w[nm] / per_sub[nm]["fp64_events_per_s"] for nm in names)
     mixed_cap_dev = 1.0 / sum(mix_w[nm] / per_sub[nm]["mixed_events_per_s"] for nm in names)
@@ -783,6 +792,9 @@ def run_serve(args):
                                    "submitting stream around submission and observed completion"},
         "p50_ms": q(0.50), "p99_ms": q(0.99),
         "serving": {"capacity_events_per_s": capacity, "host_wall_s": wall, "device_ms": dev_ms,
+                    "capacity_from_device_rates_for_these_requests": expected_capacity,
+                    "server_efficiency": capacity / expected_capacity,
+                    "events_by_subprocess": {nm: int(sum(n for x, _, n in timed_reqs if x == nm)) for nm in names},
                     "flagged_fraction": flagged, "server_busy_s": srv_stats["busy_seconds"],
                     "latency": {"offered_load": SERVE_LOAD, "arrivals": "Poisson", "p50_ms": q(0.50),
                                 "p99_ms": q(0.99), "max_ms": lat_sorted[-1], "wall_s": load_wall,

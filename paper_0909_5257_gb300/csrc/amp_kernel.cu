@@ -29,7 +29,9 @@
 #include <cmath>
 #include <cstdint>
 #include <string>
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/mea.h"
@@ -42,6 +44,17 @@ namespace mea {
 uint64_t& launch_counter() {
   static uint64_t c = 0;
   return c;
+}
+
+cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> set;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = set.find(kernel);
+  if (it != set.end() && it->second >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) set[kernel] = bytes;
+  return e;
 }
 
 namespace {
@@ -504,12 +517,14 @@ static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n
   return best;
 }
 
-// CTAs of the interpreter kernel of this placement that can be resident on
-// one SM (registers, shared memory, threads): the kernel is persistent (a
-// grid-stride loop over tiles), so a grid beyond what is resident at once
-// would leave the CTAs that start late to finish their share of the tiles
-// alone.
-static int interp_resident(bool fp64, bool jsm, bool ssm, bool aout, int threads, size_t smem) {
+// CTAs of the interpreter kernel of this placement that registers and
+// threads allow on one SM (shared memory is limited by the caller): the
+// kernel is persistent (a grid-stride loop over tiles), so a grid beyond what
+// is resident at once would leave the CTAs that start late to finish their
+// share of the tiles alone.  Computed from the kernel's register count
+// (cudaFuncGetAttributes, read only): planning may run on any host thread
+// while another launches these kernels, so it changes no function attribute.
+static int interp_resident(bool fp64, bool jsm, bool ssm, bool aout, int threads) {
   const void* k;
   if (aout) k = ssm ? (const void*)amp_kernel<float, true, true, true> : (const void*)amp_kernel<float, true, false, true>;
   else if (fp64)
@@ -518,16 +533,15 @@ static int interp_resident(bool fp64, bool jsm, bool ssm, bool aout, int threads
   else
     k = jsm ? (ssm ? (const void*)amp_kernel<float, true, true, false> : (const void*)amp_kernel<float, true, false, false>)
             : (ssm ? (const void*)amp_kernel<float, false, true, false> : (const void*)amp_kernel<float, false, false, false>);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return n;
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = ((std::max(fa.numRegs, 1) + 7) / 8) * 8 * 32;  // allocated per warp in units of 8 per thread
+  const int by_regs = 65536 / std::max(regs_warp * warps, 1);
+  return std::max(0, std::min({by_regs, 2048 / (warps * 32), 32}));
 }
 
 AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms,
@@ -554,7 +568,7 @@ AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int 
       int per_sm = (int)std::min<size_t>(smem_per_sm / std::max<size_t>(sm, 1), 2048 / threads);
       per_sm = std::min(per_sm, 32);
       if (per_sm < 1) continue;
-      const int res = interp_resident(fp64, jsm, ssm, p.n_colour == 0 && !fp64, threads, sm);
+      const int res = interp_resident(fp64, jsm, ssm, p.n_colour == 0 && !fp64, threads);
       if (res >= 1) per_sm = std::min(per_sm, res);
       double util = (double)(E * H) / threads;
       double lanes_sm = (double)per_sm * E * H;
@@ -638,7 +652,7 @@ std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, 
       int per_sm = (int)std::min<size_t>(smem_per_sm / std::max<size_t>(sm, 1), 2048 / threads);
       per_sm = std::min(per_sm, 32);
       if (per_sm < 1) continue;
-      const int res = interp_resident(fp64, pl[0] != 0, pl[1] != 0, p.n_colour == 0 && !fp64, threads, sm);
+      const int res = interp_resident(fp64, pl[0] != 0, pl[1] != 0, p.n_colour == 0 && !fp64, threads);
       if (res >= 1) per_sm = std::min(per_sm, res);
       AmpConfig c;
       c.H = H; c.E_cta = E; c.threads = threads; c.smem = sm;
@@ -646,6 +660,20 @@ std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, 
       c.grid = per_sm * num_sms;
       c.per_sm = per_sm;
       out.push_back(cap(c));
+      // with slots in global memory, fewer resident lanes per SM leave each lane
+      // more of the L1 and L2 for its wavefunction slots (fewer DRAM trips)
+      // against less latency hiding: the tuner times both sides
+      if (!pl[1]) {
+        int prev = per_sm;
+        for (int k : {per_sm / 2, 2, 1}) {
+          if (k < 1 || k >= prev) continue;
+          AmpConfig r = c;
+          r.per_sm = k;
+          r.grid = k * num_sms;
+          out.push_back(cap(r));
+          prev = k;
+        }
+      }
     }
   }
   return out;
@@ -676,34 +704,41 @@ int carveout_percent(const AmpConfig& c) {
 }
 
 template <typename R, bool J, bool S, bool O = false>
-static void launch_one(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
-  cudaFuncSetAttribute(amp_kernel<R, J, S, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-  cudaFuncSetAttribute(amp_kernel<R, J, S, O>, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_percent(c));
+static cudaError_t launch_one(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
+  cudaError_t e = ensure_dynamic_smem((const void*)amp_kernel<R, J, S, O>, c.smem);
+  if (e != cudaSuccess) return e;
+  // the carveout is a preference: a value the driver refuses leaves the launch valid
+  if (cudaFuncSetAttribute(amp_kernel<R, J, S, O>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           carveout_percent(c)) != cudaSuccess)
+    cudaGetLastError();
   amp_kernel<R, J, S, O><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const AmpLaunch& a,
                        cudaStream_t s) {
   if (c.grid <= 0) return cudaSuccess;
+  if (c.threads < 32 || c.threads > kMaxThreads || c.E_cta < 1 || c.E_cta * c.H > c.threads)
+    return cudaErrorInvalidConfiguration;
+  cudaError_t err = cudaSuccess;
   if (a.amp_out) {
     // diagram amplitudes out (no colour accumulators): FP32 interpreter only
     if (fp64 || p.n_colour != 0) return cudaErrorInvalidValue;
-    if (c.slots_in_smem) launch_one<float, true, true, true>(p, c, a, s);
-    else launch_one<float, true, false, true>(p, c, a, s);
+    err = c.slots_in_smem ? launch_one<float, true, true, true>(p, c, a, s) : launch_one<float, true, false, true>(p, c, a, s);
   } else if (p.gen) {
     p.gen->launch(fp64, c.regvar, p, c, a, s);
+    err = cudaGetLastError();
   } else if (fp64) {
-    if (c.jamp_in_smem && c.slots_in_smem) launch_one<double, true, true>(p, c, a, s);
-    else if (c.jamp_in_smem) launch_one<double, true, false>(p, c, a, s);
-    else if (c.slots_in_smem) launch_one<double, false, true>(p, c, a, s);
-    else launch_one<double, false, false>(p, c, a, s);
+    if (c.jamp_in_smem && c.slots_in_smem) err = launch_one<double, true, true>(p, c, a, s);
+    else if (c.jamp_in_smem) err = launch_one<double, true, false>(p, c, a, s);
+    else if (c.slots_in_smem) err = launch_one<double, false, true>(p, c, a, s);
+    else err = launch_one<double, false, false>(p, c, a, s);
   } else {
-    if (c.jamp_in_smem && c.slots_in_smem) launch_one<float, true, true>(p, c, a, s);
-    else if (c.jamp_in_smem) launch_one<float, true, false>(p, c, a, s);
-    else if (c.slots_in_smem) launch_one<float, false, true>(p, c, a, s);
-    else launch_one<float, false, false>(p, c, a, s);
+    if (c.jamp_in_smem && c.slots_in_smem) err = launch_one<float, true, true>(p, c, a, s);
+    else if (c.jamp_in_smem) err = launch_one<float, true, false>(p, c, a, s);
+    else if (c.slots_in_smem) err = launch_one<float, false, true>(p, c, a, s);
+    else err = launch_one<float, false, false>(p, c, a, s);
   }
-  cudaError_t err = cudaGetLastError();
   if (err == cudaSuccess) ++launch_counter();
   return err;
 }

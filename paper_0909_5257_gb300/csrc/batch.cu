@@ -80,8 +80,10 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
     // the tensor-core path runs the amplitude-output interpreter: time that
     dp.gen = nullptr;
     dp.n_colour = 0;
+    // a sample large enough to fill the GPU's resident lanes (its slot traffic
+    // competes for L2 only at that size): up to 4 GB of diagram amplitudes
     const size_t per_event = (size_t)H * 2 * (size_t)P->jmap.kd * sizeof(float);
-    n = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((size_t(1) << 30) / std::max<size_t>(per_event, 1))));
+    n = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((size_t(4) << 30) / std::max<size_t>(per_event, 1))));
     lda = ((2 * n * H + 127) / 128) * 128;
     if (abuf.ensure(sizeof(float) * (size_t)P->jmap.kd * (size_t)lda) != cudaSuccess ||
         rowmax.ensure(sizeof(float) * 2 * (size_t)H * n) != cudaSuccess ||
@@ -202,7 +204,7 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
         mea::candidate_configs(dp, fp64, H, (int64_t)1 << 40, P->num_sms, P->smem_optin, P->smem_per_sm);
     for (auto& f : full)
       if (f.E_cta == c.E_cta && f.threads == c.threads && f.jamp_in_smem == c.jamp_in_smem &&
-          f.slots_in_smem == c.slots_in_smem && f.regvar == c.regvar)
+          f.slots_in_smem == c.slots_in_smem && f.regvar == c.regvar && f.per_sm == c.per_sm)
         c.grid = f.grid;
     P->tuned[ti] = c;
     P->tuned_H[ti] = H;

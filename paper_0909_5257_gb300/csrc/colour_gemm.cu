@@ -338,7 +338,7 @@ cudaError_t launch_colour_gemm(const ColourGemmArgs& a, int num_sms, cudaStream_
   if (a.n_pairs <= 0) return cudaSuccess;
   if (a.nc < 32 || a.nc > 256 || a.nc % 32 != 0 || a.kp % kKC != 0 || a.np % a.nc != 0) return cudaErrorInvalidValue;
   size_t sm = colour_gemm_smem(a.nc);
-  cudaError_t e = cudaFuncSetAttribute(colour_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = ensure_dynamic_smem((const void*)colour_gemm_kernel, sm);
   if (e != cudaSuccess) return e;
   int64_t tiles = (2 * a.n_pairs + kM - 1) / kM;
   int tmem = 32;

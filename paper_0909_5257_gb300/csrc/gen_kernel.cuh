@@ -133,8 +133,10 @@ __global__ void __launch_bounds__(MAXT, MINB) gen_kernel(const DevProgram P, con
 template <typename R, typename Body, int MINB, int MAXT>
 void gen_launch_v(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
   auto k = gen_kernel<R, Body, MINB, MAXT>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-  cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_percent(c));
+  if (ensure_dynamic_smem((const void*)k, c.smem) != cudaSuccess) return;
+  // the carveout is a preference: a value the driver refuses leaves the launch valid
+  if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_percent(c)) != cudaSuccess)
+    cudaGetLastError();
   k<<<c.grid, c.threads, c.smem, s>>>(p, a, c);
 }
 

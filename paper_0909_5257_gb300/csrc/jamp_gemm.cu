@@ -337,7 +337,7 @@ cudaError_t launch_jamp_gemm(const JampGemmArgs& a, int num_sms, cudaStream_t s)
   if (a.n_pairs <= 0) return cudaSuccess;
   if (a.nc < 16 || a.nc > kMaxNC || a.nc % 16 != 0 || a.kpad % kKC != 0) return cudaErrorInvalidValue;
   const size_t sm = jamp_gemm_smem(a.nc);
-  cudaError_t e = cudaFuncSetAttribute(jamp_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = ensure_dynamic_smem((const void*)jamp_gemm_kernel, sm);
   if (e != cudaSuccess) return e;
   const int64_t work = ((2 * a.n_pairs + kM - 1) / kM) * a.n_splits;
   int tmem = 32;

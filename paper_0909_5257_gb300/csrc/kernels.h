@@ -130,4 +130,10 @@ cudaError_t launch_xsec_sums(const double* me2, const int32_t* att, int64_t n, d
 
 uint64_t& launch_counter();
 
+// Raise the largest dynamic shared memory a kernel may be launched with to at
+// least `bytes` (never lowers it).  Serialised across host threads: a launch
+// on one thread must not see another thread's smaller setting between its own
+// setting and its launch.
+cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes);
+
 }  // namespace mea

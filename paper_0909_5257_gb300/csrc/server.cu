@@ -41,6 +41,7 @@ struct SrvReq {
   int in_flight = 0;
   size_t reserve = 0;
   mea_status status = MEA_OK;
+  std::string error;  // message of the failure (the worker thread's mea_last_error), if any
   bool complete = false;
   Clock::time_point t_submit, t_done;
 };
@@ -48,6 +49,8 @@ struct SrvReq {
 struct SrvSlot {
   cudaStream_t s = nullptr;
   cudaEvent_t ev = nullptr;
+  // one scratch set per process the slot has run: sized once, so that chunks
+  // of different processes never regrow (and free) buffers between them
   std::map<mea_process_t, std::unique_ptr<mea::EvalScratch>> scratch;
   SrvReq* req = nullptr;
   int64_t cn = 0;
@@ -115,6 +118,7 @@ void mea_server_s::run() {
       r->in_flight--;
       progress = true;
       if (q != cudaSuccess) {
+        if (r->error.empty()) r->error = std::string("chunk failed on the device: ") + cudaGetErrorString(q);
         cudaGetLastError();
         r->next = r->n;
         if (r->in_flight == 0) complete_req(this, r, MEA_E_CUDA);
@@ -146,6 +150,7 @@ void mea_server_s::run() {
       r->next += cn;
       progress = true;
       if (st != MEA_OK) {
+        if (r->error.empty()) r->error = mea_last_error();
         r->status = st;
         r->next = r->n;
         if (r->in_flight == 0) complete_req(this, r, st);
@@ -247,8 +252,9 @@ mea_status mea_server_wait(mea_server_t S, uint64_t id, int timeout_ms, double* 
     return mea::set_error(MEA_E_TIMEOUT, "mea_server_wait: request " + std::to_string(id) + " not complete");
   if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
   mea_status st = r->status;
+  const std::string why = r->error;
   S->reqs.erase(it);
-  if (st != MEA_OK) return mea::set_error(st, "mea_server_wait: request failed");
+  if (st != MEA_OK) return mea::set_error(st, "mea_server_wait: request failed: " + why);
   return MEA_OK;
 }
 
