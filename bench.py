@@ -193,19 +193,20 @@ def max_over_ranks_value(x: float, dist=None, device=None) -> float:
 def serve_requests(rank: int, n_req: int, seed: int = SEED_BASE + 4):
     """The serving workload's request stream: request k = (subprocess index,
     events, first event of its momenta in that subprocess's generator
-    stream).  Rank r takes requests [r*n_req, (r+1)*n_req) of one seeded
-    stream, so the ranks' requests are disjoint (weak scaling)."""
-    rng = np.random.default_rng(seed)
-    total = (rank + 1) * n_req
-    kinds = rng.choice(len(SERVE_MIX), size=total, p=[w for *_, w in SERVE_MIX])
-    sizes = np.exp(rng.uniform(np.log(SERVE_SIZES[0]), np.log(SERVE_SIZES[1]), size=total)).astype(np.int64)
-    firsts = np.zeros(total, dtype=np.int64)
-    nxt = [0] * len(SERVE_MIX)
-    for k in range(total):
-        firsts[k] = nxt[kinds[k]]
-        nxt[kinds[k]] += int(sizes[k])
-    lo = rank * n_req
-    return [(int(kinds[k]), int(sizes[k]), int(firsts[k])) for k in range(lo, total)]
+    stream), drawn from its own seeded generator, so the stream does not
+    depend on how much of it is taken.  Rank r takes requests
+    [r*n_req, (r+1)*n_req): the ranks' requests are disjoint (weak scaling)."""
+    p = [w for *_, w in SERVE_MIX]
+    lo, hi = np.log(SERVE_SIZES[0]), np.log(SERVE_SIZES[1])
+    out, nxt = [], [0] * len(SERVE_MIX)
+    for k in range((rank + 1) * n_req):
+        rng = np.random.default_rng([seed, k])
+        kind = int(rng.choice(len(SERVE_MIX), p=p))
+        size = min(SERVE_SIZES[1], max(SERVE_SIZES[0], int(round(np.exp(rng.uniform(lo, hi))))))
+        if k >= rank * n_req:
+            out.append((kind, size, nxt[kind]))
+        nxt[kind] += size
+    return out
 
 
 def _dist():
@@ -341,10 +342,11 @@ def serve_cpu_baseline(procs):
 
 
 # ---- device-resident workloads ---------------------------------------------------
-def device_workload(name, steps, warmup, rank=0, ws=1, dist=None, autotune=True, sampled=True):
+def device_workload(name, steps, warmup, rank=0, ws=1, dist=None, autotune=True, sampled=True, fp64_events=None):
     """Evaluate every subprocess of a device-resident workload `steps` times
-    (after `warmup`), mixed and FP64; per-subprocess rates, errors, the
-    timing of each evaluation (CUDA events on the launching stream)."""
+    (after `warmup`), mixed and FP64 (on the first fp64_events events, all by
+    default); per-subprocess rates, errors, the timing of each evaluation
+    (CUDA events on the launching stream)."""
     import torch
     from paper_0909_5257_gb300 import mea
 
@@ -370,20 +372,24 @@ def device_workload(name, steps, warmup, rank=0, ws=1, dist=None, autotune=True,
     if autotune:
         for (sname, *_), P, m, o in zip(subs, procs, moms, outs):
             k = n if P.n_ext <= 5 else min(n, 1 << 16)
-            tuned[sname] = {pn: P.autotune(m[:k], o[:k], precision=pr)
-                            for pr, pn in ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64"))}
+            k64 = k if fp64_events is None else min(k, fp64_events)
+            tuned[sname] = {pn: P.autotune(m[:kk], o[:kk], precision=pr)
+                            for pr, pn, kk in ((mea.PREC_MIXED, "mixed", k), (mea.PREC_FP64, "fp64", k64))}
         torch.cuda.synchronize()
 
+    n64 = n if fp64_events is None else min(n, fp64_events)
+
     def step(prec, ev_pairs=None):
+        ne = n if prec == mea.PREC_MIXED else n64
         for i, P in enumerate(procs):
             if ev_pairs is not None:
                 ev_pairs[i][0].record(stream)
-            P.evaluate(moms[i], outs[i], precision=prec, flags=flags[i], stream=stream)
+            P.evaluate(moms[i][:ne], outs[i][:ne], precision=prec, flags=flags[i][:ne], stream=stream)
             if ev_pairs is not None:
                 ev_pairs[i][1].record(stream)
 
     def timed(prec, k):
-        for _ in range(warmup):
+        for _ in range(warmup if prec == mea.PREC_MIXED else min(warmup, 1)):
             step(prec)
         barrier()
         pairs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -410,9 +416,9 @@ def device_workload(name, steps, warmup, rank=0, ws=1, dist=None, autotune=True,
     per_sub = {}
     for i, (sname, pdg, nf, lo, hi) in enumerate(subs):
         info = procs[i].info
-        rel = (mixed_out[i] / fp64_out[i] - 1.0).abs()
+        rel = (mixed_out[i][:n64] / fp64_out[i][:n64] - 1.0).abs()
         d = {"mixed_events_per_s": n / (statistics.median(per_mixed[i]) * 1e-3),
-             "fp64_events_per_s": n / (statistics.median(per64[i]) * 1e-3),
+             "fp64_events_per_s": n64 / (statistics.median(per64[i]) * 1e-3), "fp64_events": n64,
              "diagrams": info["n_diagrams"], "colours": info["n_colour"], "helicities": info["n_hel_nonzero"],
              "flagged_fraction": float((mixed_flags[i] != 0).float().mean().item()),
              "mixed_vs_fp64_rel_err_median": float(rel.median().item()),
@@ -434,7 +440,7 @@ def device_workload(name, steps, warmup, rank=0, ws=1, dist=None, autotune=True,
             torch.cuda.synchronize()
             d["sampled_helicity_events_per_s"] = n / (ev0.elapsed_time(ev1) / 3 * 1e-3)
         per_sub[sname] = d
-    return {"subs": subs, "n": n, "procs": procs, "moms": moms, "per_sub": per_sub, "tuned": tuned,
+    return {"subs": subs, "n": n, "n64": n64, "procs": procs, "moms": moms, "per_sub": per_sub, "tuned": tuned,
             "ms_mixed": ms_mixed, "ms_fp64": ms64, "per_mixed": per_mixed, "launches": launches}
 
 
@@ -446,7 +452,7 @@ BATCH_SPEC = [  # (name, pdg, n_final, sqrt(s) range, configured events)
 ]
 
 
-def batch_workload(steps, warmup, scale=1.0):
+def batch_workload(steps, warmup, scale=1.0, with_fp64=True):
     """Batched mixed launch: four subprocesses of very uneven cost, counts
     perturbed by a seeded draw, autotuned per process, evaluated by one
     CUDA-graph launch per step (mea_batch_*); mixed vs FP64 graph."""
@@ -468,7 +474,8 @@ def batch_workload(steps, warmup, scale=1.0):
         scratch = torch.empty(k, dtype=torch.float64, device="cuda")
         tune[name] = P.autotune(m[:k], scratch, precision=mea.PREC_MIXED)
     res = {}
-    for prec, pname in ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64")):
+    precs = ((mea.PREC_MIXED, "mixed"), (mea.PREC_FP64, "fp64")) if with_fp64 else ((mea.PREC_MIXED, "mixed"),)
+    for prec, pname in precs:
         outs = [torch.empty(n, dtype=torch.float64, device="cuda") for n in n_ev]
         flags = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in n_ev]
         B = mea.Batch(list(zip(procs, moms, outs, flags)), precision=prec)
@@ -490,13 +497,15 @@ def batch_workload(steps, warmup, scale=1.0):
         B.close()
     errs = {}
     for i, (name, *_) in enumerate(BATCH_SPEC):
-        rel = (res["mixed_out"][i] / res["fp64_out"][i] - 1.0).abs()
-        errs[name] = {"events": n_ev[i], "mixed_vs_fp64_rel_err_median": float(rel.median()),
-                      "mixed_vs_fp64_rel_err_max": float(rel.max()),
+        errs[name] = {"events": n_ev[i],
                       "autotune": {k: tune[name][k] for k in ("threads", "events_per_cta", "register_cap")}}
+        if with_fp64:
+            rel = (res["mixed_out"][i] / res["fp64_out"][i] - 1.0).abs()
+            errs[name]["mixed_vs_fp64_rel_err_median"] = float(rel.median())
+            errs[name]["mixed_vs_fp64_rel_err_max"] = float(rel.max())
     return {"workload": "batched mixed launch (one CUDA graph): " +
                         ", ".join(f"{b[0]} {n}" for b, n in zip(BATCH_SPEC, n_ev)),
-            "mixed": res["mixed"], "fp64": res["fp64"], "per_subprocess": errs}
+            "mixed": res["mixed"], "fp64": res.get("fp64"), "per_subprocess": errs}
 
 
 # ---- serving headline ---------------------------------------------------------------
@@ -564,6 +573,15 @@ def run_serve(args):
     fp32_peak, _ = mea.measure_alu_peak(False, 0.3)
     fp64_peak, _ = mea.measure_alu_peak(True, 0.3)
     peak_clocks = sampler.stop()
+
+    phase = {}
+    t_phase = time.perf_counter()
+
+    def lap(name):
+        nonlocal t_phase
+        now = time.perf_counter()
+        phase[name] = round(now - t_phase, 1)
+        t_phase = now
 
     # ---- per subprocess: device-timed mixed (stage timing) and FP64 on the same inputs
     per_sub, stage_ms_ev, tune = {}, {}, {}
@@ -660,6 +678,7 @@ def run_serve(args):
                 tensor[f"{nm} {stg}"] = {"useful_tflops": useful, "executed_tflops": executed,
                                          "useful_frac": useful / bf16_sus, "executed_frac": executed / bf16_sus}
 
+    lap("per_subprocess_and_roofline")
     # ---- serving: capacity (timed steps), latency under Poisson load, e2e
     n_req = args.steps * REQS_PER_STEP
     reqs = serve_requests(rank, n_req)
@@ -718,6 +737,7 @@ def run_serve(args):
     capacity = ws * total / (dev_ms * 1e-3)
     flagged = float(sum(int((f != 0).sum()) for f in flags)) / total
 
+    lap("serving_capacity")
     # latency under Poisson arrivals at SERVE_LOAD x capacity (this rank's share)
     rng = np.random.default_rng(SEED_BASE + 5 + rank)
     mean_gap = (total / len(timed_reqs)) / (SERVE_LOAD * capacity / ws)
@@ -737,6 +757,7 @@ def run_serve(args):
     for (nm, _, n), l in zip(timed_reqs, lat):
         by_proc.setdefault(nm, []).append(l)
 
+    lap("serving_latency")
     # e2e: momenta from pinned host memory, results back to pinned host memory
     host = [m.cpu().pin_memory() for _, m, _ in timed_reqs]
     host_out = [torch.empty(n, dtype=torch.float64).pin_memory() for _, _, n in timed_reqs]
@@ -765,6 +786,7 @@ def run_serve(args):
            "how": "per request: pinned host momenta -> device (copy stream), mea_server_submit; |M|^2 "
                   "device -> pinned host after completion; wall clock over all requests"}
     del host, host_out, dev_in
+    lap("serving_e2e")
 
     if rank != 0:
         if dist is not None:
@@ -819,18 +841,26 @@ def run_serve(args):
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"], out["fp64_vs_oracle"] = serve_cpu_baseline(procs)
+        lap("cpu_baseline")
     if not args.no_extra:
         extra = {}
-        for wl in ("3jet", "4jet"):
-            r = device_workload(wl, 3, 2, sampled=(wl == "3jet"))
+        # bounded: FP64 on a subsample (2^18 / 2^16 events), the batch's FP64 graph left out
+        for wl, n64 in (("3jet", 1 << 18), ("4jet", 1 << 16)):
+            t_wl = time.perf_counter()
+            r = device_workload(wl, 3, 2, sampled=(wl == "3jet"), fp64_events=n64)
             extra[wl] = {"workload": WORKLOAD_TEXT[wl],
                          "mixed_events_per_s": len(r["subs"]) * r["n"] / (r["ms_mixed"] * 1e-3),
-                         "fp64_events_per_s": len(r["subs"]) * r["n"] / (r["ms_fp64"] * 1e-3),
-                         "per_subprocess": r["per_sub"]}
+                         "fp64_events_per_s": len(r["subs"]) * r["n64"] / (r["ms_fp64"] * 1e-3),
+                         "fp64_events_per_subprocess": r["n64"], "per_subprocess": r["per_sub"],
+                         "wall_s": time.perf_counter() - t_wl}
             del r
             torch.cuda.empty_cache()
-        extra["batch"] = batch_workload(3, 2)
+        t_wl = time.perf_counter()
+        extra["batch"] = batch_workload(3, 2, with_fp64=False)
+        extra["batch"]["wall_s"] = time.perf_counter() - t_wl
         out["other_workloads"] = extra
+        lap("other_workloads")
+    out["phase_wall_s"] = phase
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

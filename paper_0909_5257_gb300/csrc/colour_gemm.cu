@@ -50,11 +50,16 @@ constexpr int kPlaneA = kM * kKC * 2;
 
 __host__ __device__ constexpr size_t stage_bytes(int nc) { return (size_t)3 * kPlaneA + (size_t)2 * nc * kKC * 2; }
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// 1-D bulk copy global -> shared (TMA), completing `bytes` on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
 
 __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -63,7 +68,8 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
   const int NC = g.nc;
   const size_t SB = stage_bytes(NC);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SB);  // [2] MMA commits of the two TMEM buffers
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* kbar = bar + 2;                                      // [2] K tiles landed in each stage
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 4);
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
   float* rscale = reinterpret_cast<float*>(tslot + 4);           // [128] per-row scale 2^-e
   // scratch that lives in stage 1's first operand plane while no MMA reads it:
@@ -71,11 +77,23 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
   float* rmax = reinterpret_cast<float*>(smem + SB);                     // [256]
   double* part = reinterpret_cast<double*>(smem + SB + kThreads * 4);    // [256]
 
+  {
+    // the layout above must fit the dynamic shared memory of this launch
+    uint32_t dyn = 0;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    if ((size_t)dyn < (size_t)(reinterpret_cast<unsigned char*>(rscale + kM) - smem)) {
+      if (t == 0 && g.status) atomicExch(g.status, 2);
+      return;  // before any barrier, copy or tensor-memory use
+    }
+  }
   uint32_t tmem_cols = 32;
   while (tmem_cols < (uint32_t)(2 * NC)) tmem_cols <<= 1;
+  uint32_t kphase[2] = {0u, 0u};  // thread 0: next phase of each stage's K-tile barrier
   if (t == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
+    mbar_init(&kbar[0], 1);
+    mbar_init(&kbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
   }
@@ -96,7 +114,6 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
   const bool use_blo = g.b_lo != nullptr;
   const int row = t & (kM - 1);
   const int half = t >> 7;  // conversion: k groups of this thread; epilogue: column half
-  const int nvec = NC * kKC / 8;  // 16-byte vectors per K tile plane
 
   auto wait_buf = [&](int b) -> bool {
     if (!outstanding[b]) return true;
@@ -147,18 +164,19 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
         }
       }
     };
+    // K tiles of iteration it into stage st: one thread issues 1-D bulk copies
+    // (TMA) of the precomputed contiguous tiles, completing on kbar[st]; the
+    // stage's previous MMAs were waited for (epilogue of it-1, same thread)
     auto copy_tiles = [&](int it, int st) {
+      if (t != 0 || *abort_flag) return;
       const int nb = it / n_kc, kc = it % n_kc;
       unsigned char* b_hi = smem + st * SB + 3 * kPlaneA;
       unsigned char* b_lo = b_hi + (size_t)NC * kKC * 2;
       const size_t tile_off = ((size_t)nb * n_kc + kc) * NC * kKC;
-      const uint4* shi = reinterpret_cast<const uint4*>(g.b_hi + tile_off);
-      for (int i = t; i < nvec; i += kThreads) cp_async16(b_hi + 16 * i, shi + i);
-      if (use_blo) {
-        const uint4* slo = reinterpret_cast<const uint4*>(g.b_lo + tile_off);
-        for (int i = t; i < nvec; i += kThreads) cp_async16(b_lo + 16 * i, slo + i);
-      }
-      cp_async_commit();
+      const uint32_t bytes = (uint32_t)(NC * kKC * 2);
+      mbar_expect_tx(&kbar[st], use_blo ? 2 * bytes : bytes);
+      bulk_g2s(b_hi, g.b_hi + tile_off, bytes, &kbar[st]);
+      if (use_blo) bulk_g2s(b_lo, g.b_lo + tile_off, bytes, &kbar[st]);
     };
     // epilogue of iteration it (buffer it % 2): this thread's row, its half of the columns
     auto epilogue = [&](int it) {
@@ -223,11 +241,18 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
         *reinterpret_cast<uint4*>(a_mid + off) = *reinterpret_cast<const uint4*>(mv);
         *reinterpret_cast<uint4*>(a_lo + off) = *reinterpret_cast<const uint4*>(lv);
       }
-      cp_async_wait_all();  // this stage's K tiles
       fence_async_smem();
       fence_before();
       __syncthreads();
       fence_after();
+      if (t == 0 && !*abort_flag) {
+        // this stage's K tiles
+        if (!mbar_wait(&kbar[st], kphase[st])) {
+          atomicExch(abort_flag, 1);
+          if (g.status) atomicExch(g.status, 1);
+        }
+        kphase[st] ^= 1u;
+      }
       if (!*abort_flag) {
         if (t == 0) {
           const uint32_t lbo = 128, sbo = (kKC / 8) * 128;
@@ -276,6 +301,13 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
   // the tensor memory they write is released
   for (int b = 0; b < 2; ++b)
     if (outstanding[b]) mbar_wait(&bar[b], phase[b]);
+  // K-tile copies still in flight (only after an expired wait) land before the
+  // CTA's shared memory goes away
+  if (t == 0 && *abort_flag)
+    for (int b = 0; b < 2; ++b) {
+      mbar_wait(&kbar[b], 0u);
+      mbar_wait(&kbar[b], 1u);
+    }
   fence_before();
   __syncthreads();
   fence_after();
@@ -332,7 +364,8 @@ ColourTiles build_colour_tiles(const std::vector<int64_t>& K, int m) {
   return T;
 }
 
-size_t colour_gemm_smem(int nc) { return 2 * stage_bytes(nc) + 16 + 16 + (size_t)kM * 4; }
+// two stages, 4 mbarriers (32 B), TMEM slot and abort flag (16 B), row scales (512 B)
+size_t colour_gemm_smem(int nc) { return 2 * stage_bytes(nc) + 32 + 16 + (size_t)kM * 4 + 64; }
 
 cudaError_t launch_colour_gemm(const ColourGemmArgs& a, int num_sms, cudaStream_t s) {
   if (a.n_pairs <= 0) return cudaSuccess;

@@ -44,3 +44,24 @@ def test_two_rank_sharding_and_timing_reduction(tmp_path):
     assert np.array_equal(np.concatenate(shards), whole)  # disjoint, covering, in order
     for r in range(world):
         assert np.load(tmp_path / f"max{r}.npy")[0] == 0.5 * world
+
+
+def test_serving_request_stream_shards_without_overlap():
+    """The serving workload's request stream (bench.serve_requests): each rank
+    takes its own consecutive slice of one seeded stream, so two ranks see
+    disjoint requests whose momenta ranges do not overlap, and rank 0's slice
+    is the same whatever the world size."""
+    import bench
+    n = 17
+    r0, r1 = bench.serve_requests(0, n), bench.serve_requests(1, n)
+    both = bench.serve_requests(0, 2 * n)
+    assert r0 + r1 == both
+    seen = {}
+    for kind, size, first in both:
+        assert bench.SERVE_SIZES[0] <= size <= bench.SERVE_SIZES[1]
+        for a, b in seen.get(kind, []):
+            assert first >= b or first + size <= a
+        seen.setdefault(kind, []).append((first, first + size))
+    kinds = [k for k, _, _ in bench.serve_requests(0, 4000)]
+    shares = np.bincount(kinds, minlength=3) / len(kinds)
+    assert np.allclose(shares, [w for *_, w in bench.SERVE_MIX], atol=0.03)
