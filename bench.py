@@ -73,9 +73,10 @@ FP64_EVENTS = {"gg>ggggg": 2048, "uu~>ggggg": 8192, "uu>uuggg": 16384}
 CPU_SAMPLE = {"gg>ggggg": 16, "uu~>ggggg": 16, "uu>uuggg": 8}
 REF_PER_STEP = {"gg>ggggg": 4, "uu~>ggggg": 4, "uu>uuggg": 2}
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) per event of the dominant
-# kernel, from the capture summarised in profiles/ (None: not captured for
-# the current kernel)
-TRAFFIC_BYTES_PER_EVENT = {}
+# kernel, from the full-size one-pass ncu capture summarised under profiles/,
+# keyed by (subprocess, stage, threads, events per CTA, grid): a launch in
+# another configuration reports null
+TRAFFIC_BYTES_PER_EVENT = {("gg>ggggg", "amplitudes", 128, 1, 1368): (41.71e9 + 35.25e9) / 2731}
 
 # ---- device-resident workloads (extra keys) ------------------------------------
 WORKLOADS = {
@@ -648,7 +649,9 @@ def run_serve(args):
     if dom_stage == "amplitudes":
         flop = events_per_launch * H * fl_stage["amplitudes"]
         achieved = flop / (ms_per_launch * 1e-3) / 1e12
-        tpe = TRAFFIC_BYTES_PER_EVENT.get((dom_nm, dom_stage))
+        tc = tune.get(dom_nm) or {}
+        tpe = TRAFFIC_BYTES_PER_EVENT.get((dom_nm, dom_stage, tc.get("threads"), tc.get("events_per_cta"),
+                                           tc.get("grid")))
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": achieved / fp32_peak, "traffic": None if tpe is None else tpe * events_per_launch,
                     "kernel": f"amp_kernel<float> amplitude output ({dom_nm}), {events_per_launch:.0f} events "
@@ -724,9 +727,14 @@ def run_serve(args):
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     c0.record(stream)
     t0 = time.perf_counter()
+    # the timed region as the profiler's collection range (cudaProfilerStart/Stop:
+    # process-wide, so the server's worker-thread launches are inside it; no-ops
+    # without a profiler)
+    torch.cuda.profiler.start()
     serve_all(srv, timed_reqs, out_list=outs, flag_list=flags)
     c1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     wall = time.perf_counter() - t0
     barrier()
     clocks = sampler.stop()
@@ -938,19 +946,30 @@ def run_device(args):
 
 
 def run_single(args):
-    """One subprocess, --events events generated on the device, evaluated once
-    (tuning on first use from 2^16 events), then again inside an NVTX range
-    "eval" (the range a profiler restricts itself to); prints timing."""
+    """One subprocess, --events events generated on the device, evaluated
+    once (tuning on first use; below 2^16 events tuned beforehand on 2^16
+    events, as the serving workload's per-subprocess pass is; neither with
+    --no-autotune), then again inside an NVTX range "eval" (the range a
+    profiler restricts itself to); prints timing and the tuned configuration."""
     import torch
     from paper_0909_5257_gb300 import mea
     pdg, lo, hi = SINGLE[args.process]
     torch.cuda.set_device(0)
     prec = mea.PREC_FP64 if args.precision == "fp64" else mea.PREC_MIXED
-    P = mea.Process(pdg)
+    P = mea.Process(pdg, auto_tune=not args.no_autotune)
     n = args.events
-    mom = torch.empty((n, len(pdg), 4), dtype=torch.float64, device="cuda")
-    mea.generate_phase_space(len(pdg) - 2, n, mom, rs_lo=lo, rs_hi=hi)
-    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    # below 2^16 events the evaluation would not tune itself: tune on 2^16
+    # events of the same generator, as the serving workload does
+    tune_here = n < (1 << 16) and not args.no_autotune
+    n_gen = max(n, 1 << 16) if tune_here else n
+    mom = torch.empty((n_gen, len(pdg), 4), dtype=torch.float64, device="cuda")
+    mea.generate_phase_space(len(pdg) - 2, n_gen, mom, rs_lo=lo, rs_hi=hi)
+    out = torch.empty(n_gen, dtype=torch.float64, device="cuda")
+    tuned = None
+    if tune_here:
+        r = P.autotune(mom[:1 << 16], out[:1 << 16], precision=prec)
+        tuned = {k: r[k] for k in ("threads", "events_per_cta", "grid", "slots_in_shared")}
+    mom, out = mom[:n], out[:n]
     P.evaluate(mom, out, precision=prec)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -963,7 +982,8 @@ def run_single(args):
     P.check_status()
     ms = e0.elapsed_time(e1)
     print(json.dumps({"process": args.process, "events": n, "precision": args.precision, "ms": ms,
-                      "events_per_s": n / (ms * 1e-3), "mean_me2": float(out.mean())}), flush=True)
+                      "events_per_s": n / (ms * 1e-3), "mean_me2": float(out.mean()),
+                      "config": tuned}), flush=True)
 
 
 def main():

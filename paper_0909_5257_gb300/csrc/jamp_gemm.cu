@@ -134,14 +134,22 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
     float pa[kKC / 8 / (kThreads / kM)][8];
     uint4 pb[kTileVec];
     const int nb = NC * kKC / 8;  // 16-byte vectors per coefficient tile
+    const float* arow = g.A + r;
     auto prefetch = [&](int kc) {
+      const bool full = (kc + 1) * kKC <= g.kd;
 #pragma unroll
       for (int j = 0; j < kKC / 8 / (kThreads / kM); ++j) {
         const int kg = (t >> 7) + j * (kThreads / kM);
+        const float* src = arow + (size_t)(kc * kKC + kg * 8) * g.lda;
+        if (full) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int d = kc * kKC + kg * 8 + i;
-          pa[j][i] = (row_ok && d < g.kd) ? __ldg(g.A + (size_t)d * g.lda + r) : 0.f;
+          for (int i = 0; i < 8; ++i) pa[j][i] = row_ok ? __ldg(src + (size_t)i * g.lda) : 0.f;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int d = kc * kKC + kg * 8 + i;
+            pa[j][i] = (row_ok && d < g.kd) ? __ldg(src + (size_t)i * g.lda) : 0.f;
+          }
         }
       }
       const uint4* src = reinterpret_cast<const uint4*>(g.tiles + ((size_t)split * n_kc + kc) * NC * kKC);
@@ -172,14 +180,16 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
             float h[2], mm[2], l[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-              // round to the nearest integer by adding and removing 1.5 * 2^23
-              // (exact for |x| < 2^22; here |x| <= 2^12), on the FMA pipe
-              const float x = __fmul_rn(pa[j][i + u], sc);
-              h[u] = __fsub_rn(__fadd_rn(x, kRoundMagic), kRoundMagic);
-              const float r1 = __fmul_rn(__fsub_rn(x, h[u]), w1);
-              mm[u] = __fsub_rn(__fadd_rn(r1, kRoundMagic), kRoundMagic);
-              const float r2 = __fmul_rn(__fsub_rn(r1, mm[u]), w1);
-              l[u] = __fsub_rn(__fadd_rn(r2, kRoundMagic), kRoundMagic);
+              // x = a sc, r1 = (x - h) w1, r2 = (r1 - m) w1: every product by
+              // the powers of two sc and w1 and every difference of a value and
+              // its nearest integer is exact, so each FMA below rounds once,
+              // where adding 1.5 * 2^23 rounds to the nearest integer
+              const float a = pa[j][i + u];
+              h[u] = __fsub_rn(__fmaf_rn(a, sc, kRoundMagic), kRoundMagic);
+              const float y1 = __fmaf_rn(a, sc, -h[u]);  // x - h
+              mm[u] = __fsub_rn(__fmaf_rn(y1, w1, kRoundMagic), kRoundMagic);
+              const float y2 = __fmaf_rn(y1, w1, -mm[u]);  // r1 - m
+              l[u] = __fsub_rn(__fmaf_rn(y2, w1, kRoundMagic), kRoundMagic);
             }
             // integers of at most 2^q <= 2048 in magnitude: exact in FP16
             hv[i / 2] = __floats2half2_rn(h[0], h[1]);
