@@ -61,7 +61,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g) {
+__global__ void __launch_bounds__(kThreads, 1) colour_gemm_kernel(ColourGemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int t = threadIdx.x;
   const int warp = t >> 5;
@@ -133,11 +133,23 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
     const int64_t r = row0 + row;
     const bool row_ok = r < n_rows;
     const float* jrow = g.J + r * ldj;
+    // J is read in 16-byte vectors of one row: the row starts are 16-byte
+    // aligned (ldj is a multiple of 16, checked at launch), and a vector that
+    // starts below m ends within the row (at most ldj); entries at m and
+    // beyond are never used
+    const float4* jrow4 = reinterpret_cast<const float4*>(jrow);
     // per-row power-of-two scale so that the largest |J| lands near 2^14
     {
       float mx = 0.f;
       if (row_ok)
-        for (int k = half; k < m; k += 2) mx = fmaxf(mx, fabsf(jrow[k]));
+        for (int k4 = half; 4 * k4 < m; k4 += 2) {
+          const float4 v = jrow4[k4];
+          const int k = 4 * k4;
+          mx = fmaxf(mx, fabsf(v.x));
+          if (k + 1 < m) mx = fmaxf(mx, fabsf(v.y));
+          if (k + 2 < m) mx = fmaxf(mx, fabsf(v.z));
+          if (k + 3 < m) mx = fmaxf(mx, fabsf(v.w));
+        }
       rmax[t] = mx;
       __syncthreads();
       if (t < kM) {
@@ -156,12 +168,15 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
       const int kc = it % n_kc;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int kg = half + 2 * j;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int kk = kc * kKC + kg * 8 + i;
-          pj[j][i] = (row_ok && kk < m) ? jrow[kk] : 0.f;
+        const int kk0 = kc * kKC + (half + 2 * j) * 8;
+        float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+        if (row_ok && kk0 < m) {
+          v0 = jrow4[kk0 / 4];
+          v1 = jrow4[kk0 / 4 + 1];
         }
+        const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) pj[j][i] = (kk0 + i < m) ? v[i] : 0.f;
       }
     };
     // K tiles of iteration it into stage st: one thread issues 1-D bulk copies
@@ -187,6 +202,21 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
       const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
       const uint32_t base = tmem + (uint32_t)(b * NC) + lane;
       for (int c0 = half * (NC / 2); c0 < (half + 1) * (NC / 2); c0 += 16) {
+        float jvals[16];
+        {
+          float4 v[4] = {};
+          if (row_ok && n0 + c0 < m) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = jrow4[(n0 + c0) / 4 + q];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            jvals[4 * q] = v[q].x;
+            jvals[4 * q + 1] = v[q].y;
+            jvals[4 * q + 2] = v[q].z;
+            jvals[4 * q + 3] = v[q].w;
+          }
+        }
         float z[16];
         tmem_ld16(base + (uint32_t)c0, z);
         if (row_ok) {
@@ -196,7 +226,7 @@ __global__ void __launch_bounds__(kThreads) colour_gemm_kernel(ColourGemmArgs g)
             if (a < m) {
               // Dot2 (Ogita, Rump, Oishi 2005): exact product error by FMA,
               // two-sum of the running value, errors collected in acc_lo
-              const float jv = jrow[a];
+              const float jv = jvals[i];
               const float p = __fmul_rn(jv, z[i]);
               const float pe = fmaf(jv, z[i], -p);
               const float s = __fadd_rn(acc_hi, p);
@@ -370,6 +400,8 @@ size_t colour_gemm_smem(int nc) { return 2 * stage_bytes(nc) + 32 + 16 + (size_t
 cudaError_t launch_colour_gemm(const ColourGemmArgs& a, int num_sms, cudaStream_t s) {
   if (a.n_pairs <= 0) return cudaSuccess;
   if (a.nc < 32 || a.nc > 256 || a.nc % 32 != 0 || a.kp % kKC != 0 || a.np % a.nc != 0) return cudaErrorInvalidValue;
+  // the kernel reads J in 16-byte vectors within rows of ldj >= m entries
+  if (a.ldj % 16 != 0 || a.m > a.ldj || (reinterpret_cast<uintptr_t>(a.J) & 15) != 0) return cudaErrorInvalidValue;
   size_t sm = colour_gemm_smem(a.nc);
   cudaError_t e = ensure_dynamic_smem((const void*)colour_gemm_kernel, sm);
   if (e != cudaSuccess) return e;
