@@ -297,15 +297,24 @@ mea_status mea_batch_destroy(mea_batch_t batch);
 /* ---- serving loop -----------------------------------------------------------
  * Continuous batching of evaluation requests on one GPU.  A worker thread owns
  * n_slots CUDA streams; each request (a process, device momenta and output
- * buffers) is split into chunks of at most chunk_events events, and chunks of
- * all admitted requests are dispatched to free slots in arrival order, so that
- * requests arriving while others run are admitted as slots free up and their
- * work overlaps on the device.  Admission is by memory: every request reserves
- * the scratch bytes its chunks need (library estimate) from mem_budget_bytes
- * until it completes; a request that can never fit is rejected at submission
- * (MEA_E_REJECTED), others wait in a queue.  Per-event results do not depend on
- * chunking or on the other requests in flight (bitwise), because every event
- * is evaluated by the same arithmetic in any tile.
+ * buffers) is split into chunks of about 1e11 FLOPs by the process's operation
+ * count (the FP64 path weighted 24x), a multiple of 128 events and at most
+ * chunk_events events.  Whenever a slot is free the worker dispatches a chunk
+ * of the admitted request with the least remaining estimated device time
+ * minus a quarter of the time it has waited since submission (shortest
+ * remaining work first, with aging so that long requests are not starved);
+ * requests arriving while others run start as soon as a slot frees up, and
+ * work of different requests overlaps on the device.  Admission is by memory:
+ * every slot keeps one scratch set per process it has run, so the scratch of
+ * a process is committed per process (slots x one chunk's estimate, up to its
+ * requests' chunk counts) against mem_budget_bytes and a process's chunks run
+ * on at most that many distinct slots; a request whose process is committed
+ * is admitted at once, the scratch of processes without requests is released
+ * when the budget is short, a request waits while not even one slot fits, and
+ * a request whose single chunk exceeds the budget is rejected at submission
+ * (MEA_E_REJECTED).  Per-event results do not depend on chunking or on the
+ * other requests in flight (bitwise), because every event is evaluated by the
+ * same arithmetic in any tile.
  * Thread-safe.  The caller keeps the buffers alive until the request is
  * complete.  No call blocks without a bound: mea_server_wait returns
  * MEA_E_TIMEOUT when timeout_ms expires. */
@@ -316,7 +325,7 @@ typedef struct {
   uint64_t events_completed;
   double p50_ms, p99_ms, max_ms;  /* latency submit -> completion observed */
   double busy_seconds;            /* wall time with at least one chunk in flight */
-  size_t reserved_bytes;          /* scratch currently reserved by admitted requests */
+  size_t reserved_bytes;          /* scratch currently committed to processes */
 } mea_server_stats_t;
 
 mea_status mea_server_create(size_t mem_budget_bytes, int n_slots, int64_t chunk_events, mea_server_t *out);

@@ -1,13 +1,25 @@
 // Serving loop with continuous batching (C ABI, declared in include/mea.h).
 //
 // One worker thread drives n_slots CUDA streams.  Requests are split into
-// chunks; whenever a slot is free the worker dispatches the next chunk of the
-// admitted request that has waited longest since its last chunk (round robin
-// over requests), so new requests start as soon as any slot frees up and work
-// of different requests overlaps on the GPU.  Admission is by memory:
-// each request reserves its scratch estimate from the budget until it is
-// complete.  Completion is observed with cudaEventQuery (never a blocking
-// device call in the loop); every host-side wait has a bound.
+// chunks of about the same device cost (kChunkFlop FLOPs by the process's
+// operation count, at most chunk_events events), so that no chunk holds a
+// slot for long.  Whenever a slot is free the worker dispatches the next
+// chunk of the admitted request with the least remaining work, counted in
+// estimated device seconds, minus kAging times the seconds it has waited
+// since submission: short requests overtake long ones (shortest remaining
+// work first), and a long request gains priority as it ages, so none
+// starves.  Work of different requests overlaps on the device.
+//
+// Memory: every slot keeps one scratch set per process it has run (sized
+// once, never regrown between chunks), so the scratch a process can hold is
+// at most (its slots) x (its chunk's estimate), whatever the number of its
+// requests.  Admission commits that per process against mem_budget_bytes: a
+// request whose process is committed is admitted at once (no head-of-line
+// blocking behind requests of other processes); a process's chunks run only
+// on as many distinct slots as are committed for it; when the budget is
+// short, the scratch of processes with no request left is released.
+// Completion is observed with cudaEventQuery (never a blocking device call in
+// the loop); every host-side wait has a bound.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +40,13 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Dispatch and chunking constants (see the comment at the top).
+constexpr double kChunkFlop = 1e11;    // target device work of one chunk
+constexpr int64_t kChunkQuantum = 128; // chunk sizes are multiples of this (or the whole request)
+constexpr double kAging = 0.25;        // priority gained per second waited, in seconds of work
+constexpr double kFp64Cost = 24.0;     // FP64 path cost per FLOP relative to the mixed path (measured 19-28)
+constexpr double kInitialRate = 1e13;  // FLOP/s assumed until the server has measured its own
+
 struct SrvReq {
   uint64_t id = 0;
   mea_process_t proc = nullptr;
@@ -39,7 +58,9 @@ struct SrvReq {
   int64_t next = 0;     // first event not yet dispatched
   int64_t done = 0;     // events whose chunk completed
   int in_flight = 0;
-  size_t reserve = 0;
+  int64_t chunk = 1;    // events per chunk
+  double flop_per_event = 0;
+  size_t slot_bytes = 0;  // scratch estimate of one chunk (one slot's scratch set)
   mea_status status = MEA_OK;
   std::string error;  // message of the failure (the worker thread's mea_last_error), if any
   bool complete = false;
@@ -54,18 +75,28 @@ struct SrvSlot {
   std::map<mea_process_t, std::unique_ptr<mea::EvalScratch>> scratch;
   SrvReq* req = nullptr;
   int64_t cn = 0;
+  double flop = 0;  // estimated work of the chunk in flight
   bool busy = false;
+};
+
+// Per process: the scratch committed against the budget and its use.
+struct ProcState {
+  size_t slot_bytes = 0;  // committed per slot (largest chunk estimate seen)
+  int allowed = 0;        // slots committed: distinct slots that may hold its scratch
+  int holding = 0;        // slots that hold a scratch set of it
+  int requests = 0;       // admitted requests not yet complete
 };
 
 }  // namespace
 
 struct mea_server_s {
-  size_t budget = 0, reserved = 0;
-  int64_t chunk = 1 << 14;
+  size_t budget = 0, reserved = 0;  // reserved: sum of the processes' commitments
+  int64_t chunk = 1 << 14;          // largest chunk (events)
   std::vector<SrvSlot> slots;
   std::deque<SrvReq*> waiting;  // submitted, not admitted (memory)
-  std::deque<SrvReq*> active;   // admitted, events left to dispatch
+  std::vector<SrvReq*> active;  // admitted, events left to dispatch
   std::unordered_map<uint64_t, std::unique_ptr<SrvReq>> reqs;
+  std::unordered_map<mea_process_t, ProcState> procs;
   std::mutex mu;
   std::condition_variable cv_done, cv_work;
   std::thread worker;
@@ -75,10 +106,14 @@ struct mea_server_s {
   std::vector<double> lat_ms;
   int device = 0;
   double busy_s = 0;
+  double flop_done = 0;  // estimated work of the completed chunks (for the rate)
   Clock::time_point busy_since;
   int chunks_in_flight = 0;
 
   void run();
+  double rate() const { return busy_s > 0.05 && flop_done > 0 ? flop_done / busy_s : kInitialRate; }
+  bool admit(SrvReq* r);
+  void release_idle(mea_process_t keep);
 };
 
 namespace {
@@ -88,7 +123,7 @@ void complete_req(mea_server_s* S, SrvReq* r, mea_status st) {
   if (st != MEA_OK && r->status == MEA_OK) r->status = st;
   r->complete = true;
   r->t_done = Clock::now();
-  S->reserved -= std::min(S->reserved, r->reserve);
+  S->procs[r->proc].requests--;
   S->n_completed++;
   S->ev_completed += (uint64_t)r->done;
   S->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
@@ -97,6 +132,55 @@ void complete_req(mea_server_s* S, SrvReq* r, mea_status st) {
 }
 
 }  // namespace
+
+// Release the scratch of every process other than `keep` that has no
+// admitted request left and no chunk in flight, and its commitment.
+void mea_server_s::release_idle(mea_process_t keep) {
+  for (auto& kv : procs) {
+    ProcState& ps = kv.second;
+    if (kv.first == keep || ps.requests > 0 || ps.allowed == 0) continue;
+    bool in_flight = false;
+    for (auto& sl : slots)
+      if (sl.busy && sl.req && sl.req->proc == kv.first) in_flight = true;
+    if (in_flight) continue;
+    for (auto& sl : slots) {
+      auto it = sl.scratch.find(kv.first);
+      if (it == sl.scratch.end()) continue;
+      it->second->release();
+      sl.scratch.erase(it);
+    }
+    reserved -= std::min(reserved, ps.slot_bytes * (size_t)ps.allowed);
+    ps.allowed = 0;
+    ps.holding = 0;
+    ps.slot_bytes = 0;
+  }
+}
+
+// Commit scratch for r's process (at least one slot, up to one per chunk of
+// r, at most every slot) and admit r; false if not even one slot fits.
+bool mea_server_s::admit(SrvReq* r) {
+  ProcState& ps = procs[r->proc];
+  if (r->slot_bytes > ps.slot_bytes) {
+    // a larger chunk estimate (another precision): recommit what is held at the new size
+    const size_t extra = (r->slot_bytes - ps.slot_bytes) * (size_t)ps.allowed;
+    if (reserved + extra > budget) release_idle(r->proc);
+    if (reserved + extra > budget) return false;
+    reserved += extra;
+    ps.slot_bytes = r->slot_bytes;
+  }
+  const int64_t chunks = (r->n + r->chunk - 1) / r->chunk;
+  const int want = (int)std::min<int64_t>((int64_t)slots.size(), std::max<int64_t>(1, chunks));
+  while (ps.allowed < want) {
+    if (reserved + ps.slot_bytes > budget) release_idle(r->proc);
+    if (reserved + ps.slot_bytes > budget) break;
+    reserved += ps.slot_bytes;
+    ps.allowed++;
+  }
+  if (ps.allowed == 0) return false;
+  ps.requests++;
+  active.push_back(r);
+  return true;
+}
 
 void mea_server_s::run() {
   cudaSetDevice(device);  // the worker drives the device the server was created on
@@ -121,29 +205,51 @@ void mea_server_s::run() {
         if (r->error.empty()) r->error = std::string("chunk failed on the device: ") + cudaGetErrorString(q);
         cudaGetLastError();
         r->next = r->n;
+        active.erase(std::remove(active.begin(), active.end(), r), active.end());
         if (r->in_flight == 0) complete_req(this, r, MEA_E_CUDA);
         else r->status = MEA_E_CUDA;
         continue;
       }
+      flop_done += sl.flop;
       r->done += sl.cn;
       if (r->done == r->n || (r->next == r->n && r->in_flight == 0)) complete_req(this, r, MEA_OK);
     }
-    // 2. admission by memory
-    while (!stop && !waiting.empty() && reserved + waiting.front()->reserve <= budget) {
-      SrvReq* r = waiting.front();
-      waiting.pop_front();
-      reserved += r->reserve;
-      active.push_back(r);
-      progress = true;
+    // 2. admission by memory, in arrival order, skipping requests that do not fit yet
+    if (!stop) {
+      for (auto it = waiting.begin(); it != waiting.end();) {
+        if (admit(*it)) {
+          it = waiting.erase(it);
+          progress = true;
+        } else {
+          ++it;
+        }
+      }
     }
-    // 3. dispatch chunks to free slots, round robin over admitted requests
+    // 3. dispatch: each free slot takes a chunk of the eligible request with the
+    //    least remaining work (device seconds) less kAging x its age
+    const Clock::time_point now = Clock::now();
+    const double R = rate();
     for (auto& sl : slots) {
       if (sl.busy || active.empty() || stop) continue;
-      SrvReq* r = active.front();
-      active.pop_front();
-      const int64_t c0 = r->next, cn = std::min(chunk, r->n - r->next);
+      SrvReq* r = nullptr;
+      double best = 0;
+      for (SrvReq* c : active) {
+        const ProcState& ps = procs[c->proc];
+        if (!sl.scratch.count(c->proc) && ps.holding >= ps.allowed) continue;  // no committed slot left for it
+        const double age = std::chrono::duration<double>(now - c->t_submit).count();
+        const double key = (double)(c->n - c->next) * c->flop_per_event / R - kAging * age;
+        if (!r || key < best) {
+          r = c;
+          best = key;
+        }
+      }
+      if (!r) continue;
+      const int64_t c0 = r->next, cn = std::min(r->chunk, r->n - r->next);
       auto& sc = sl.scratch[r->proc];
-      if (!sc) sc.reset(new mea::EvalScratch());
+      if (!sc) {
+        sc.reset(new mea::EvalScratch());
+        procs[r->proc].holding++;
+      }
       const int n_ext = r->proc->prog.n_ext;
       mea_status st = mea::evaluate_with(r->proc, *sc, r->mom + (size_t)c0 * n_ext * 4, cn, MEA_HEL_SUM_NONZERO,
                                          nullptr, r->prec, r->me2 + c0, r->flags ? r->flags + c0 : nullptr, sl.s);
@@ -153,6 +259,7 @@ void mea_server_s::run() {
         if (r->error.empty()) r->error = mea_last_error();
         r->status = st;
         r->next = r->n;
+        active.erase(std::remove(active.begin(), active.end(), r), active.end());
         if (r->in_flight == 0) complete_req(this, r, st);
         continue;
       }
@@ -160,10 +267,11 @@ void mea_server_s::run() {
       sl.busy = true;
       sl.req = r;
       sl.cn = cn;
+      sl.flop = (double)cn * r->flop_per_event;
       if (chunks_in_flight == 0) busy_since = Clock::now();
       ++chunks_in_flight;
       r->in_flight++;
-      if (r->next < r->n) active.push_back(r);  // back of the line: interleave requests
+      if (r->next >= r->n) active.erase(std::remove(active.begin(), active.end(), r), active.end());
     }
     if (stop) {
       if (!stopping) { stopping = true; stop_deadline = Clock::now() + std::chrono::seconds(60); }
@@ -213,16 +321,22 @@ mea_status mea_server_submit(mea_server_t S, mea_process_t P, const double* mom,
   r->prec = prec;
   r->me2 = me2;
   r->flags = flags;
-  const int64_t cn = std::min<int64_t>(std::max<int64_t>(n, 1), S->chunk);
-  const int64_t n_chunks = (n + S->chunk - 1) / S->chunk;
-  r->reserve = mea::scratch_estimate(P, cn, prec) * (size_t)std::max<int64_t>(1, std::min<int64_t>(n_chunks, (int64_t)S->slots.size()));
+  // cost model: the process's operation count per event (helicity sum), the
+  // FP64 path weighted by its measured slowdown; chunks of about kChunkFlop
+  r->flop_per_event = std::max(1.0, P->prog.flops_per_hel * (double)std::max(1, P->prog.n_hel) *
+                                        (prec == MEA_PREC_FP64 ? kFp64Cost : 1.0));
+  int64_t cn = (int64_t)(kChunkFlop / r->flop_per_event) / kChunkQuantum * kChunkQuantum;
+  cn = std::min(S->chunk, std::max(kChunkQuantum, cn));
+  r->chunk = std::min<int64_t>(std::max<int64_t>(n, 1), cn);
+  r->slot_bytes = mea::scratch_estimate(P, r->chunk, prec);
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->stop) return mea::set_error(MEA_E_REJECTED, "mea_server_submit: server is stopping");
   S->n_submitted++;
-  if (r->reserve > S->budget) {
+  if (r->slot_bytes > S->budget) {
     S->n_rejected++;
-    return mea::set_error(MEA_E_REJECTED, "mea_server_submit: request needs " + std::to_string(r->reserve) +
-                                              " bytes of scratch, budget is " + std::to_string(S->budget));
+    return mea::set_error(MEA_E_REJECTED, "mea_server_submit: one chunk of the request needs " +
+                                              std::to_string(r->slot_bytes) + " bytes of scratch, budget is " +
+                                              std::to_string(S->budget));
   }
   r->id = S->next_id++;
   r->t_submit = Clock::now();
@@ -284,7 +398,7 @@ mea_status mea_server_destroy(mea_server_t S) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->stop = true;
     for (SrvReq* r : S->waiting) {
-      r->reserve = 0;  // never admitted: nothing reserved
+      S->procs[r->proc].requests++;  // never admitted: balance the count complete_req takes back
       complete_req(S, r, MEA_E_REJECTED);
     }
     S->waiting.clear();

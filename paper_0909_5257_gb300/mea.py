@@ -403,8 +403,9 @@ class Batch:
 
 class Server:
     """Continuous-batching request loop (mea_server_*): requests of any
-    process are split into chunks dispatched round robin to n_slots streams,
-    admitted by a scratch-memory budget."""
+    process are split into chunks of similar device cost, dispatched to
+    n_slots streams shortest remaining work first (with aging), admitted by
+    a scratch-memory budget committed per process."""
 
     def __init__(self, mem_budget_bytes=4 << 30, n_slots=4, chunk_events=1 << 14):
         h = ctypes.c_void_p()
