@@ -125,17 +125,19 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
     }
     __syncthreads();
 
-    // Register prefetch: each thread holds its 4 x 8 amplitudes and 4 tile
-    // vectors of the next chunk, issued right after the current chunk is
-    // converted so that the loads overlap the MMAs and the barrier.
+    // Register prefetch: each thread holds its 2 x 8 amplitudes of the next
+    // two chunks (two buffers, used alternately) and the coefficient-tile
+    // vectors of the next chunk; a chunk's loads are issued right after the
+    // buffer they replace is converted, so they have two chunks' time to land.
     const int row = t & (kM - 1);
     const int64_t r = row0 + row;
     const bool row_ok = r < n_rows;
-    float pa[kKC / 8 / (kThreads / kM)][8];
+    typedef float ABuf[kKC / 8 / (kThreads / kM)][8];
+    ABuf pa0, pa1;  // amplitudes of the chunks two apart: prefetched two chunks ahead
     uint4 pb[kTileVec];
     const int nb = NC * kKC / 8;  // 16-byte vectors per coefficient tile
     const float* arow = g.A + r;
-    auto prefetch = [&](int kc) {
+    auto prefetch_a = [&](int kc, ABuf& pa) {
       const bool full = (kc + 1) * kKC <= g.kd;
 #pragma unroll
       for (int j = 0; j < kKC / 8 / (kThreads / kM); ++j) {
@@ -152,6 +154,8 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
           }
         }
       }
+    };
+    auto prefetch_b = [&](int kc) {
       const uint4* src = reinterpret_cast<const uint4*>(g.tiles + ((size_t)split * n_kc + kc) * NC * kKC);
 #pragma unroll
       for (int j = 0; j < kTileVec; ++j) {
@@ -159,8 +163,10 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
         if (i < nb) pb[j] = __ldg(src + i);
       }
     };
-    prefetch(0);
-    for (int kc = 0; kc < n_kc; ++kc) {
+    prefetch_a(0, pa0);
+    if (n_kc > 1) prefetch_a(1, pa1);
+    prefetch_b(0);
+    auto step = [&](int kc, ABuf& pa) {
       const int st = kc & 1;
       wait_stage(st);  // the MMAs that read this stage two chunks ago are done
       unsigned char* a_h = smem + st * SB;
@@ -211,7 +217,8 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
           if (i < nb) dst[i] = pb[j];
         }
       }
-      if (kc + 1 < n_kc) prefetch(kc + 1);
+      if (kc + 2 < n_kc) prefetch_a(kc + 2, pa);
+      if (kc + 1 < n_kc) prefetch_b(kc + 1);
       fence_async_smem();
       fence_before();
       __syncthreads();
@@ -231,6 +238,10 @@ __global__ void __launch_bounds__(kThreads) jamp_gemm_kernel(JampGemmArgs g) {
         }
         outstanding[st] = 1;
       }
+    };
+    for (int kc = 0; kc < n_kc; kc += 2) {
+      step(kc, pa0);
+      if (kc + 1 < n_kc) step(kc + 1, pa1);
     }
     // all MMAs of this tile: the last chunk's commit covers every earlier one,
     // but each barrier's phases are consumed in order
