@@ -76,7 +76,8 @@ REF_PER_STEP = {"gg>ggggg": 4, "uu~>ggggg": 4, "uu>uuggg": 2}
 # kernel, from the full-size one-pass ncu capture summarised under profiles/,
 # keyed by (subprocess, stage, threads, events per CTA, grid): a launch in
 # another configuration reports null
-TRAFFIC_BYTES_PER_EVENT = {("gg>ggggg", "amplitudes", 128, 1, 1368): (41.71e9 + 35.25e9) / 2731}
+TRAFFIC_BYTES_PER_EVENT = {("gg>ggggg", "amplitudes", 128, 1, 1368): (41.71e9 + 35.25e9) / 2731,
+                           ("gg>ggggg", "amplitudes", 224, 2, 760): (42.25e9 + 35.25e9) / 2731}
 
 # ---- device-resident workloads (extra keys) ------------------------------------
 WORKLOADS = {
@@ -565,7 +566,7 @@ def run_serve(args):
 
     stream = torch.cuda.current_stream()
     names = [s[0] for s in SERVE_MIX]
-    procs = {name: mea.Process(pdg) for name, pdg, _, _ in SERVE_MIX}
+    procs = {name: mea.Process(pdg, auto_tune=not args.no_autotune) for name, pdg, _, _ in SERVE_MIX}
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     # measured ALU peaks of this GPU (FMA chains), with the SM clock they ran at
@@ -596,7 +597,8 @@ def run_serve(args):
         out = torch.empty(n, dtype=torch.float64, device="cuda")
         fl = torch.empty(n, dtype=torch.uint8, device="cuda")
         k = min(n, 1 << 16)
-        tune[name] = P.autotune(mom[:k], out[:k], precision=mea.PREC_MIXED)
+        if not args.no_autotune:
+            tune[name] = P.autotune(mom[:k], out[:k], precision=mea.PREC_MIXED)
         P.evaluate(mom, out, precision=mea.PREC_MIXED, flags=fl, stream=stream)
         torch.cuda.synchronize()
         P.set_stage_timing(True)

@@ -380,6 +380,7 @@ AmpConfig cached_plan(mea_process_s* P, const DevProgram& dp, bool fp64, bool tc
 bool uses_tensor_path(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode hm) {
   return use_tensor_colour(P, prec, hm);
 }
+int64_t tensor_chunk_events(const mea_process_s* P, int H, int64_t n) { return tc_chunk_events(P, H, n); }
 mea_status evaluate_with(mea_process_s* P, EvalScratch& S, const double* mom, int64_t n, mea_hel_mode hm,
                          const int8_t* hel, mea_prec_mode prec, double* me2, uint8_t* flags, cudaStream_t s) {
   return do_evaluate(P, S, mom, n, hm, hel, prec, me2, flags, s);

@@ -80,10 +80,9 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
     // the tensor-core path runs the amplitude-output interpreter: time that
     dp.gen = nullptr;
     dp.n_colour = 0;
-    // a sample large enough to fill the GPU's resident lanes (its slot traffic
-    // competes for L2 only at that size): up to 4 GB of diagram amplitudes
-    const size_t per_event = (size_t)H * 2 * (size_t)P->jmap.kd * sizeof(float);
-    n = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((size_t(4) << 30) / std::max<size_t>(per_event, 1))));
+    // the sample is one chunk of the size an evaluation of n events launches
+    // (its grid fill and its slot traffic in L2 decide between tiles)
+    n = mea::tensor_chunk_events(P, H, n);
     lda = ((2 * n * H + 127) / 128) * 128;
     if (abuf.ensure(sizeof(float) * (size_t)P->jmap.kd * (size_t)lda) != cudaSuccess ||
         rowmax.ensure(sizeof(float) * 2 * (size_t)H * n) != cudaSuccess ||

@@ -103,6 +103,8 @@ mea_status evaluate_with(mea_process_s* P, EvalScratch& S, const double* mom, in
 // True when evaluations of this precision / helicity mode run the tensor-core
 // path (amplitude-output interpreter + colour-amplitude and colour GEMMs).
 bool uses_tensor_path(const mea_process_s* P, mea_prec_mode prec, mea_hel_mode hm);
+// Events per chunk the tensor-core path launches for an evaluation of n events.
+int64_t tensor_chunk_events(const mea_process_s* P, int H, int64_t n);
 // mea_autotune with the process lock already held.
 mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_prec_mode prec, double* me2,
                            mea_tune_result* out);
