@@ -74,10 +74,10 @@ CPU_SAMPLE = {"gg>ggggg": 16, "uu~>ggggg": 16, "uu>uuggg": 8}
 REF_PER_STEP = {"gg>ggggg": 4, "uu~>ggggg": 4, "uu>uuggg": 2}
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) per event of the dominant
 # kernel, from the full-size one-pass ncu capture summarised under profiles/,
-# keyed by (subprocess, stage, threads, events per CTA, grid): a launch in
-# another configuration reports null
-TRAFFIC_BYTES_PER_EVENT = {("gg>ggggg", "amplitudes", 128, 1, 1368): (41.71e9 + 35.25e9) / 2731,
-                           ("gg>ggggg", "amplitudes", 224, 2, 760): (42.25e9 + 35.25e9) / 2731}
+# keyed by (subprocess, stage, helicity-shared kernel, threads, events per
+# CTA, grid): a launch in another configuration reports null
+TRAFFIC_BYTES_PER_EVENT = {("gg>ggggg", "amplitudes", False, 128, 1, 1368): (41.71e9 + 35.25e9) / 2731,
+                           ("gg>ggggg", "amplitudes", False, 224, 2, 760): (42.25e9 + 35.25e9) / 2731}
 
 # ---- device-resident workloads (extra keys) ------------------------------------
 WORKLOADS = {
@@ -500,7 +500,8 @@ def batch_workload(steps, warmup, scale=1.0, with_fp64=True):
     errs = {}
     for i, (name, *_) in enumerate(BATCH_SPEC):
         errs[name] = {"events": n_ev[i],
-                      "autotune": {k: tune[name][k] for k in ("threads", "events_per_cta", "register_cap")}}
+                      "autotune": {k: tune[name][k] for k in ("threads", "events_per_cta", "register_cap",
+                                                                "helicity_shared")}}
         if with_fp64:
             rel = (res["mixed_out"][i] / res["fp64_out"][i] - 1.0).abs()
             errs[name]["mixed_vs_fp64_rel_err_median"] = float(rel.median())
@@ -525,6 +526,15 @@ def _stage_flops(info, H):
 
 def _cdiv(a, b):
     return -(-a // b)
+
+
+def _helicity_shared(P, tune_result):
+    """Whether the tensor-core path's amplitude stage of P runs the
+    helicity-shared kernel: the tuner's choice, else the heuristic's (the
+    helicity-shared kernel wherever the process has its layout)."""
+    if tune_result:
+        return bool(tune_result.get("helicity_shared", 0))
+    return P.info["hs_variants"] > 0
 
 
 def _jamp_executed_flops(info):
@@ -631,6 +641,7 @@ def run_serve(args):
             "flagged_fraction": float((fl != 0).float().mean()),
             "diagrams": info["n_diagrams"], "colours": info["n_colour"], "helicities": info["n_hel_nonzero"],
             "stage_ms_per_event": {k2: v[0] for k2, v in stage_ms_ev[name].items()},
+            "amplitude_kernel": "helicity-shared" if _helicity_shared(P, tune.get(name)) else "per-lane",
         }
         del mom, out, fl, o64
         torch.cuda.empty_cache()
@@ -649,15 +660,21 @@ def run_serve(args):
         stage_ms_ev[dom_nm][dom_stage][1], 1)
     events_per_launch = SUB_EVENTS[dom_nm] / max(stage_ms_ev[dom_nm][dom_stage][1], 1)
     if dom_stage == "amplitudes":
-        flop = events_per_launch * H * fl_stage["amplitudes"]
-        achieved = flop / (ms_per_launch * 1e-3) / 1e12
         tc = tune.get(dom_nm) or {}
-        tpe = TRAFFIC_BYTES_PER_EVENT.get((dom_nm, dom_stage, tc.get("threads"), tc.get("events_per_cta"),
+        shared = _helicity_shared(procs[dom_nm], tc)
+        # algorithmic FLOPs of the kernel that ran: the helicity-shared one
+        # evaluates each wavefunction once per helicity pattern of its legs
+        per_event = info["hs_flops_per_event"] if shared else H * fl_stage["amplitudes"]
+        flop = events_per_launch * per_event
+        achieved = flop / (ms_per_launch * 1e-3) / 1e12
+        tpe = TRAFFIC_BYTES_PER_EVENT.get((dom_nm, dom_stage, shared, tc.get("threads"), tc.get("events_per_cta"),
                                            tc.get("grid")))
+        kname = "amp_hs_kernel<float> (helicity-shared)" if shared else "amp_kernel<float> amplitude output"
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": achieved / fp32_peak, "traffic": None if tpe is None else tpe * events_per_launch,
-                    "kernel": f"amp_kernel<float> amplitude output ({dom_nm}), {events_per_launch:.0f} events "
+                    "kernel": f"{kname} ({dom_nm}), {events_per_launch:.0f} events "
                               "per launch, CUDA events per launch on its stream",
+                    "flops_per_event": per_event,
                     "peak_note": "measured on this GPU: FMA-chain kernel (mea_measure_alu_peak), "
                                  f"SM clock median {peak_clocks.get('sm_mhz')} MHz",
                     "share_of_mix_device_time": share[(dom_nm, dom_stage)] / tot_share}
@@ -958,7 +975,7 @@ def run_single(args):
     pdg, lo, hi = SINGLE[args.process]
     torch.cuda.set_device(0)
     prec = mea.PREC_FP64 if args.precision == "fp64" else mea.PREC_MIXED
-    P = mea.Process(pdg, auto_tune=not args.no_autotune)
+    P = mea.Process(pdg, auto_tune=not args.no_autotune, helicity_sharing=args.helicity_sharing)
     n = args.events
     # below 2^16 events the evaluation would not tune itself: tune on 2^16
     # events of the same generator, as the serving workload does
@@ -970,7 +987,8 @@ def run_single(args):
     tuned = None
     if tune_here:
         r = P.autotune(mom[:1 << 16], out[:1 << 16], precision=prec)
-        tuned = {k: r[k] for k in ("threads", "events_per_cta", "grid", "slots_in_shared")}
+        tuned = {k: r[k] for k in ("threads", "events_per_cta", "grid", "slots_in_shared", "helicity_shared",
+                                   "register_cap")}
     mom, out = mom[:n], out[:n]
     P.evaluate(mom, out, precision=prec)
     torch.cuda.synchronize()
@@ -998,6 +1016,8 @@ def main():
     ap.add_argument("--process", default="gg5g", choices=sorted(SINGLE), help="single: the subprocess")
     ap.add_argument("--events", type=int, default=4096, help="single: events")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="single: precision")
+    ap.add_argument("--helicity-sharing", type=int, default=0, choices=[0, 1, 2],
+                    help="single: amplitude kernel of the tensor-core path (0 tuned, 1 per-lane, 2 helicity-shared)")
     ap.add_argument("--scale", type=float, default=1.0, help="batch: multiply the configured event counts")
     ap.add_argument("--ref-events", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")

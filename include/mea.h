@@ -109,6 +109,16 @@ typedef struct {
                             even ones the body with one vertex call per diagram (pins
                             the rounding order for reproducible results); other
                             values -> MEA_E_ARG */
+  int helicity_sharing;  /* amplitude stage of the tensor-core path (MEA_PREC_MIXED,
+                            helicity sums): 0 (default) the autotuner and the
+                            heuristic choose between the per-lane interpreter (one
+                            lane per event and helicity combination) and the
+                            helicity-shared kernel (one warp per event; every
+                            off-shell current evaluated once per helicity pattern
+                            of its own legs instead of once per combination, the
+                            same operations on the same inputs); 1 per-lane
+                            interpreter only; 2 helicity-shared kernel only;
+                            other values -> MEA_E_ARG */
 } mea_options;
 
 /* Per-event flag bits written to flags_dev.  An event re-evaluated in FP64
@@ -148,6 +158,13 @@ typedef struct {
   int64_t n_colour_entries;    /* non-zero diagram -> colour-amplitude coefficients c_{alpha d}
                                   of Eq. (color-amplitude) over the accumulated colour
                                   amplitudes; flops_per_hel holds 4 FLOPs for each */
+  int64_t hs_variants;         /* helicity-shared evaluation, per event: wavefunction
+                                  variants evaluated (each produced wavefunction once per
+                                  helicity pattern of its legs); 0 when not available */
+  int hs_arena_variants;       /* its work space per event, in 32-byte FP32 wavefunctions */
+  double hs_flops_per_event;   /* its FLOPs per event for the non-zero helicity sum:
+                                  variants and n_hel_nonzero x diagram amplitudes, each at
+                                  its operation's cost (no colour entries) */
 } mea_process_info_t;
 
 /* ---- process handles ---------------------------------------------------- */
@@ -259,10 +276,14 @@ typedef struct {
   double best_ms;        /* time of the chosen configuration on the sample */
   double default_ms;     /* time of the heuristic default on the sample */
   int register_cap;      /* straight-line kernels: registers per thread of the
-                            chosen variant (128, 85 or 168); 0 for the interpreter */
+                            chosen variant (128, 85 or 168); helicity-shared kernel:
+                            64 for its capped variant, 0 for the uncapped one; 0
+                            for the interpreter */
   int vertex_partials;   /* 1: diagrams sharing a vertex partial use it (always
                             for the interpreter and FP64); 0: the straight-line
                             body with one vertex call per diagram was faster */
+  int helicity_shared;   /* 1: the helicity-shared amplitude kernel was chosen
+                            (threads = 32 x events_per_cta, one warp per event) */
 } mea_tune_result;
 
 mea_status mea_autotune(mea_process_t proc, const double *momenta_dev, int64_t n_sample,

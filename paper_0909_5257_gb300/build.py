@@ -17,9 +17,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmea.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["generator.cpp", "amp_kernel.cu", "ps_kernel.cu", "api.cu", "colour_gemm.cu", "jamp_gemm.cu", "batch.cu",
+SOURCES = ["generator.cpp", "helshare.cpp", "amp_kernel.cu", "amp_hs_kernel.cu", "ps_kernel.cu", "api.cu", "colour_gemm.cu", "jamp_gemm.cu", "batch.cu",
            "server.cu", "peak.cu"]
-HEADERS = ["generator.h", "kernels.h", "colour_gemm.h", "jamp_gemm.h", "tc_common.cuh", "process.h", "heget.cuh", "amp_common.cuh", "gen_kernel.cuh", "codegen.cpp",
+HEADERS = ["generator.h", "helshare.h", "kernels.h", "colour_gemm.h", "jamp_gemm.h", "tc_common.cuh", "process.h", "heget.cuh", "amp_common.cuh", "gen_kernel.cuh", "codegen.cpp",
            "../phasespace/phasespace.h", "../../include/mea.h"]
 # Processes whose straight-line kernels are emitted at build time (live state
 # small enough for registers); every other process runs on the interpreter.

@@ -547,6 +547,16 @@ static int interp_resident(bool fp64, bool jsm, bool ssm, bool aout, int threads
 AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms,
                    size_t max_smem, size_t smem_per_sm, int hint) {
   if (p.gen && hint == 0) return plan_generated(p, fp64, H, n_events, num_sms);
+  if (hint == 0 && hs_supported(p, fp64, H)) {
+    // amplitude output with helicity sharing: each current once per helicity
+    // pattern of its own legs instead of once per lane
+    AmpConfig c = hs_plan(p, H, num_sms, max_smem, smem_per_sm);
+    if (c.grid > 0) {
+      const int64_t tiles = (n_events + c.E_cta - 1) / c.E_cta;
+      if (tiles < c.grid) c.grid = (int)std::max<int64_t>(tiles, 1);
+      return c;
+    }
+  }
   AmpConfig best;
   best.H = H;
   double best_score = -1;
@@ -638,6 +648,10 @@ std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, 
     }
     return out;
   }
+  if (hs_supported(p, fp64, H)) {
+    for (AmpConfig c : hs_candidates(p, H, num_sms, max_smem, smem_per_sm)) out.push_back(cap(c));
+    if (p.hs_only) return out;
+  }
   const int placements[4][2] = {{1, 1}, {1, 0}, {0, 1}, {0, 0}};
   for (auto& pl : placements) {
     if (p.n_colour == 0 && !pl[0]) continue;  // no colour accumulators: one placement axis
@@ -686,6 +700,7 @@ size_t jamp_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig
 }
 
 size_t slot_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig& c) {
+  if (c.helshare) return hs_arena_bytes(p, c);
   if (c.slots_in_smem) return 0;
   return (size_t)c.grid * p.n_slots * 8 * c.threads * (fp64 ? sizeof(double) : sizeof(float));
 }
@@ -718,9 +733,15 @@ static cudaError_t launch_one(const DevProgram& p, const AmpConfig& c, const Amp
 cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const AmpLaunch& a,
                        cudaStream_t s) {
   if (c.grid <= 0) return cudaSuccess;
+  cudaError_t err = cudaSuccess;
+  if (c.helshare) {
+    if (fp64) return cudaErrorInvalidValue;
+    err = launch_amp_hs(p, c, a, s);
+    if (err == cudaSuccess) ++launch_counter();
+    return err;
+  }
   if (c.threads < 32 || c.threads > kMaxThreads || c.E_cta < 1 || c.E_cta * c.H > c.threads)
     return cudaErrorInvalidConfiguration;
-  cudaError_t err = cudaSuccess;
   if (a.amp_out) {
     // diagram amplitudes out (no colour accumulators): FP32 interpreter only
     if (fp64 || p.n_colour != 0) return cudaErrorInvalidValue;

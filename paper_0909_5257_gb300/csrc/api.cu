@@ -433,6 +433,11 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
     destroy(P);
     return fail(MEA_E_ARG, "mea_create_process: kernel_variant out of range");
   }
+  if (opts && (opts->helicity_sharing < 0 || opts->helicity_sharing > 2)) {
+    destroy(P);
+    return fail(MEA_E_ARG, "mea_create_process: helicity_sharing out of range");
+  }
+  P->opts.helicity_sharing = 0;
   if (opts) {
     P->opts.kernel_variant = opts->kernel_variant;
     if (opts->alpha_s > 0) P->opts.alpha_s = opts->alpha_s;
@@ -441,12 +446,19 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
     P->opts.colour_mode = opts->colour_mode;
     P->opts.chunk_events = opts->chunk_events;
     P->opts.auto_tune = opts->auto_tune;
+    P->opts.helicity_sharing = opts->helicity_sharing;
   }
   try {
     P->prog = mea::build_program(std::vector<int>(pdg, pdg + n_ext));
   } catch (std::exception& e) {
     destroy(P);
     return fail(MEA_E_UNSUPPORTED, std::string("mea_create_process: ") + e.what());
+  }
+  try {
+    P->hs = mea::build_helicity_shared(P->prog, P->prog.n_hel);
+    P->hs_ok = true;
+  } catch (std::exception&) {
+    P->hs_ok = false;  // the per-lane interpreter covers the process alone
   }
   const mea::Program& G = P->prog;
   cudaError_t e = cudaGetDevice(&P->device);
@@ -541,6 +553,17 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
       std::vector<__half>().swap(P->jmap.tiles);
     }
   }
+  if (P->hs_ok && P->jmap.ok && P->opts.helicity_sharing != 1) {
+    // helicity-shared layout for the tensor-core path's amplitude stage
+    const mea::HsOp* dhs = nullptr;
+    if ((e = upload(P, P->hs.ops, &dhs)) != cudaSuccess) {
+      destroy(P);
+      return fail(MEA_E_CUDA, std::string("mea_create_process: ") + cudaGetErrorString(e));
+    }
+    D.hs = dhs;
+    D.hs_arena = P->hs.arena;
+    D.hs_only = P->opts.helicity_sharing == 2;
+  }
   *out = P;
   return MEA_OK;
 }
@@ -557,6 +580,12 @@ mea_status mea_create_process_host_only(const int* pdg, int n_ext, const mea_opt
   } catch (std::exception& e) {
     destroy(P);
     return fail(MEA_E_UNSUPPORTED, std::string("mea_create_process_host_only: ") + e.what());
+  }
+  try {
+    P->hs = mea::build_helicity_shared(P->prog, P->prog.n_hel);
+    P->hs_ok = true;
+  } catch (std::exception&) {
+    P->hs_ok = false;
   }
   *out = P;
   return MEA_OK;
@@ -583,6 +612,11 @@ mea_status mea_process_info(mea_process_t P, mea_process_info_t* info) {
   for (const mea::Op& op : G.ops)
     if (mea::is_amp_op(op.type)) nnz += op.col_count;
   info->n_colour_entries = nnz;
+  if (P->hs_ok) {
+    info->hs_variants = P->hs.variants;
+    info->hs_arena_variants = P->hs.arena;
+    info->hs_flops_per_event = P->hs.flops_event;
+  }
   return MEA_OK;
 }
 

@@ -203,7 +203,8 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
         mea::candidate_configs(dp, fp64, H, (int64_t)1 << 40, P->num_sms, P->smem_optin, P->smem_per_sm);
     for (auto& f : full)
       if (f.E_cta == c.E_cta && f.threads == c.threads && f.jamp_in_smem == c.jamp_in_smem &&
-          f.slots_in_smem == c.slots_in_smem && f.regvar == c.regvar && f.per_sm == c.per_sm)
+          f.slots_in_smem == c.slots_in_smem && f.regvar == c.regvar && f.per_sm == c.per_sm &&
+          f.helshare == c.helshare)
         c.grid = f.grid;
     P->tuned[ti] = c;
     P->tuned_H[ti] = H;
@@ -220,8 +221,9 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
     out->candidates = (int)cands.size();
     out->best_ms = best;
     out->default_ms = def_ms;
-    out->register_cap = dp.gen ? (fp64 ? 128 : mea::kGenCapRegisters[c.regvar / 2]) : 0;
+    out->register_cap = dp.gen ? (fp64 ? 128 : mea::kGenCapRegisters[c.regvar / 2]) : ((c.helshare && c.regvar == 0) ? 64 : 0);
     out->vertex_partials = (dp.gen && !fp64 && (c.regvar & 1)) ? 0 : 1;
+    out->helicity_shared = c.helshare ? 1 : 0;
   }
   return MEA_OK;
 }

@@ -841,6 +841,8 @@ double op_cost(const Op& op) { return (op.type == OP_PIOV && op.leg == 2) ? 128 
 
 }  // namespace
 
+double op_flop_cost(const Op& op) { return op_cost(op); }
+
 Program build_program(const std::vector<int>& pdg, const BuildOptions& opt) {
   Program P;
   Builder B;

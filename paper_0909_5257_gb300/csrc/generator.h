@@ -122,4 +122,7 @@ Program build_program(const std::vector<int>& pdg, const BuildOptions& opt = Bui
 // Distinct signed non-zero values of the upper triangle of K (Table 5 count).
 int count_unique_colour_values(const Program& p);
 
+// Algorithmic real-FLOP cost of one operation (colour entries not included).
+double op_flop_cost(const Op& op);
+
 }  // namespace mea

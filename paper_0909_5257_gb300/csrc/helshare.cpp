@@ -1,0 +1,108 @@
+// Helicity-shared layout of a process program (see helshare.h).
+#include "helshare.h"
+
+#include <stdexcept>
+#include <string>
+
+namespace mea {
+
+HsProgram build_helicity_shared(const Program& P, int H) {
+  if (P.n_ext > 8) throw std::runtime_error("helicity sharing: more than 8 legs");
+  const int n_ops = (int)P.ops.size();
+  HsProgram Q;
+  Q.ops.assign(n_ops, HsOp{});
+
+  // Pass 1: the producer (op index) of the value each input reads, the legs
+  // of every produced value and the last op that reads it.
+  std::vector<int> holder(P.n_slots, -1), last_read(n_ops, -1);
+  std::vector<int> src(4 * (size_t)n_ops, -1);
+  std::vector<uint32_t> legs(n_ops, 0);
+  for (int i = 0; i < n_ops; ++i) {
+    const Op& op = P.ops[i];
+    const int n_in = op.type == OP_EXT ? 0 : op.n_in;
+    uint32_t u = 0;
+    for (int k = 0; k < n_in; ++k) {
+      const int s = holder.at(op.in[k]);
+      if (s < 0) throw std::runtime_error("helicity sharing: slot read before it is written");
+      src[4 * (size_t)i + k] = s;
+      last_read[s] = i;
+      u |= legs[s];
+    }
+    if (!is_amp_op(op.type)) {
+      legs[i] = op.type == OP_EXT ? (1u << op.leg) : u;
+      if (op.type != OP_EXT && !is_partial_op(op.type) && legs[i] != P.masks.at(op.mout))
+        throw std::runtime_error("helicity sharing: current legs differ from its momentum row");
+      holder.at(op.out) = i;
+    } else if (u != (1u << P.n_ext) - 1u) {
+      throw std::runtime_error("helicity sharing: amplitude does not cover every leg");
+    }
+  }
+
+  // Pass 2: arena blocks.  Power-of-two sizes, one free list per size; a new
+  // block starts at a multiple of min(size, 4) variants (128 bytes), so that a
+  // warp's accesses to a block are whole cache lines.  An op's output is placed
+  // before the blocks of its last-read inputs are released.
+  std::vector<std::vector<int>> free_list(10);
+  int top = 0;
+  int64_t live = 0;
+  std::vector<int> off(n_ops, -1);
+  double lanes_issued = 0;
+  for (int i = 0; i < n_ops; ++i) {
+    const Op& op = P.ops[i];
+    HsOp& h = Q.ops[i];
+    const int n_in = op.type == OP_EXT ? 0 : op.n_in;
+    for (int k = 0; k < n_in; ++k) {
+      const int s = src[4 * (size_t)i + k];
+      h.in_off[k] = (uint16_t)off[s];
+      h.in_mask[k] = (uint8_t)legs[s];
+    }
+    if (!is_amp_op(op.type)) {
+      const int c = __builtin_popcount(legs[i]);
+      const int nv = 1 << c;
+      int o;
+      if (!free_list[c].empty()) {
+        o = free_list[c].back();
+        free_list[c].pop_back();
+      } else {
+        const int al = nv < 4 ? nv : 4;
+        top = (top + al - 1) / al * al;
+        o = top;
+        top += nv;
+      }
+      if (top > 65535) throw std::runtime_error("helicity sharing: arena beyond 65535 variants");
+      off[i] = o;
+      live += nv;
+      if (live > Q.live_peak) Q.live_peak = live;
+      h.out_off = (uint16_t)o;
+      h.out_mask = (uint8_t)legs[i];
+      Q.variants += nv;
+      Q.lane_copies += H;
+      Q.flops_event += nv * op_flop_cost(op);
+      Q.flops_event_lane += (double)H * op_flop_cost(op);
+      lanes_issued += (double)((nv + 31) / 32 * 32);
+      if (last_read[i] < 0) {  // never read: released at once
+        free_list[c].push_back(o);
+        live -= nv;
+      }
+    } else {
+      Q.amp_lanes += H;
+      Q.flops_event += (double)H * op_flop_cost(op);
+      Q.flops_event_lane += (double)H * op_flop_cost(op);
+    }
+    for (int k = 0; k < n_in; ++k) {
+      const int s = src[4 * (size_t)i + k];
+      bool again = false;  // the same value read twice by this op: release once
+      for (int j = 0; j < k; ++j) again = again || src[4 * (size_t)i + j] == s;
+      if (last_read[s] == i && !again) {
+        const int c = __builtin_popcount(legs[s]);
+        free_list[c].push_back(off[s]);
+        live -= 1 << c;
+      }
+    }
+  }
+  Q.arena = top;
+  Q.lane_use = lanes_issued > 0 ? (double)Q.variants / lanes_issued : 0.0;
+  return Q;
+}
+
+}  // namespace mea

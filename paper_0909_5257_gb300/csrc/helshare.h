@@ -1,0 +1,55 @@
+// Helicity-shared evaluation of a process program.
+//
+// Every wavefunction the program produces (external state, off-shell current,
+// vertex partial) depends on the helicities of the external legs that flow
+// into it and on nothing else of the helicity combination.  The per-lane
+// interpreter evaluates it once per (event, helicity) lane; here it is
+// evaluated once per distinct helicity pattern of its own legs ("variant"):
+// a current of k legs has 2^k variants, however many of the summed
+// helicity combinations share each.  Diagram amplitudes depend on every leg
+// and are still evaluated once per summed combination.  The values are the
+// same operations on the same inputs, so every amplitude is bit-identical to
+// the per-lane interpreter's.
+//
+// Storage: per event, an arena of 32-byte FP32 wavefunction variants.  The
+// produced value of leg set S occupies 2^|S| consecutive variants, variant v
+// holding the helicity pattern whose i-th lowest leg of S has helicity +1
+// exactly when bit i of v is set.  Blocks are allocated in program order and
+// released after their last reader (never before the reading op's own output
+// is placed, so an op's output never overlaps its inputs).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "generator.h"
+
+namespace mea {
+
+// 16-byte record parallel to Program::ops.
+struct HsOp {
+  uint16_t out_off;    // arena offset (variants) of the produced block (slot-producing ops)
+  uint16_t in_off[4];  // arena offsets of the inputs' blocks
+  uint8_t out_mask;    // legs of the produced wavefunction (bit l: leg l)
+  uint8_t in_mask[4];  // legs of each input
+  uint8_t pad;
+};
+static_assert(sizeof(HsOp) == 16, "HsOp must stay 16 bytes");
+
+struct HsProgram {
+  std::vector<HsOp> ops;
+  int arena = 0;              // variants per event (the allocator's high-water mark)
+  int64_t live_peak = 0;      // largest sum of live variants (no fragmentation)
+  int64_t variants = 0;       // variant evaluations of slot-producing ops per event
+  int64_t lane_copies = 0;    // the same ops evaluated once per helicity lane (H x ops)
+  int64_t amp_lanes = 0;      // amplitude evaluations per event (H x diagrams)
+  double flops_event = 0;     // FLOPs per event: variants and amplitude lanes x op cost
+  double flops_event_lane = 0;  // the same for the per-lane interpreter (colour entries excluded)
+  double lane_use = 0;        // variant evaluations / warp lanes issued for them (32-lane warps)
+};
+
+// Builds the helicity-shared layout of P for H summed helicity combinations.
+// Throws std::runtime_error when the process has more than 8 legs or the
+// arena exceeds 65535 variants.
+HsProgram build_helicity_shared(const Program& P, int H);
+
+}  // namespace mea

@@ -12,6 +12,7 @@ namespace mea {
 struct DevProgram;
 struct AmpConfig;
 struct AmpLaunch;
+struct HsOp;
 
 // A straight-line per-process kernel emitted by codegen.cpp at build time.
 struct GenEntry {
@@ -49,6 +50,9 @@ struct DevProgram {
   const GenEntry* gen = nullptr;      // straight-line kernel of this process, if emitted
   int gen_forced = -1;                // FP32 variant pinned by mea_options.kernel_variant (-1: free)
   const float* amp_w = nullptr;       // [n_diagrams] sum_alpha |c_alpha d| (amplitude-output mode)
+  const HsOp* hs = nullptr;           // helicity-shared layout of the program (helshare.h), or null
+  int hs_arena = 0;                   // its variants per event
+  bool hs_only = false;               // amplitude-output mode: plan and tune the helicity-shared kernel only
 };
 
 struct AmpLaunch {
@@ -84,6 +88,9 @@ struct AmpConfig {
   bool slots_in_smem = true;
   int regvar = 0;  // straight-line kernels: variant, 2 * cap + body (see GenEntry)
   int per_sm = 1;  // CTAs meant to be resident per SM (sets the shared-memory carveout)
+  bool helshare = false;  // amplitude-output mode: the helicity-shared kernel (amp_hs_kernel.cu):
+                          // one warp per event, E_cta = warps per CTA, regvar its register
+                          // variant (0: 64 registers, 1: uncapped)
 };
 
 // Shared-memory carveout (percent of the SM's unified L1/shared storage) that
@@ -105,6 +112,15 @@ size_t slot_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig
 
 cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const AmpLaunch& a,
                        cudaStream_t s);
+
+// Helicity-shared amplitude kernel (amp_hs_kernel.cu): amplitude-output mode,
+// FP32, helicity sums of up to 128 combinations, processes of up to 7 legs.
+bool hs_supported(const DevProgram& p, bool fp64, int H);
+size_t hs_smem_bytes(const DevProgram& p, int warps);  // dynamic shared memory of a CTA
+size_t hs_arena_bytes(const DevProgram& p, const AmpConfig& c);  // global variant arena of a launch
+std::vector<AmpConfig> hs_candidates(const DevProgram& p, int H, int num_sms, size_t max_smem, size_t smem_per_sm);
+AmpConfig hs_plan(const DevProgram& p, int H, int num_sms, size_t max_smem, size_t smem_per_sm);  // grid 0: none
+cudaError_t launch_amp_hs(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s);
 
 // Helicity sum + flags for the split colour stage: me2 = 1/4 sum_h pairval.
 // With jabs ([n_splits][n_events*H] sums of |J|), pair_kappa holds sum |c A|

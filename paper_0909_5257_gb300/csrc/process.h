@@ -12,6 +12,7 @@
 
 #include "../../include/mea.h"
 #include "generator.h"
+#include "helshare.h"
 #include "jamp_gemm.h"
 #include "kernels.h"
 
@@ -53,6 +54,8 @@ mea_status set_error(mea_status s, const std::string& msg);
 
 struct mea_process_s {
   mea::Program prog;
+  mea::HsProgram hs;  // helicity-shared layout of prog (valid when hs_ok)
+  bool hs_ok = false;
   mea::DevProgram dev;
   mea_options opts;
   int device = 0;

@@ -37,7 +37,7 @@ class MeaError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("alpha_s", ctypes.c_double), ("flag_threshold", ctypes.c_double),
                 ("reeval_fp64", ctypes.c_int), ("colour_mode", ctypes.c_int), ("chunk_events", ctypes.c_int64),
-                ("auto_tune", ctypes.c_int), ("kernel_variant", ctypes.c_int)]
+                ("auto_tune", ctypes.c_int), ("kernel_variant", ctypes.c_int), ("helicity_sharing", ctypes.c_int)]
 
 
 class ProcessInfo(ctypes.Structure):
@@ -46,14 +46,16 @@ class ProcessInfo(ctypes.Structure):
                 ("n_slots", ctypes.c_int), ("n_colour_amplitudes", ctypes.c_int),
                 ("cf_denominator", ctypes.c_int64), ("cf_max_abs_numerator", ctypes.c_int64),
                 ("flops_per_hel", ctypes.c_double), ("colour_flops_per_hel", ctypes.c_double),
-                ("flops_per_hel_plain", ctypes.c_double), ("n_colour_entries", ctypes.c_int64)]
+                ("flops_per_hel_plain", ctypes.c_double), ("n_colour_entries", ctypes.c_int64),
+                ("hs_variants", ctypes.c_int64), ("hs_arena_variants", ctypes.c_int),
+                ("hs_flops_per_event", ctypes.c_double)]
 
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("events_per_cta", ctypes.c_int), ("grid", ctypes.c_int),
                 ("colour_amps_in_shared", ctypes.c_int), ("slots_in_shared", ctypes.c_int),
                 ("candidates", ctypes.c_int), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
-                ("register_cap", ctypes.c_int), ("vertex_partials", ctypes.c_int)]
+                ("register_cap", ctypes.c_int), ("vertex_partials", ctypes.c_int), ("helicity_shared", ctypes.c_int)]
 
 
 class BatchItem(ctypes.Structure):
@@ -196,13 +198,14 @@ class Process:
     """
 
     def __init__(self, pdg, alpha_s=0.118, flag_threshold=1e-5, reeval_fp64=True,
-                 colour_mode=0, host_only=False, chunk_events=0, auto_tune=True, kernel_variant=0):
+                 colour_mode=0, host_only=False, chunk_events=0, auto_tune=True, kernel_variant=0,
+                 helicity_sharing=0):
         lib = load()
         self.pdg = list(pdg)
         self.n_ext = len(self.pdg)
         arr = (ctypes.c_int * self.n_ext)(*self.pdg)
         opts = Options(alpha_s, flag_threshold, 1 if reeval_fp64 else 0, colour_mode, chunk_events,
-                       1 if auto_tune else 0, kernel_variant)
+                       1 if auto_tune else 0, kernel_variant, helicity_sharing)
         h = ctypes.c_void_p()
         fn = lib.mea_create_process_host_only if host_only else lib.mea_create_process
         _check(fn(arr, self.n_ext, ctypes.byref(opts), ctypes.byref(h)))

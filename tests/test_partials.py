@@ -48,3 +48,30 @@ def test_schedules_compute_the_same_colour_amplitudes(tmp_path):
         assert worst < 1e-13, (name, worst)
     assert int(lines[3 * 3 + 2]) > 0  # gg > gggg shares partials
     assert int(lines[3 * 10 + 2]) == 81 + 225  # gg > ggggg: vvv and gggg groups
+
+
+def test_helicity_shared_layout_gives_the_per_lane_amplitudes(tmp_path):
+    """The helicity-shared layout (helshare.h: every produced wavefunction once
+    per helicity pattern of its own legs, in an arena of variant blocks
+    released after their last reader) gives every diagram amplitude of every
+    summed helicity combination bit for bit as the per-combination evaluation
+    through the program's slots (host, FP64, random inputs); every block lies
+    in the arena and no op's output block overlaps its inputs."""
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path / "helshare_check")
+    subprocess.run([cxx, "-O1", "-std=c++17", "-fopenmp", "-I", CSRC, "-o", exe,
+                    os.path.join(HERE, "native", "helshare_check.cpp"),
+                    os.path.join(CSRC, "generator.cpp"), os.path.join(CSRC, "helshare.cpp")], check=True)
+    procs = ["21,21,21,21", "2,-2,21,21", "21,21,21,21,21", "2,2,2,2,21", "21,21,21,21,21,21",
+             "2,-2,21,21,21,21", "2,2,2,2,21,21", "2,2,2,2,21,21,21", "2,-2,21,21,21,21,21",
+             "21,21,21,21,21,21,21", "2,21,2,21,21", "2,-2,1,-1,21"]
+    r = subprocess.run([exe] + procs, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    rows = [line.split() for line in r.stdout.splitlines()]
+    assert [row[0] for row in rows] == procs
+    for name, compared, mismatched, arena in rows:
+        assert int(compared) > 0 and int(mismatched) == 0, name
+    # g g -> 5g: 112 combinations x 7245 diagrams compared
+    assert int(rows[9][1]) == 112 * 7245
