@@ -111,14 +111,17 @@ typedef struct {
                             values -> MEA_E_ARG */
   int helicity_sharing;  /* amplitude stage of the tensor-core path (MEA_PREC_MIXED,
                             helicity sums): 0 (default) the autotuner and the
-                            heuristic choose between the per-lane interpreter (one
-                            lane per event and helicity combination) and the
+                            heuristic choose among the per-lane interpreter (one
+                            lane per event and helicity combination), the
                             helicity-shared kernel (one warp per event; every
                             off-shell current evaluated once per helicity pattern
-                            of its own legs instead of once per combination, the
-                            same operations on the same inputs); 1 per-lane
-                            interpreter only; 2 helicity-shared kernel only;
-                            other values -> MEA_E_ARG */
+                            of its own legs instead of once per combination) and
+                            the split kernel (the currents of up to n_ext - 3
+                            legs shared that way in a prologue, the rest per
+                            lane); all three apply the same operations to the
+                            same inputs (bit-identical results); 1 per-lane
+                            interpreter only; 2 helicity-shared kernel only; 3
+                            split kernel only; other values -> MEA_E_ARG */
 } mea_options;
 
 /* Per-event flag bits written to flags_dev.  An event re-evaluated in FP64
@@ -165,6 +168,10 @@ typedef struct {
   double hs_flops_per_event;   /* its FLOPs per event for the non-zero helicity sum:
                                   variants and n_hel_nonzero x diagram amplitudes, each at
                                   its operation's cost (no colour entries) */
+  int hsp_area_variants;       /* split evaluation: prologue variants per event (the
+                                  wavefunctions of up to n_ext - 3 legs); 0 when not available */
+  double hsp_flops_per_event;  /* its FLOPs per event: the prologue variants and
+                                  n_hel_nonzero x the per-lane ops, each at its cost */
 } mea_process_info_t;
 
 /* ---- process handles ---------------------------------------------------- */
@@ -283,7 +290,8 @@ typedef struct {
                             for the interpreter and FP64); 0: the straight-line
                             body with one vertex call per diagram was faster */
   int helicity_shared;   /* 1: the helicity-shared amplitude kernel was chosen
-                            (threads = 32 x events_per_cta, one warp per event) */
+                            (threads = 32 x events_per_cta, one warp per event);
+                            2: the split kernel */
 } mea_tune_result;
 
 mea_status mea_autotune(mea_process_t proc, const double *momenta_dev, int64_t n_sample,

@@ -75,9 +75,25 @@ struct HsInputs {
   }
 };
 
+// Split evaluation's per-lane inputs: the prologue variant that lam selects,
+// or the transient current of the previous op (kHsTransient).
+struct HsSplitInputs {
+  const float* area;
+  const uint8_t* pext;
+  int NL;
+  const HsOp& q;
+  uint32_t lam;
+  const W4<float>& tr;
+  __device__ __forceinline__ W4<float> operator()(int k) const {
+    if (q.in_off[k] == kHsTransient) return tr;
+    return ld_var(area, q.in_off[k] + pext[q.in_mask[k] * NL + lam]);
+  }
+};
+
 // The wavefunction a slot-producing op makes (lam: the helicity bits of the
 // variant; external states read their own leg's bit).
-__device__ __forceinline__ W4<float> hs_produce(const Op& op, const DevProgram& P, const HsInputs& x,
+template <class X>
+__device__ __forceinline__ W4<float> hs_produce(const Op& op, const DevProgram& P, const X& x,
                                                 const float* et, const float* mt, float g, float gg) {
   switch (op.type) {
     case OP_EXT: {
@@ -132,7 +148,8 @@ __device__ __forceinline__ W4<float> hs_produce(const Op& op, const DevProgram& 
 }
 
 // The diagram amplitude of an amplitude op.
-__device__ __forceinline__ cx<float> hs_amplitude(const Op& op, const HsInputs& x, const float* mt, float g,
+template <class X>
+__device__ __forceinline__ cx<float> hs_amplitude(const Op& op, const X& x, const float* mt, float g,
                                                   float gg) {
   switch (op.type) {
     case OP_AVVV: {
@@ -307,6 +324,154 @@ void hs_launch(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cuda
   else amp_hs_kernel<4, CAP><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
 }
 
+// Split helicity sharing (helshare.h, build_split_shared): a CTA owns a tile
+// of E events x H helicity lanes, as the per-lane interpreter does.  Per tile:
+// phase 0 the per-event tables (tile_prep); the prologue -- every wavefunction
+// of at most n_ext - 3 legs once per helicity pattern of its legs, for the E
+// events, level by level with one CTA barrier per level (its threads take the
+// (event, op, variant) tasks of a level in turn) -- into the per-event area
+// (shared memory when ASMEM, else the CTA's region of global memory); then
+// each lane runs the rest of the program for its (event, helicity): the
+// currents of n_ext - 2 legs into one register-held transient, read by the
+// next op, and the diagram amplitudes, written out as in the per-lane
+// interpreter's amplitude-output mode.
+template <bool ASMEM>
+__global__ void __launch_bounds__(512) amp_hsp_kernel(const DevProgram P, const AmpLaunch A, const AmpConfig C) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n_ext = P.n_ext, NL = 1 << n_ext, H = C.H, E = C.E_cta;
+  const int t = threadIdx.x, L = blockDim.x;
+  const int tab_stride = event_table_stride(n_ext, P.n_masks);
+  const size_t area_stride = (size_t)P.hsp_area * 8;  // floats per event
+  // shared memory: bit-extraction table [NL][NL], bit-deposit table [NL][NL],
+  // (ASMEM) the areas [E][area][8 reals], per-event tables [E][tab_stride],
+  // input-check bits [E]
+  uint8_t* pext_t = smem;
+  uint8_t* pdep_t = smem + NL * NL;
+  size_t off = ((size_t)2 * NL * NL + 15) & ~size_t(15);
+  float* area_base;
+  if (ASMEM) {
+    area_base = reinterpret_cast<float*>(smem + off);
+    off += (size_t)E * area_stride * sizeof(float);
+  } else {
+    area_base = A.slot_scratch + (size_t)blockIdx.x * E * area_stride;
+  }
+  float* tab = reinterpret_cast<float*>(smem + off);
+  off += (size_t)E * tab_stride * sizeof(float);
+  off = (off + 15) & ~size_t(15);
+  unsigned int* evflag = reinterpret_cast<unsigned int*>(smem + off);
+  for (int i = t; i < NL * NL; i += L) {
+    const uint32_t S = (uint32_t)(i / NL), x = (uint32_t)(i % NL);
+    uint32_t pe = 0, pd = 0;
+    int k = 0;
+    for (int l = 0; l < n_ext; ++l)
+      if (S >> l & 1u) {
+        if (x >> l & 1u) pe |= 1u << k;
+        if (x >> k & 1u) pd |= 1u << l;
+        ++k;
+      }
+    pext_t[i] = (uint8_t)pe;
+    pdep_t[i] = (uint8_t)pd;
+  }
+  for (int i = t; i < E; i += L) evflag[i] = 0u;
+
+  const int e = t / H, h = t - (t / H) * H;  // this lane's (event in tile, helicity)
+  const bool lane_ok = t < E * H;
+  uint32_t lam = 0;
+  if (lane_ok)
+    for (int l = 0; l < n_ext; ++l) {
+      const int8_t v = A.hel_mode == 0 ? P.hel[h * n_ext + l] : P.hel_all[h * n_ext + l];
+      if (v > 0) lam |= 1u << l;
+    }
+  const int64_t n = A.n_events;
+  const int64_t n_tiles = (n + E - 1) / E;
+  const float g = (float)P.g;
+  const float gg = (float)(P.g * P.g);
+  const HsOpWords* all_ops = reinterpret_cast<const HsOpWords*>(P.ops);
+  const int4* all_rec = reinterpret_cast<const int4*>(P.hsp_rec);
+  const HsOpWords* mops = reinterpret_cast<const HsOpWords*>(P.hsp_main_ops);
+  const int4* mrec = reinterpret_cast<const int4*>(P.hsp_main_rec);
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t ev0 = tile * E;
+    const int e_here = (int)((n - ev0 < E) ? (n - ev0) : E);
+    __syncthreads();  // tables filled (first tile) / the previous tile's reads done
+    tile_prep<float>(P, A, tab, tab_stride, ev0, n, E, t, L, evflag);
+    __syncthreads();
+    // ---- prologue, level by level
+    int begin = 0;
+    for (int lv = 0; lv < P.hsp_levels; ++lv) {
+      const int end = P.hsp_level_end[lv];
+      const int nt = end - begin;
+      for (int i = t; i < e_here * nt; i += L) {
+        const int pe = i / nt;
+        const uint32_t task = __ldg(P.hsp_tasks + begin + (i - pe * nt));
+        const int oi = (int)(task >> 8), v = (int)(task & 0xffu);
+        HsOpWords ow;
+        ow.v[0] = __ldg(&all_ops[oi].v[0]);
+        ow.v[1] = __ldg(&all_ops[oi].v[1]);
+        HsRec q;
+        q.v = __ldg(all_rec + oi);
+        float* ar = area_base + (size_t)pe * area_stride;
+        const float* et = tab + (size_t)pe * tab_stride;
+        const HsInputs x{ar, pext_t, NL, q.h, (uint32_t)pdep_t[q.h.out_mask * NL + v]};
+        st_var(ar, q.h.out_off + v, hs_produce(ow.op, P, x, et, et + 8 * n_ext, g, gg));
+      }
+      begin = end;
+      __syncthreads();  // the level's variants are read by every lane from here on
+    }
+    // ---- one (event, helicity) per lane
+    const int64_t ev = ev0 + e;
+    if (lane_ok && e < e_here) {
+      const float* et = tab + (size_t)e * tab_stride;
+      const float* mt = et + 8 * n_ext;
+      const float* ar = area_base + (size_t)e * area_stride;
+      const int64_t pair = ev * H + h;
+      float mx_re = 0.f, mx_im = 0.f, mass = 0.f;
+      bool finite = true;
+      int d_amp = 0;
+      W4<float> tr;
+      for (int k = 0; k < 4; ++k) tr.c[k] = {0.f, 0.f};
+      int4 nx0 = __ldg(&mops[0].v[0]), nx1 = __ldg(&mops[0].v[1]), nxq = __ldg(mrec);
+      for (int i = 0; i < P.hsp_n_main; ++i) {
+        HsOpWords ow;
+        ow.v[0] = nx0;
+        ow.v[1] = nx1;
+        HsRec q;
+        q.v = nxq;
+        if (i + 1 < P.hsp_n_main) {
+          nx0 = __ldg(&mops[i + 1].v[0]);
+          nx1 = __ldg(&mops[i + 1].v[1]);
+          nxq = __ldg(mrec + i + 1);
+        }
+        const Op& op = ow.op;
+        const HsSplitInputs x{ar, pext_t, NL, q.h, lam, tr};
+        if (!hs_is_amp(op.type)) {
+          tr = hs_produce(op, P, x, et, mt, g, gg);
+        } else {
+          const cx<float> amp = hs_amplitude(op, x, mt, g, gg);
+          *reinterpret_cast<float2*>(A.amp_out + (size_t)d_amp * A.lda + 2 * pair) = make_float2(amp.r, amp.i);
+          const float a_r = fabsf(amp.r), a_i = fabsf(amp.i);
+          finite = finite && isfinite(a_r) && isfinite(a_i);
+          mx_re = fmaxf(mx_re, a_r);
+          mx_im = fmaxf(mx_im, a_i);
+          mass += __ldg(P.amp_w + d_amp) * (a_r + a_i);
+          ++d_amp;
+        }
+      }
+      const float nan = __int_as_float(0x7fc00000);
+      A.amp_rowmax[2 * pair] = finite ? mx_re : nan;
+      A.amp_rowmax[2 * pair + 1] = finite ? mx_im : nan;
+      A.pair_kappa[pair] = mass;  // divided by sum |J| after the colour-amplitude stage
+    }
+    __syncthreads();
+    if (t < E) {
+      // the helicity sum runs after the colour stages: hand over the input checks
+      if (t < e_here) A.ev_flags[ev0 + t] = (uint8_t)evflag[t];
+      evflag[t] = 0u;
+    }
+  }
+}
+
 }  // namespace
 
 bool hs_supported(const DevProgram& p, bool fp64, int H) {
@@ -384,6 +549,87 @@ AmpConfig hs_plan(const DevProgram& p, int H, int num_sms, size_t max_smem, size
   AmpConfig none;
   none.grid = 0;
   return none;
+}
+
+// ---- split evaluation (amp_hsp_kernel)
+bool hsp_supported(const DevProgram& p, bool fp64, int H) {
+  return !fp64 && p.hsp_main_ops != nullptr && p.hsp_area > 0 && p.n_colour == 0 && H >= 1 && H <= 512 &&
+         p.n_ext <= 7;
+}
+
+size_t hsp_smem_bytes(const DevProgram& p, int events, bool area_in_smem) {
+  const int NL = 1 << p.n_ext;
+  size_t b = ((size_t)2 * NL * NL + 15) & ~size_t(15);
+  if (area_in_smem) b += (size_t)events * p.hsp_area * 8 * sizeof(float);
+  b += (size_t)events * event_table_stride(p.n_ext, p.n_masks) * sizeof(float);
+  b = (b + 15) & ~size_t(15);
+  return b + (size_t)events * sizeof(unsigned int) + 16;
+}
+
+size_t hsp_area_bytes(const DevProgram& p, const AmpConfig& c) {
+  return c.slots_in_smem ? 0 : (size_t)c.grid * c.E_cta * (size_t)p.hsp_area * 8 * sizeof(float);
+}
+
+std::vector<AmpConfig> hsp_candidates(const DevProgram& p, int H, int num_sms, size_t max_smem,
+                                      size_t smem_per_sm) {
+  std::vector<AmpConfig> out;
+  for (int sm_area = 1; sm_area >= 0; --sm_area) {
+    const void* k = sm_area ? (const void*)amp_hsp_kernel<true> : (const void*)amp_hsp_kernel<false>;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    int last_threads = -1;
+    for (int E = 1; E * H <= 512; ++E) {
+      const int threads = ((E * H + 31) / 32) * 32;
+      // the largest E for each thread count (fewest idle lanes)
+      if ((E + 1) * H <= 512 && (((E + 1) * H + 31) / 32) * 32 == threads) continue;
+      if (threads == last_threads) continue;
+      last_threads = threads;
+      const size_t sm = hsp_smem_bytes(p, E, sm_area != 0);
+      if (sm > max_smem) break;
+      const int warps = threads / 32;
+      const int regs_warp = ((std::max(fa.numRegs, 1) + 7) / 8) * 8 * 32;
+      const int res = std::min({65536 / std::max(regs_warp * warps, 1), (int)(smem_per_sm / (sm + 1024)),
+                                2048 / threads, 32});
+      if (res < 1) continue;
+      int prev = 0;
+      for (int r : {res, res / 2}) {
+        if (r < 1 || r == prev) continue;
+        prev = r;
+        AmpConfig c;
+        c.H = H;
+        c.E_cta = E;
+        c.threads = threads;
+        c.smem = sm;
+        c.jamp_in_smem = true;
+        c.slots_in_smem = sm_area != 0;  // the prologue area in shared memory
+        c.hsplit = true;
+        c.per_sm = r;
+        c.grid = r * num_sms;
+        out.push_back(c);
+      }
+    }
+  }
+  return out;
+}
+
+cudaError_t launch_amp_hsp(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
+  if (!hsp_supported(p, false, c.H) || !a.amp_out || (!c.slots_in_smem && !a.slot_scratch) || a.event_list ||
+      a.hel_mode == 2)
+    return cudaErrorInvalidValue;
+  if (c.threads < 32 || c.threads > 512 || c.threads % 32 != 0 || c.E_cta < 1 || c.E_cta * c.H > c.threads ||
+      c.smem != hsp_smem_bytes(p, c.E_cta, c.slots_in_smem))
+    return cudaErrorInvalidConfiguration;
+  const void* k = c.slots_in_smem ? (const void*)amp_hsp_kernel<true> : (const void*)amp_hsp_kernel<false>;
+  cudaError_t e = ensure_dynamic_smem(k, c.smem);
+  if (e != cudaSuccess) return e;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_percent(c)) != cudaSuccess)
+    cudaGetLastError();
+  if (c.slots_in_smem) amp_hsp_kernel<true><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
+  else amp_hsp_kernel<false><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_amp_hs(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {

@@ -547,6 +547,18 @@ static int interp_resident(bool fp64, bool jsm, bool ssm, bool aout, int threads
 AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int num_sms,
                    size_t max_smem, size_t smem_per_sm, int hint) {
   if (p.gen && hint == 0) return plan_generated(p, fp64, H, n_events, num_sms);
+  if (hint == 0 && p.hsp_only && hsp_supported(p, fp64, H)) {
+    // split evaluation only: the candidate with the most resident lanes
+    std::vector<AmpConfig> cs = hsp_candidates(p, H, num_sms, max_smem, smem_per_sm);
+    if (!cs.empty()) {
+      AmpConfig c = cs.front();
+      for (const AmpConfig& x : cs)
+        if ((int64_t)x.per_sm * x.E_cta > (int64_t)c.per_sm * c.E_cta) c = x;
+      const int64_t tiles = (n_events + c.E_cta - 1) / c.E_cta;
+      if (tiles < c.grid) c.grid = (int)std::max<int64_t>(tiles, 1);
+      return c;
+    }
+  }
   if (hint == 0 && hs_supported(p, fp64, H)) {
     // amplitude output with helicity sharing: each current once per helicity
     // pattern of its own legs instead of once per lane
@@ -652,6 +664,10 @@ std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, 
     for (AmpConfig c : hs_candidates(p, H, num_sms, max_smem, smem_per_sm)) out.push_back(cap(c));
     if (p.hs_only) return out;
   }
+  if (hsp_supported(p, fp64, H)) {
+    for (AmpConfig c : hsp_candidates(p, H, num_sms, max_smem, smem_per_sm)) out.push_back(cap(c));
+    if (p.hsp_only) return out;
+  }
   const int placements[4][2] = {{1, 1}, {1, 0}, {0, 1}, {0, 0}};
   for (auto& pl : placements) {
     if (p.n_colour == 0 && !pl[0]) continue;  // no colour accumulators: one placement axis
@@ -701,6 +717,7 @@ size_t jamp_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig
 
 size_t slot_scratch_bytes_needed(const DevProgram& p, bool fp64, const AmpConfig& c) {
   if (c.helshare) return hs_arena_bytes(p, c);
+  if (c.hsplit) return hsp_area_bytes(p, c);
   if (c.slots_in_smem) return 0;
   return (size_t)c.grid * p.n_slots * 8 * c.threads * (fp64 ? sizeof(double) : sizeof(float));
 }
@@ -734,9 +751,9 @@ cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const
                        cudaStream_t s) {
   if (c.grid <= 0) return cudaSuccess;
   cudaError_t err = cudaSuccess;
-  if (c.helshare) {
+  if (c.helshare || c.hsplit) {
     if (fp64) return cudaErrorInvalidValue;
-    err = launch_amp_hs(p, c, a, s);
+    err = c.helshare ? launch_amp_hs(p, c, a, s) : launch_amp_hsp(p, c, a, s);
     if (err == cudaSuccess) ++launch_counter();
     return err;
   }

@@ -433,7 +433,7 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
     destroy(P);
     return fail(MEA_E_ARG, "mea_create_process: kernel_variant out of range");
   }
-  if (opts && (opts->helicity_sharing < 0 || opts->helicity_sharing > 2)) {
+  if (opts && (opts->helicity_sharing < 0 || opts->helicity_sharing > 3)) {
     destroy(P);
     return fail(MEA_E_ARG, "mea_create_process: helicity_sharing out of range");
   }
@@ -459,6 +459,12 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
     P->hs_ok = true;
   } catch (std::exception&) {
     P->hs_ok = false;  // the per-lane interpreter covers the process alone
+  }
+  try {
+    P->hsp = mea::build_split_shared(P->prog, P->prog.n_hel);
+    P->hsp_ok = P->hsp.levels <= 8 && !P->hsp.main_ops.empty();
+  } catch (std::exception&) {
+    P->hsp_ok = false;
   }
   const mea::Program& G = P->prog;
   cudaError_t e = cudaGetDevice(&P->device);
@@ -553,7 +559,27 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
       std::vector<__half>().swap(P->jmap.tiles);
     }
   }
-  if (P->hs_ok && P->jmap.ok && P->opts.helicity_sharing != 1) {
+  if (P->hsp_ok && P->jmap.ok && (P->opts.helicity_sharing == 0 || P->opts.helicity_sharing == 3)) {
+    // split layout for the tensor-core path's amplitude stage
+    const uint32_t* dt = nullptr;
+    const mea::HsOp *dr = nullptr, *dmr = nullptr;
+    const mea::Op* dmo = nullptr;
+    if ((e = upload(P, P->hsp.tasks, &dt)) != cudaSuccess || (e = upload(P, P->hsp.rec, &dr)) != cudaSuccess ||
+        (e = upload(P, P->hsp.main_ops, &dmo)) != cudaSuccess || (e = upload(P, P->hsp.main_rec, &dmr)) != cudaSuccess) {
+      destroy(P);
+      return fail(MEA_E_CUDA, std::string("mea_create_process: ") + cudaGetErrorString(e));
+    }
+    D.hsp_tasks = dt;
+    D.hsp_rec = dr;
+    D.hsp_main_ops = dmo;
+    D.hsp_main_rec = dmr;
+    D.hsp_n_main = (int)P->hsp.main_ops.size();
+    D.hsp_levels = P->hsp.levels;
+    for (int l = 0; l < P->hsp.levels; ++l) D.hsp_level_end[l] = P->hsp.level_end[l];
+    D.hsp_area = P->hsp.area;
+    D.hsp_only = P->opts.helicity_sharing == 3;
+  }
+  if (P->hs_ok && P->jmap.ok && (P->opts.helicity_sharing == 0 || P->opts.helicity_sharing == 2)) {
     // helicity-shared layout for the tensor-core path's amplitude stage
     const mea::HsOp* dhs = nullptr;
     if ((e = upload(P, P->hs.ops, &dhs)) != cudaSuccess) {
@@ -587,6 +613,12 @@ mea_status mea_create_process_host_only(const int* pdg, int n_ext, const mea_opt
   } catch (std::exception&) {
     P->hs_ok = false;
   }
+  try {
+    P->hsp = mea::build_split_shared(P->prog, P->prog.n_hel);
+    P->hsp_ok = P->hsp.levels <= 8 && !P->hsp.main_ops.empty();
+  } catch (std::exception&) {
+    P->hsp_ok = false;
+  }
   *out = P;
   return MEA_OK;
 }
@@ -616,6 +648,10 @@ mea_status mea_process_info(mea_process_t P, mea_process_info_t* info) {
     info->hs_variants = P->hs.variants;
     info->hs_arena_variants = P->hs.arena;
     info->hs_flops_per_event = P->hs.flops_event;
+  }
+  if (P->hsp_ok) {
+    info->hsp_area_variants = P->hsp.area;
+    info->hsp_flops_per_event = P->hsp.flops_event;
   }
   return MEA_OK;
 }

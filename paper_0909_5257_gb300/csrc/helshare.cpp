@@ -105,4 +105,84 @@ HsProgram build_helicity_shared(const Program& P, int H) {
   return Q;
 }
 
+HsSplitProgram build_split_shared(const Program& P, int H) {
+  if (P.n_ext > 8 || P.n_ext < 5) throw std::runtime_error("split sharing: 5 to 8 legs");
+  const int n_ops = (int)P.ops.size();
+  const int K = P.n_ext - 3;
+  std::vector<int> holder(P.n_slots, -1), last_read(n_ops, -1), reads(n_ops, 0);
+  std::vector<int> src(4 * (size_t)n_ops, -1);
+  std::vector<uint32_t> legs(n_ops, 0);
+  for (int i = 0; i < n_ops; ++i) {
+    const Op& op = P.ops[i];
+    const int n_in = op.type == OP_EXT ? 0 : op.n_in;
+    uint32_t u = 0;
+    for (int k = 0; k < n_in; ++k) {
+      const int s = holder.at(op.in[k]);
+      if (s < 0) throw std::runtime_error("split sharing: slot read before it is written");
+      src[4 * (size_t)i + k] = s;
+      last_read[s] = i;
+      ++reads[s];
+      u |= legs[s];
+    }
+    if (!is_amp_op(op.type)) {
+      legs[i] = op.type == OP_EXT ? (1u << op.leg) : u;
+      holder.at(op.out) = i;
+    }
+  }
+  HsSplitProgram Q;
+  Q.levels = K;
+  Q.rec.assign(n_ops, HsOp{});
+  // prologue values: offsets level by level, in program order within a level
+  std::vector<int> off(n_ops, -1);
+  int top = 0;
+  for (int lv = 1; lv <= K; ++lv) {
+    for (int i = 0; i < n_ops; ++i) {
+      const Op& op = P.ops[i];
+      if (is_amp_op(op.type) || __builtin_popcount(legs[i]) != lv) continue;
+      const int nv = 1 << lv;
+      const int al = nv < 4 ? nv : 4;
+      top = (top + al - 1) / al * al;
+      off[i] = top;
+      top += nv;
+      if (top > 65535) throw std::runtime_error("split sharing: area beyond 65535 variants");
+      for (int v = 0; v < nv; ++v) Q.tasks.push_back((uint32_t)i << 8 | (uint32_t)v);
+      Q.prologue_variants += nv;
+      Q.flops_event += nv * op_flop_cost(op);
+    }
+    Q.level_end.push_back((int)Q.tasks.size());
+  }
+  Q.area = top;
+  for (int i = 0; i < n_ops; ++i) {
+    const Op& op = P.ops[i];
+    const bool amp = is_amp_op(op.type);
+    const bool shared = !amp && __builtin_popcount(legs[i]) <= K;
+    if (!amp && !shared && (reads[i] != 1 || last_read[i] != i + 1))
+      throw std::runtime_error("split sharing: a longer value is not read once by the next op");
+    HsOp& h = Q.rec[i];
+    const int n_in = op.type == OP_EXT ? 0 : op.n_in;
+    int transients = 0;
+    for (int k = 0; k < n_in; ++k) {
+      const int s = src[4 * (size_t)i + k];
+      h.in_mask[k] = (uint8_t)legs[s];
+      if (off[s] >= 0) {
+        h.in_off[k] = (uint16_t)off[s];
+      } else {
+        h.in_off[k] = kHsTransient;
+        ++transients;
+        if (shared) throw std::runtime_error("split sharing: a prologue value reads a transient");
+      }
+    }
+    if (transients > 1) throw std::runtime_error("split sharing: an op reads two transients");
+    if (shared) {
+      h.out_off = (uint16_t)off[i];
+      h.out_mask = (uint8_t)legs[i];
+    } else {
+      Q.main_ops.push_back(op);
+      Q.main_rec.push_back(h);
+      Q.flops_event += (double)H * op_flop_cost(op);
+    }
+  }
+  return Q;
+}
+
 }  // namespace mea

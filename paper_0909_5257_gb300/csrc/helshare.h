@@ -52,4 +52,33 @@ struct HsProgram {
 // arena exceeds 65535 variants.
 HsProgram build_helicity_shared(const Program& P, int H);
 
+// Split evaluation: the wavefunctions of at most n_ext - 3 legs (external
+// states, the shorter currents and vertex partials, which the diagrams share
+// and which stay live over most of the program) are evaluated once per
+// helicity pattern of their legs in a prologue, level by level (level k: the
+// values of k legs, whose inputs all have fewer); the rest of the program --
+// the currents of n_ext - 2 legs, each read once by the very next op, and the
+// diagram amplitudes -- runs once per (event, helicity) lane with that one
+// transient current in registers.  Same operations on the same inputs as the
+// per-lane program: bit-identical amplitudes.
+constexpr uint16_t kHsTransient = 0xFFFFu;  // HsOp::in_off of an input held in registers
+
+struct HsSplitProgram {
+  int area = 0;                    // variants per event of the prologue values
+  int levels = 0;                  // prologue levels (leg counts 1 .. levels)
+  std::vector<uint32_t> tasks;     // prologue: (op index << 8) | variant, level by level
+  std::vector<int> level_end;      // end of each level's tasks
+  std::vector<HsOp> rec;           // per op of the program: prologue ops: output and input blocks;
+                                   //   other ops: input blocks, kHsTransient for the transient
+  std::vector<Op> main_ops;        // the per-lane ops in program order (transient currents, amplitudes)
+  std::vector<HsOp> main_rec;      // their records
+  int64_t prologue_variants = 0;
+  double flops_event = 0;          // per event: prologue variants + H x per-lane ops, each at its cost
+};
+
+// Throws std::runtime_error when the program does not have that structure (a
+// longer value read other than once by the next op) or the area exceeds 65535
+// variants.
+HsSplitProgram build_split_shared(const Program& P, int H);
+
 }  // namespace mea

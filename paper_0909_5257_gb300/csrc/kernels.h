@@ -53,6 +53,16 @@ struct DevProgram {
   const HsOp* hs = nullptr;           // helicity-shared layout of the program (helshare.h), or null
   int hs_arena = 0;                   // its variants per event
   bool hs_only = false;               // amplitude-output mode: plan and tune the helicity-shared kernel only
+  // split evaluation (helshare.h build_split_shared), or null
+  const uint32_t* hsp_tasks = nullptr;  // prologue tasks, level by level
+  int hsp_level_end[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int hsp_levels = 0;
+  const HsOp* hsp_rec = nullptr;        // [n_ops] records of the whole program
+  const Op* hsp_main_ops = nullptr;     // the per-lane ops
+  const HsOp* hsp_main_rec = nullptr;
+  int hsp_n_main = 0;
+  int hsp_area = 0;                     // prologue variants per event
+  bool hsp_only = false;                // amplitude-output mode: plan and tune the split kernel only
 };
 
 struct AmpLaunch {
@@ -88,6 +98,8 @@ struct AmpConfig {
   bool slots_in_smem = true;
   int regvar = 0;  // straight-line kernels: variant, 2 * cap + body (see GenEntry)
   int per_sm = 1;  // CTAs meant to be resident per SM (sets the shared-memory carveout)
+  bool hsplit = false;    // amplitude-output mode: the split kernel (amp_hsp_kernel, amp_hs_kernel.cu):
+                          // E_cta events x H lanes; slots_in_smem = its prologue area in shared memory
   bool helshare = false;  // amplitude-output mode: the helicity-shared kernel (amp_hs_kernel.cu):
                           // one warp per event, E_cta = warps per CTA, regvar its register
                           // variant (0: 64 registers, 1: uncapped)
@@ -121,6 +133,12 @@ size_t hs_arena_bytes(const DevProgram& p, const AmpConfig& c);  // global varia
 std::vector<AmpConfig> hs_candidates(const DevProgram& p, int H, int num_sms, size_t max_smem, size_t smem_per_sm);
 AmpConfig hs_plan(const DevProgram& p, int H, int num_sms, size_t max_smem, size_t smem_per_sm);  // grid 0: none
 cudaError_t launch_amp_hs(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s);
+// Split kernel: prologue of shared short wavefunctions, the rest per lane.
+bool hsp_supported(const DevProgram& p, bool fp64, int H);
+size_t hsp_smem_bytes(const DevProgram& p, int events, bool area_in_smem);
+size_t hsp_area_bytes(const DevProgram& p, const AmpConfig& c);
+std::vector<AmpConfig> hsp_candidates(const DevProgram& p, int H, int num_sms, size_t max_smem, size_t smem_per_sm);
+cudaError_t launch_amp_hsp(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s);
 
 // Helicity sum + flags for the split colour stage: me2 = 1/4 sum_h pairval.
 // With jabs ([n_splits][n_events*H] sums of |J|), pair_kappa holds sum |c A|

@@ -56,6 +56,8 @@ struct mea_process_s {
   mea::Program prog;
   mea::HsProgram hs;  // helicity-shared layout of prog (valid when hs_ok)
   bool hs_ok = false;
+  mea::HsSplitProgram hsp;  // split layout of prog (valid when hsp_ok)
+  bool hsp_ok = false;
   mea::DevProgram dev;
   mea_options opts;
   int device = 0;

@@ -48,7 +48,8 @@ class ProcessInfo(ctypes.Structure):
                 ("flops_per_hel", ctypes.c_double), ("colour_flops_per_hel", ctypes.c_double),
                 ("flops_per_hel_plain", ctypes.c_double), ("n_colour_entries", ctypes.c_int64),
                 ("hs_variants", ctypes.c_int64), ("hs_arena_variants", ctypes.c_int),
-                ("hs_flops_per_event", ctypes.c_double)]
+                ("hs_flops_per_event", ctypes.c_double), ("hsp_area_variants", ctypes.c_int),
+                ("hsp_flops_per_event", ctypes.c_double)]
 
 
 class TuneResult(ctypes.Structure):

@@ -9,8 +9,12 @@
 // live blocks, a wrong leg set or a wrong bit extraction changes some
 // amplitude.  Inputs are random: external wavefunctions per (leg, helicity),
 // leg momenta and the mask rows formed from them.  Also checks that every
-// block lies inside the arena.  Prints per process: name, amplitudes
-// compared, mismatches, arena variants; exit status 1 on any mismatch.
+// block lies inside the arena.  The split layout (prologue values once per
+// helicity pattern, level by level; the rest per combination with one
+// transient current) is checked the same way.  Prints per process: name,
+// amplitudes compared, mismatches, arena variants, and the same for the split
+// layout (area variants; -1 for processes of 4 legs); exit status 1 on any
+// mismatch.
 #define MEA_HD inline
 #include <cmath>
 #include <cstdint>
@@ -181,8 +185,52 @@ int main(int argc, char** argv) {
         ++d;
       }
     }
-    if (mismatched) bad = 1;
-    std::printf("%s %lld %lld %d\n", argv[a], (long long)compared, (long long)mismatched, Q.arena);
+    // split: prologue values once per helicity pattern, level by level; the
+    // rest per combination with the transient current held aside
+    int64_t split_compared = 0, split_mismatched = 0;
+    int split_area = -1;
+    if (P.n_ext >= 5) {
+      const HsSplitProgram S = build_split_shared(P, P.n_hel);
+      split_area = S.area;
+      std::vector<W4<double>> area(S.area);
+      for (size_t t = 0; t < S.tasks.size(); ++t) {
+        const int i = (int)(S.tasks[t] >> 8), v = (int)(S.tasks[t] & 0xffu);
+        const Op& op = P.ops[i];
+        const HsOp& q = S.rec[i];
+        const uint32_t lf = pdep((uint32_t)v, q.out_mask);
+        W4<double> x[4];
+        const int n_in = op.type == OP_EXT ? 0 : op.n_in;
+        for (int k = 0; k < n_in; ++k) {
+          if (q.in_off[k] == kHsTransient) { std::printf("prologue input is transient\n"); bad = 1; continue; }
+          x[k] = area[q.in_off[k] + pext(lf, q.in_mask[k])];
+        }
+        if (q.out_off + (1 << __builtin_popcount(q.out_mask)) > S.area) { std::printf("prologue block outside\n"); bad = 1; continue; }
+        area[q.out_off + v] = produce(op, x, in, lf);
+      }
+      for (int h = 0; h < P.n_hel; ++h) {
+        W4<double> tr;
+        int dd = 0;
+        for (size_t j = 0; j < S.main_ops.size(); ++j) {
+          const Op& op = S.main_ops[j];
+          const HsOp& q = S.main_rec[j];
+          W4<double> x[4];
+          for (int k = 0; k < op.n_in; ++k)
+            x[k] = q.in_off[k] == kHsTransient ? tr : area[q.in_off[k] + pext(lam[h], q.in_mask[k])];
+          if (is_amp_op(op.type)) {
+            const cx<double> z = amplitude(op, x, in);
+            const cx<double>& r = ref[(size_t)h * P.n_diagrams + dd++];
+            ++split_compared;
+            if (std::memcmp(&z, &r, sizeof(z)) != 0) ++split_mismatched;
+          } else {
+            tr = produce(op, x, in, lam[h]);
+          }
+        }
+        if (dd != P.n_diagrams) { std::printf("split: %d amplitudes, %d diagrams\n", dd, P.n_diagrams); bad = 1; }
+      }
+    }
+    if (mismatched || split_mismatched) bad = 1;
+    std::printf("%s %lld %lld %d %lld %lld %d\n", argv[a], (long long)compared, (long long)mismatched, Q.arena,
+                (long long)split_compared, (long long)split_mismatched, split_area);
   }
   return bad;
 }

@@ -110,7 +110,7 @@ def test_kernel_variant_out_of_range_is_an_argument_error():
 def test_helicity_sharing_option_out_of_range_is_an_argument_error():
     """mea_options.helicity_sharing is checked before any device work."""
     from paper_0909_5257_gb300 import mea
-    for v in (-1, 3):
+    for v in (-1, 4):
         with pytest.raises(mea.MeaError) as e:
             mea.Process([21] * 6, helicity_sharing=v)
         assert e.value.status == -1
@@ -128,6 +128,10 @@ def test_helicity_shared_evaluation_counts():
     assert 2.1 < per_lane / info["hs_flops_per_event"] < 2.4
     small = mea.Process([2, 2, 2, 2, 21, 21, 21], host_only=True).info
     assert 0 < small["hs_variants"] < small["n_hel_nonzero"] * small["n_ops"]
+    # split evaluation: the wavefunctions of up to 4 legs in a prologue area of
+    # 16 180 variants per event, the rest per lane
+    assert info["hsp_area_variants"] == 16180
+    assert info["hs_flops_per_event"] < info["hsp_flops_per_event"] < per_lane
 
 
 def test_vertex_partials_reduce_the_flop_count():

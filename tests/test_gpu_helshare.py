@@ -2,10 +2,13 @@
 
 On the tensor-core path (mixed precision, processes without a straight-line
 kernel) the amplitude stage can run as the per-lane interpreter (one lane per
-event and helicity combination) or as the helicity-shared kernel (one warp per
+event and helicity combination), as the helicity-shared kernel (one warp per
 event, every wavefunction evaluated once per helicity pattern of its own
-legs).  Both apply the same HELAS operations to the same inputs, so every
-diagram amplitude, and with it |M|^2 and the flags, is the same bit for bit:
+legs) or as the split kernel (the wavefunctions of up to n_ext - 3 legs
+shared that way in a prologue, the rest per lane with one transient current
+in registers).  All apply the same HELAS operations to the same inputs, so
+every diagram amplitude, and with it |M|^2 and the flags, is the same bit for
+bit:
 checked here for the serving processes and g g -> 4g, for the non-zero and
 the full helicity sums, across several chunks with a ragged tail and after
 autotuning.  Parity with the oracle of the default (helicity-shared) path is
@@ -55,12 +58,29 @@ def test_helicity_shared_equals_per_lane_bit_for_bit(name, pdg, rs, n, chunk):
     mea = _mea()
     mom = _events(pdg, rs, n, ps.SEED_BASE + 611)
     lane = mea.Process(pdg, helicity_sharing=1, auto_tune=False, chunk_events=chunk)
-    shared = mea.Process(pdg, helicity_sharing=2, auto_tune=False, chunk_events=chunk)
     a, fa = _run(lane, mom)
-    b, fb = _run(shared, mom)
     assert torch.isfinite(a).all()
-    assert torch.equal(a, b), (name, float(((a - b).abs() / a.abs()).max()))
-    assert torch.equal(fa, fb)
+    for mode in (2, 3):
+        other = mea.Process(pdg, helicity_sharing=mode, auto_tune=False, chunk_events=chunk)
+        b, fb = _run(other, mom)
+        assert torch.equal(a, b), (name, mode, float(((a - b).abs() / a.abs()).max()))
+        assert torch.equal(fa, fb), (name, mode)
+
+
+@pytest.mark.parametrize("name,pdg,rs,n,chunk", CASES[:3])
+def test_split_kernel_every_candidate_shape(name, pdg, rs, n, chunk):
+    """Tuned split kernel (shared-memory and global prologue areas, several
+    tile shapes timed): its choice equals the per-lane kernel bit for bit."""
+    mea = _mea()
+    mom = _events(pdg, rs, n, ps.SEED_BASE + 614)
+    lane = mea.Process(pdg, helicity_sharing=1, auto_tune=False, chunk_events=chunk)
+    a, _ = _run(lane, mom)
+    P = mea.Process(pdg, helicity_sharing=3, auto_tune=False, chunk_events=chunk)
+    scratch = torch.empty(n, dtype=torch.float64, device="cuda")
+    r = P.autotune(mom, scratch, precision=mea.PREC_MIXED)
+    assert r["helicity_shared"] == 2 and r["candidates"] >= 2
+    b, _ = _run(P, mom)
+    assert torch.equal(a, b), r
 
 
 def test_helicity_shared_full_helicity_sum():
@@ -69,12 +89,13 @@ def test_helicity_shared_full_helicity_sum():
     pdg = [21] * 6
     mom = _events(pdg, (300.0, 3000.0), 333, ps.SEED_BASE + 612)
     lane = mea.Process(pdg, helicity_sharing=1, auto_tune=False)
-    shared = mea.Process(pdg, helicity_sharing=2, auto_tune=False)
     a, _ = _run(lane, mom, hel_mode=mea.HEL_SUM_ALL)
-    b, _ = _run(shared, mom, hel_mode=mea.HEL_SUM_ALL)
-    assert torch.equal(a, b)
-    c, _ = _run(shared, mom)
-    assert torch.allclose(b, c, rtol=1e-6, atol=0)
+    for mode in (2, 3):
+        shared = mea.Process(pdg, helicity_sharing=mode, auto_tune=False)
+        b, _ = _run(shared, mom, hel_mode=mea.HEL_SUM_ALL)
+        assert torch.equal(a, b), mode
+        c, _ = _run(shared, mom)
+        assert torch.allclose(b, c, rtol=1e-6, atol=0)
 
 
 @pytest.mark.parametrize("pdg,rs", [([21] * 6, (300.0, 3000.0)), ([2, -2] + [21] * 5, (500.0, 5000.0))])

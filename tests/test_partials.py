@@ -53,10 +53,13 @@ def test_schedules_compute_the_same_colour_amplitudes(tmp_path):
 def test_helicity_shared_layout_gives_the_per_lane_amplitudes(tmp_path):
     """The helicity-shared layout (helshare.h: every produced wavefunction once
     per helicity pattern of its own legs, in an arena of variant blocks
-    released after their last reader) gives every diagram amplitude of every
-    summed helicity combination bit for bit as the per-combination evaluation
-    through the program's slots (host, FP64, random inputs); every block lies
-    in the arena and no op's output block overlaps its inputs."""
+    released after their last reader) and the split layout (the wavefunctions
+    of up to n_ext - 3 legs shared that way in a prologue, level by level, the
+    rest per combination with one transient current) give every diagram
+    amplitude of every summed helicity combination bit for bit as the
+    per-combination evaluation through the program's slots (host, FP64, random
+    inputs); every block lies in its arena and no op's output block overlaps
+    its inputs."""
     cxx = shutil.which("g++")
     if cxx is None:
         pytest.skip("no host C++ compiler")
@@ -71,7 +74,10 @@ def test_helicity_shared_layout_gives_the_per_lane_amplitudes(tmp_path):
     assert r.returncode == 0, r.stdout + r.stderr
     rows = [line.split() for line in r.stdout.splitlines()]
     assert [row[0] for row in rows] == procs
-    for name, compared, mismatched, arena in rows:
+    for name, compared, mismatched, arena, s_compared, s_mismatched, s_area in rows:
         assert int(compared) > 0 and int(mismatched) == 0, name
-    # g g -> 5g: 112 combinations x 7245 diagrams compared
-    assert int(rows[9][1]) == 112 * 7245
+        if len(name.split(",")) >= 5:
+            assert int(s_compared) == int(compared) and int(s_mismatched) == 0, name
+    # g g -> 5g: 112 combinations x 7245 diagrams compared; prologue area of
+    # the wavefunctions of up to 4 legs
+    assert int(rows[9][1]) == 112 * 7245 and int(rows[9][6]) == 16180
