@@ -1016,8 +1016,9 @@ def main():
     ap.add_argument("--process", default="gg5g", choices=sorted(SINGLE), help="single: the subprocess")
     ap.add_argument("--events", type=int, default=4096, help="single: events")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="single: precision")
-    ap.add_argument("--helicity-sharing", type=int, default=0, choices=[0, 1, 2],
-                    help="single: amplitude kernel of the tensor-core path (0 tuned, 1 per-lane, 2 helicity-shared)")
+    ap.add_argument("--helicity-sharing", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="single: amplitude kernel of the tensor-core path (0 tuned, 1 per-lane, 2 helicity-shared, "
+                         "3 split)")
     ap.add_argument("--scale", type=float, default=1.0, help="batch: multiply the configured event counts")
     ap.add_argument("--ref-events", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
