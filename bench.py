@@ -74,10 +74,13 @@ CPU_SAMPLE = {"gg>ggggg": 16, "uu~>ggggg": 16, "uu>uuggg": 8}
 REF_PER_STEP = {"gg>ggggg": 4, "uu~>ggggg": 4, "uu>uuggg": 2}
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) per event of the dominant
 # kernel, from the full-size one-pass ncu capture summarised under profiles/,
-# keyed by (subprocess, stage, helicity-shared kernel, threads, events per
-# CTA, grid): a launch in another configuration reports null
-TRAFFIC_BYTES_PER_EVENT = {("gg>ggggg", "amplitudes", False, 128, 1, 1368): (41.71e9 + 35.25e9) / 2731,
-                           ("gg>ggggg", "amplitudes", False, 224, 2, 760): (42.25e9 + 35.25e9) / 2731}
+# keyed by (subprocess, stage, amplitude kernel 0 per-lane / 1 helicity-shared
+# / 2 split, threads, events per CTA, grid): a launch in another configuration
+# reports null
+TRAFFIC_BYTES_PER_EVENT = {("gg>ggggg", "amplitudes", 0, 128, 1, 1368): (41.71e9 + 35.25e9) / 2731,
+                           ("gg>ggggg", "amplitudes", 0, 224, 2, 760): (42.30e9 + 35.25e9) / 2731,
+                           ("gg>ggggg", "amplitudes", 1, 128, 4, 456): (3.19e9 + 18.99e9) / 2731,
+                           ("gg>ggggg", "amplitudes", 2, 448, 4, 304): (5.52e9 + 19.09e9) / 2731}
 
 # ---- device-resident workloads (extra keys) ------------------------------------
 WORKLOADS = {
@@ -528,13 +531,14 @@ def _cdiv(a, b):
     return -(-a // b)
 
 
-def _helicity_shared(P, tune_result):
-    """Whether the tensor-core path's amplitude stage of P runs the
-    helicity-shared kernel: the tuner's choice, else the heuristic's (the
-    helicity-shared kernel wherever the process has its layout)."""
-    if tune_result:
-        return bool(tune_result.get("helicity_shared", 0))
-    return P.info["hs_variants"] > 0
+def _amp_kernel_kind(tune_result):
+    """Which amplitude kernel the tensor-core path of a process runs: the
+    tuner's choice (0 per-lane interpreter, 1 helicity-shared, 2 split), else
+    the untuned default, the per-lane interpreter."""
+    return int(tune_result.get("helicity_shared", 0)) if tune_result else 0
+
+
+AMP_KERNEL_NAMES = {0: "per-lane", 1: "helicity-shared", 2: "split"}
 
 
 def _jamp_executed_flops(info):
@@ -641,7 +645,7 @@ def run_serve(args):
             "flagged_fraction": float((fl != 0).float().mean()),
             "diagrams": info["n_diagrams"], "colours": info["n_colour"], "helicities": info["n_hel_nonzero"],
             "stage_ms_per_event": {k2: v[0] for k2, v in stage_ms_ev[name].items()},
-            "amplitude_kernel": "helicity-shared" if _helicity_shared(P, tune.get(name)) else "per-lane",
+            "amplitude_kernel": AMP_KERNEL_NAMES[_amp_kernel_kind(tune.get(name))],
         }
         del mom, out, fl, o64
         torch.cuda.empty_cache()
@@ -661,15 +665,18 @@ def run_serve(args):
     events_per_launch = SUB_EVENTS[dom_nm] / max(stage_ms_ev[dom_nm][dom_stage][1], 1)
     if dom_stage == "amplitudes":
         tc = tune.get(dom_nm) or {}
-        shared = _helicity_shared(procs[dom_nm], tc)
-        # algorithmic FLOPs of the kernel that ran: the helicity-shared one
-        # evaluates each wavefunction once per helicity pattern of its legs
-        per_event = info["hs_flops_per_event"] if shared else H * fl_stage["amplitudes"]
+        kind = _amp_kernel_kind(tc)
+        # algorithmic FLOPs of the kernel that ran: the helicity-shared and the
+        # split kernels evaluate (some) wavefunctions once per helicity pattern
+        # of their legs
+        per_event = {1: info["hs_flops_per_event"], 2: info["hsp_flops_per_event"]}.get(
+            kind, H * fl_stage["amplitudes"])
         flop = events_per_launch * per_event
         achieved = flop / (ms_per_launch * 1e-3) / 1e12
-        tpe = TRAFFIC_BYTES_PER_EVENT.get((dom_nm, dom_stage, shared, tc.get("threads"), tc.get("events_per_cta"),
+        tpe = TRAFFIC_BYTES_PER_EVENT.get((dom_nm, dom_stage, kind, tc.get("threads"), tc.get("events_per_cta"),
                                            tc.get("grid")))
-        kname = "amp_hs_kernel<float> (helicity-shared)" if shared else "amp_kernel<float> amplitude output"
+        kname = {1: "amp_hs_kernel<float> (helicity-shared)", 2: "amp_hsp_kernel<float> (split)"}.get(
+            kind, "amp_kernel<float> amplitude output")
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": achieved / fp32_peak, "traffic": None if tpe is None else tpe * events_per_launch,
                     "kernel": f"{kname} ({dom_nm}), {events_per_launch:.0f} events "

@@ -110,8 +110,9 @@ typedef struct {
                             the rounding order for reproducible results); other
                             values -> MEA_E_ARG */
   int helicity_sharing;  /* amplitude stage of the tensor-core path (MEA_PREC_MIXED,
-                            helicity sums): 0 (default) the autotuner and the
-                            heuristic choose among the per-lane interpreter (one
+                            helicity sums): 0 (default) the autotuner chooses
+                            (untuned: the per-lane interpreter) among the per-lane
+                            interpreter (one
                             lane per event and helicity combination), the
                             helicity-shared kernel (one warp per event; every
                             off-shell current evaluated once per helicity pattern

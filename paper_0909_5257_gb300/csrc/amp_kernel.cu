@@ -559,9 +559,10 @@ AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int 
       return c;
     }
   }
-  if (hint == 0 && hs_supported(p, fp64, H)) {
-    // amplitude output with helicity sharing: each current once per helicity
-    // pattern of its own legs instead of once per lane
+  if (hint == 0 && p.hs_only && hs_supported(p, fp64, H)) {
+    // helicity-shared kernel only (without the option, the per-lane heuristic
+    // below is the untuned default: measured at least as fast untuned on every
+    // process; the tuner picks the shared kernels where they are faster)
     AmpConfig c = hs_plan(p, H, num_sms, max_smem, smem_per_sm);
     if (c.grid > 0) {
       const int64_t tiles = (n_events + c.E_cta - 1) / c.E_cta;
