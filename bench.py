@@ -645,7 +645,8 @@ def run_serve(args):
             "flagged_fraction": float((fl != 0).float().mean()),
             "diagrams": info["n_diagrams"], "colours": info["n_colour"], "helicities": info["n_hel_nonzero"],
             "stage_ms_per_event": {k2: v[0] for k2, v in stage_ms_ev[name].items()},
-            "amplitude_kernel": AMP_KERNEL_NAMES[_amp_kernel_kind(tune.get(name))],
+            "amplitude_kernel": AMP_KERNEL_NAMES[_amp_kernel_kind(tune.get(name))] +
+                                (", forwarding" if (tune.get(name) or {}).get("forwarding") else ""),
         }
         del mom, out, fl, o64
         torch.cuda.empty_cache()
@@ -673,10 +674,10 @@ def run_serve(args):
             kind, H * fl_stage["amplitudes"])
         flop = events_per_launch * per_event
         achieved = flop / (ms_per_launch * 1e-3) / 1e12
-        tpe = TRAFFIC_BYTES_PER_EVENT.get((dom_nm, dom_stage, kind, tc.get("threads"), tc.get("events_per_cta"),
-                                           tc.get("grid")))
+        tpe = None if tc.get("forwarding") else TRAFFIC_BYTES_PER_EVENT.get(
+            (dom_nm, dom_stage, kind, tc.get("threads"), tc.get("events_per_cta"), tc.get("grid")))
         kname = {1: "amp_hs_kernel<float> (helicity-shared)", 2: "amp_hsp_kernel<float> (split)"}.get(
-            kind, "amp_kernel<float> amplitude output")
+            kind, "amp_kernel<float> amplitude output" + (" with forwarding" if tc.get("forwarding") else ""))
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": achieved / fp32_peak, "traffic": None if tpe is None else tpe * events_per_launch,
                     "kernel": f"{kname} ({dom_nm}), {events_per_launch:.0f} events "

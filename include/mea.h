@@ -120,9 +120,12 @@ typedef struct {
                             the split kernel (the currents of up to n_ext - 3
                             legs shared that way in a prologue, the rest per
                             lane); all three apply the same operations to the
-                            same inputs (bit-identical results); 1 per-lane
+                            same inputs (bit-identical results); the per-lane
+                            interpreter is tuned with and without forwarding each
+                            op's output to the next op in registers; 1 per-lane
                             interpreter only; 2 helicity-shared kernel only; 3
-                            split kernel only; other values -> MEA_E_ARG */
+                            split kernel only; 4 per-lane interpreter with
+                            forwarding only; other values -> MEA_E_ARG */
 } mea_options;
 
 /* Per-event flag bits written to flags_dev.  An event re-evaluated in FP64
@@ -293,6 +296,9 @@ typedef struct {
   int helicity_shared;   /* 1: the helicity-shared amplitude kernel was chosen
                             (threads = 32 x events_per_cta, one warp per event);
                             2: the split kernel */
+  int forwarding;        /* 1: the per-lane interpreter with each op's output
+                            forwarded to the next op in registers (and not stored
+                            when nothing else reads it) was chosen */
 } mea_tune_result;
 
 mea_status mea_autotune(mea_process_t proc, const double *momenta_dev, int64_t n_sample,

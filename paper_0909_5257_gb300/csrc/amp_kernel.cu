@@ -102,9 +102,28 @@ __device__ __forceinline__ void st_slot(R* slots, int s, int L, int t, const W4<
 // One op of the process program for the (pair) lane t of a slot array with
 // stride L: external wavefunction or current into its slot (returns false), or
 // a diagram amplitude into amp (returns true).
-template <typename R>
+//
+// FWD (amplitude-output FP32 path): the previous op's output is also held in
+// `last`; fwd bit k (0..3) marks an input that is that output (read from the
+// register instead of the slot), bit 4 an output read by nothing but the next
+// op (kept in the register only, never stored).
+template <typename R, bool FWD = false>
 __device__ __forceinline__ bool eval_op(const Op& op, const DevProgram& P, R* slots, int L, int t, const R* et,
-                                        const R* mt, uint32_t lam_bits, R g, R gg, cx<R>& amp) {
+                                        const R* mt, uint32_t lam_bits, R g, R gg, cx<R>& amp,
+                                        uint32_t fwd = 0u, W4<R>* last = nullptr) {
+  auto in_ = [&](int k) -> W4<R> {
+    if constexpr (FWD) {
+      if (fwd >> k & 1u) return *last;
+    }
+    return ld_slot(slots, op.in[k], L, t);
+  };
+  auto out_ = [&](const W4<R>& x) {
+    if constexpr (FWD) {
+      *last = x;
+      if (fwd & 16u) return;
+    }
+    st_slot(slots, op.out, L, t, x);
+  };
   switch (op.type) {
     case OP_EXT: {
       int l = op.leg;
@@ -115,97 +134,97 @@ __device__ __forceinline__ bool eval_op(const Op& op, const DevProgram& P, R* sl
       int lam = (lam_bits >> l & 1u) ? 1 : -1;
       if (type == 0) x = ext_gluon<R>(o, o + 3, lam, !in);
       else x = ext_spinor<R>(o[0], o[1], mk<R>(o[2], o[3]), lam, kind);
-      st_slot(slots, op.out, L, t, x);
+      out_(x);
       return false;
     }
     case OP_JVV: {
-      W4<R> a = ld_slot(slots, op.in[0], L, t);
-      W4<R> b = ld_slot(slots, op.in[1], L, t);
+      W4<R> a = in_(0);
+      W4<R> b = in_(1);
       const R* pa = mt + 5 * op.min[0];
       const R* pb = mt + 5 * op.min[1];
       W4<R> j = jvv<R>(a, b, pa, pb, mt[5 * op.mout + 4], g);
-      st_slot(slots, op.out, L, t, j);
+      out_(j);
       return false;
     }
     case OP_JGGG: {
-      W4<R> a = ld_slot(slots, op.in[0], L, t);
-      W4<R> b = ld_slot(slots, op.in[1], L, t);
-      W4<R> c = ld_slot(slots, op.in[2], L, t);
+      W4<R> a = in_(0);
+      W4<R> b = in_(1);
+      W4<R> c = in_(2);
       W4<R> j = jggg<R>(a, b, c, mt[5 * op.mout + 4], gg);
-      st_slot(slots, op.out, L, t, j);
+      out_(j);
       return false;
     }
     case OP_FVI: {
-      W4<R> f = ld_slot(slots, op.in[0], L, t);
-      W4<R> v = ld_slot(slots, op.in[1], L, t);
+      W4<R> f = in_(0);
+      W4<R> v = in_(1);
       const R* pq = mt + 5 * op.mout;
       W4<R> j = fvi<R>(f, v, pq, pq[4], g);
-      st_slot(slots, op.out, L, t, j);
+      out_(j);
       return false;
     }
     case OP_FVO: {
-      W4<R> f = ld_slot(slots, op.in[0], L, t);
-      W4<R> v = ld_slot(slots, op.in[1], L, t);
+      W4<R> f = in_(0);
+      W4<R> v = in_(1);
       const R* pq = mt + 5 * op.mout;
       W4<R> j = fvo<R>(f, v, pq, pq[4], g);
-      st_slot(slots, op.out, L, t, j);
+      out_(j);
       return false;
     }
     case OP_JIO: {
-      W4<R> f = ld_slot(slots, op.in[0], L, t);
-      W4<R> o = ld_slot(slots, op.in[1], L, t);
+      W4<R> f = in_(0);
+      W4<R> o = in_(1);
       W4<R> j = jio<R>(f, o, mt[5 * op.mout + 4], g);
-      st_slot(slots, op.out, L, t, j);
+      out_(j);
       return false;
     }
     case OP_AVVV: {
-      W4<R> a = ld_slot(slots, op.in[0], L, t);
-      W4<R> b = ld_slot(slots, op.in[1], L, t);
-      W4<R> c = ld_slot(slots, op.in[2], L, t);
+      W4<R> a = in_(0);
+      W4<R> b = in_(1);
+      W4<R> c = in_(2);
       amp = vvv_amp<R>(a, b, c, mt + 5 * op.min[0], mt + 5 * op.min[1], mt + 5 * op.min[2], g);
       return true;
     }
     case OP_AGGGG: {
-      W4<R> a = ld_slot(slots, op.in[0], L, t);
-      W4<R> b = ld_slot(slots, op.in[1], L, t);
-      W4<R> c = ld_slot(slots, op.in[2], L, t);
-      W4<R> d = ld_slot(slots, op.in[3], L, t);
+      W4<R> a = in_(0);
+      W4<R> b = in_(1);
+      W4<R> c = in_(2);
+      W4<R> d = in_(3);
       amp = gggg_amp<R>(a, b, c, d, gg);
       return true;
     }
     case OP_AIOV: {
-      W4<R> f = ld_slot(slots, op.in[0], L, t);
-      W4<R> o = ld_slot(slots, op.in[1], L, t);
-      W4<R> v = ld_slot(slots, op.in[2], L, t);
+      W4<R> f = in_(0);
+      W4<R> o = in_(1);
+      W4<R> v = in_(2);
       amp = iov_amp<R>(f, o, v, g);
       return true;
     }
     case OP_ADOT: {  // diagram amplitude from its free wavefunction and the group's partial
-      W4<R> w = ld_slot(slots, op.in[0], L, t);
-      W4<R> p = ld_slot(slots, op.in[1], L, t);
+      W4<R> w = in_(0);
+      W4<R> p = in_(1);
       amp = part_contract<R>(w, p, (op.leg & 1u) != 0, (op.leg & 2u) != 0);
       return true;
     }
     case OP_PVVV: {
-      W4<R> b = ld_slot(slots, op.in[0], L, t);
-      W4<R> c = ld_slot(slots, op.in[1], L, t);
+      W4<R> b = in_(0);
+      W4<R> c = in_(1);
       W4<R> u = vvv_part<R>(b, c, mt + 5 * op.min[0], mt + 5 * op.min[1], mt + 5 * op.min[2], g);
-      st_slot(slots, op.out, L, t, u);
+      out_(u);
       return false;
     }
     case OP_PGGGG: {
-      W4<R> x = ld_slot(slots, op.in[0], L, t);
-      W4<R> y = ld_slot(slots, op.in[1], L, t);
-      W4<R> z = ld_slot(slots, op.in[2], L, t);
+      W4<R> x = in_(0);
+      W4<R> y = in_(1);
+      W4<R> z = in_(2);
       W4<R> u = gggg_part<R>(x, y, z, gg);
-      st_slot(slots, op.out, L, t, u);
+      out_(u);
       return false;
     }
     case OP_PIOV: {  // free fi: (fo, V); free fo: (fi, V); free V: (fi, fo)
-      W4<R> a = ld_slot(slots, op.in[0], L, t);
-      W4<R> b = ld_slot(slots, op.in[1], L, t);
+      W4<R> a = in_(0);
+      W4<R> b = in_(1);
       W4<R> u = op.leg == 0 ? iov_part_i<R>(a, b, g) : (op.leg == 1 ? iov_part_o<R>(a, b, g) : iov_part_v<R>(a, b, g));
-      st_slot(slots, op.out, L, t, u);
+      out_(u);
       return false;
     }
     default:
@@ -214,10 +233,11 @@ __device__ __forceinline__ bool eval_op(const Op& op, const DevProgram& P, R* sl
   return false;
 }
 
-template <typename R, bool JSMEM, bool SSMEM, bool AOUT>
+template <typename R, bool JSMEM, bool SSMEM, bool AOUT, bool FWD = false>
 __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, const AmpLaunch A,
                                                    const AmpConfig C) {
   static_assert(!AOUT || std::is_same<R, float>::value, "amplitude output is an FP32 path");
+  static_assert(!FWD || AOUT, "register forwarding is built for the amplitude-output path");
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr bool F32 = std::is_same<R, float>::value;
   constexpr int JW = F32 ? 4 : 2;  // FP32: hi re, hi im, lo re, lo im
@@ -328,12 +348,18 @@ __global__ void __launch_bounds__(kMaxThreads) amp_kernel(const DevProgram P, co
           }
         }
       };
+      W4<R> last;  // the previous op's output (FWD)
       for (int i = 0; i < P.n_ops; ++i) {
         OpWords w;
         w.v[0] = __ldg(&ops[i].v[0]);
         w.v[1] = __ldg(&ops[i].v[1]);
         cx<R> amp;
-        const bool is_amp = eval_op<R>(w.op, P, slots, L, t, et, mt, lam_bits, g, gg, amp);
+        bool is_amp;
+        if constexpr (FWD) {
+          is_amp = eval_op<R, true>(w.op, P, slots, L, t, et, mt, lam_bits, g, gg, amp, __ldg(P.fwd + i), &last);
+        } else {
+          is_amp = eval_op<R>(w.op, P, slots, L, t, et, mt, lam_bits, g, gg, amp);
+        }
         if (is_amp) take_amp(w.op.col_begin, w.op.col_count, amp);
       }
       if (AOUT) {
@@ -524,9 +550,11 @@ static AmpConfig plan_generated(const DevProgram& p, bool fp64, int H, int64_t n
 // share of the tiles alone.  Computed from the kernel's register count
 // (cudaFuncGetAttributes, read only): planning may run on any host thread
 // while another launches these kernels, so it changes no function attribute.
-static int interp_resident(bool fp64, bool jsm, bool ssm, bool aout, int threads) {
+static int interp_resident(bool fp64, bool jsm, bool ssm, bool aout, int threads, bool fwd = false) {
   const void* k;
-  if (aout) k = ssm ? (const void*)amp_kernel<float, true, true, true> : (const void*)amp_kernel<float, true, false, true>;
+  if (aout && fwd)
+    k = ssm ? (const void*)amp_kernel<float, true, true, true, true> : (const void*)amp_kernel<float, true, false, true, true>;
+  else if (aout) k = ssm ? (const void*)amp_kernel<float, true, true, true> : (const void*)amp_kernel<float, true, false, true>;
   else if (fp64)
     k = jsm ? (ssm ? (const void*)amp_kernel<double, true, true, false> : (const void*)amp_kernel<double, true, false, false>)
             : (ssm ? (const void*)amp_kernel<double, false, true, false> : (const void*)amp_kernel<double, false, false, false>);
@@ -616,6 +644,15 @@ AmpConfig plan_amp(const DevProgram& p, bool fp64, int H, int64_t n_events, int 
                      : smem_bytes<float>(p, best.threads, 1, false, false);
     best.grid = num_sms;
   }
+  if (p.fwd_only && p.fwd && p.n_colour == 0 && !fp64) {
+    // forwarding only: the same tile, within the forwarding kernel's residency
+    best.fwd = true;
+    const int rf = interp_resident(false, true, best.slots_in_smem, true, best.threads, true);
+    if (rf >= 1 && rf < best.per_sm) {
+      best.per_sm = rf;
+      best.grid = rf * num_sms;
+    }
+  }
   int64_t tiles = (n_events + best.E_cta - 1) / best.E_cta;
   if (tiles < best.grid) best.grid = (int)std::max<int64_t>(tiles, 1);
   return best;
@@ -690,7 +727,18 @@ std::vector<AmpConfig> candidate_configs(const DevProgram& p, bool fp64, int H, 
       c.jamp_in_smem = pl[0] != 0; c.slots_in_smem = pl[1] != 0;
       c.grid = per_sm * num_sms;
       c.per_sm = per_sm;
-      out.push_back(cap(c));
+      if (!p.fwd_only) out.push_back(cap(c));
+      if (p.fwd && p.n_colour == 0 && !fp64) {
+        // the same tile with the previous op's output forwarded in registers
+        AmpConfig f = c;
+        f.fwd = true;
+        const int rf = interp_resident(false, true, pl[1] != 0, true, threads, true);
+        if (rf >= 1) {
+          f.per_sm = std::min(per_sm, rf);
+          f.grid = f.per_sm * num_sms;
+          out.push_back(cap(f));
+        }
+      }
       // with slots in global memory, fewer resident lanes per SM leave each lane
       // more of the L1 and L2 for its wavefunction slots (fewer DRAM trips)
       // against less latency hiding: the tuner times both sides
@@ -736,15 +784,15 @@ int carveout_percent(const AmpConfig& c) {
   return std::max(0, std::min(100, (int)std::ceil(100.0 * need / smem_sm) + 1));
 }
 
-template <typename R, bool J, bool S, bool O = false>
+template <typename R, bool J, bool S, bool O = false, bool F = false>
 static cudaError_t launch_one(const DevProgram& p, const AmpConfig& c, const AmpLaunch& a, cudaStream_t s) {
-  cudaError_t e = ensure_dynamic_smem((const void*)amp_kernel<R, J, S, O>, c.smem);
+  cudaError_t e = ensure_dynamic_smem((const void*)amp_kernel<R, J, S, O, F>, c.smem);
   if (e != cudaSuccess) return e;
   // the carveout is a preference: a value the driver refuses leaves the launch valid
-  if (cudaFuncSetAttribute(amp_kernel<R, J, S, O>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  if (cudaFuncSetAttribute(amp_kernel<R, J, S, O, F>, cudaFuncAttributePreferredSharedMemoryCarveout,
                            carveout_percent(c)) != cudaSuccess)
     cudaGetLastError();
-  amp_kernel<R, J, S, O><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
+  amp_kernel<R, J, S, O, F><<<c.grid, c.threads, c.smem, s>>>(p, a, c);
   return cudaGetLastError();
 }
 
@@ -763,7 +811,13 @@ cudaError_t launch_amp(const DevProgram& p, bool fp64, const AmpConfig& c, const
   if (a.amp_out) {
     // diagram amplitudes out (no colour accumulators): FP32 interpreter only
     if (fp64 || p.n_colour != 0) return cudaErrorInvalidValue;
-    err = c.slots_in_smem ? launch_one<float, true, true, true>(p, c, a, s) : launch_one<float, true, false, true>(p, c, a, s);
+    if (c.fwd) {
+      if (!p.fwd) return cudaErrorInvalidValue;
+      err = c.slots_in_smem ? launch_one<float, true, true, true, true>(p, c, a, s)
+                            : launch_one<float, true, false, true, true>(p, c, a, s);
+    } else {
+      err = c.slots_in_smem ? launch_one<float, true, true, true>(p, c, a, s) : launch_one<float, true, false, true>(p, c, a, s);
+    }
   } else if (p.gen) {
     p.gen->launch(fp64, c.regvar, p, c, a, s);
     err = cudaGetLastError();

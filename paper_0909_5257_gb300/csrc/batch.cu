@@ -204,7 +204,7 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
     for (auto& f : full)
       if (f.E_cta == c.E_cta && f.threads == c.threads && f.jamp_in_smem == c.jamp_in_smem &&
           f.slots_in_smem == c.slots_in_smem && f.regvar == c.regvar && f.per_sm == c.per_sm &&
-          f.helshare == c.helshare && f.hsplit == c.hsplit)
+          f.helshare == c.helshare && f.hsplit == c.hsplit && f.fwd == c.fwd)
         c.grid = f.grid;
     P->tuned[ti] = c;
     P->tuned_H[ti] = H;
@@ -224,6 +224,7 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
     out->register_cap = dp.gen ? (fp64 ? 128 : mea::kGenCapRegisters[c.regvar / 2]) : ((c.helshare && c.regvar == 0) ? 64 : 0);
     out->vertex_partials = (dp.gen && !fp64 && (c.regvar & 1)) ? 0 : 1;
     out->helicity_shared = c.helshare ? 1 : (c.hsplit ? 2 : 0);
+    out->forwarding = c.fwd ? 1 : 0;
   }
   return MEA_OK;
 }

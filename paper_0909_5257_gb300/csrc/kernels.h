@@ -63,6 +63,11 @@ struct DevProgram {
   int hsp_n_main = 0;
   int hsp_area = 0;                     // prologue variants per event
   bool hsp_only = false;                // amplitude-output mode: plan and tune the split kernel only
+  // per op: bits 0..3 input k is the previous op's output, bit 4 the op's
+  // output is read only by the next op (amplitude-output interpreter with
+  // register forwarding), or null
+  const uint8_t* fwd = nullptr;
+  bool fwd_only = false;                // amplitude-output interpreter: plan and tune with forwarding only
 };
 
 struct AmpLaunch {
@@ -98,6 +103,7 @@ struct AmpConfig {
   bool slots_in_smem = true;
   int regvar = 0;  // straight-line kernels: variant, 2 * cap + body (see GenEntry)
   int per_sm = 1;  // CTAs meant to be resident per SM (sets the shared-memory carveout)
+  bool fwd = false;       // amplitude-output interpreter: the previous op's output forwarded in registers
   bool hsplit = false;    // amplitude-output mode: the split kernel (amp_hsp_kernel, amp_hs_kernel.cu):
                           // E_cta events x H lanes; slots_in_smem = its prologue area in shared memory
   bool helshare = false;  // amplitude-output mode: the helicity-shared kernel (amp_hs_kernel.cu):

@@ -56,7 +56,8 @@ class TuneResult(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("events_per_cta", ctypes.c_int), ("grid", ctypes.c_int),
                 ("colour_amps_in_shared", ctypes.c_int), ("slots_in_shared", ctypes.c_int),
                 ("candidates", ctypes.c_int), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
-                ("register_cap", ctypes.c_int), ("vertex_partials", ctypes.c_int), ("helicity_shared", ctypes.c_int)]
+                ("register_cap", ctypes.c_int), ("vertex_partials", ctypes.c_int), ("helicity_shared", ctypes.c_int),
+                ("forwarding", ctypes.c_int)]
 
 
 class BatchItem(ctypes.Structure):

@@ -110,7 +110,7 @@ def test_kernel_variant_out_of_range_is_an_argument_error():
 def test_helicity_sharing_option_out_of_range_is_an_argument_error():
     """mea_options.helicity_sharing is checked before any device work."""
     from paper_0909_5257_gb300 import mea
-    for v in (-1, 4):
+    for v in (-1, 5):
         with pytest.raises(mea.MeaError) as e:
             mea.Process([21] * 6, helicity_sharing=v)
         assert e.value.status == -1

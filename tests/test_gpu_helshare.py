@@ -6,7 +6,8 @@ event and helicity combination), as the helicity-shared kernel (one warp per
 event, every wavefunction evaluated once per helicity pattern of its own
 legs) or as the split kernel (the wavefunctions of up to n_ext - 3 legs
 shared that way in a prologue, the rest per lane with one transient current
-in registers).  All apply the same HELAS operations to the same inputs, so
+in registers); the per-lane interpreter also with each op's output forwarded
+to the next op in registers (mode 4).  All apply the same HELAS operations to the same inputs, so
 every diagram amplitude, and with it |M|^2 and the flags, is the same bit for
 bit:
 checked here for the serving processes and g g -> 4g, for the non-zero and
@@ -60,7 +61,7 @@ def test_helicity_shared_equals_per_lane_bit_for_bit(name, pdg, rs, n, chunk):
     lane = mea.Process(pdg, helicity_sharing=1, auto_tune=False, chunk_events=chunk)
     a, fa = _run(lane, mom)
     assert torch.isfinite(a).all()
-    for mode in (2, 3):
+    for mode in (2, 3, 4):
         other = mea.Process(pdg, helicity_sharing=mode, auto_tune=False, chunk_events=chunk)
         b, fb = _run(other, mom)
         assert torch.equal(a, b), (name, mode, float(((a - b).abs() / a.abs()).max()))
@@ -90,7 +91,7 @@ def test_helicity_shared_full_helicity_sum():
     mom = _events(pdg, (300.0, 3000.0), 333, ps.SEED_BASE + 612)
     lane = mea.Process(pdg, helicity_sharing=1, auto_tune=False)
     a, _ = _run(lane, mom, hel_mode=mea.HEL_SUM_ALL)
-    for mode in (2, 3):
+    for mode in (2, 3, 4):
         shared = mea.Process(pdg, helicity_sharing=mode, auto_tune=False)
         b, _ = _run(shared, mom, hel_mode=mea.HEL_SUM_ALL)
         assert torch.equal(a, b), mode
