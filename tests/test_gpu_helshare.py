@@ -1,4 +1,4 @@
-"""The helicity-shared amplitude kernel (amp_hs_kernel.cu) on the GPU.
+"""The shared and forwarding amplitude kernels (amp_hs_kernel.cu, amp_kernel.cu) on the GPU.
 
 On the tensor-core path (mixed precision, processes without a straight-line
 kernel) the amplitude stage can run as the per-lane interpreter (one lane per
@@ -12,8 +12,8 @@ every diagram amplitude, and with it |M|^2 and the flags, is the same bit for
 bit:
 checked here for the serving processes and g g -> 4g, for the non-zero and
 the full helicity sums, across several chunks with a ragged tail and after
-autotuning.  Parity with the oracle of the default (helicity-shared) path is
-in test_gpu_parity.py and test_gpu_5jet_golden.py.
+autotuning.  Parity with the oracle of the tuned default path is in
+test_gpu_parity.py and test_gpu_5jet_golden.py.
 """
 import numpy as np
 import pytest
