@@ -177,11 +177,27 @@ mea_status autotune_locked(mea_process_s* P, const double* mom, int64_t n, mea_p
     std::vector<int> again{0};
     for (size_t r = 0; r < order.size() && again.size() < 4; ++r)
       if (order[r].second != 0 && order[r].first < 1e30) again.push_back(order[r].second);
+    // the fastest tile without register forwarding is also timed again: a
+    // forwarding tile must beat it clearly (the sample is one evaluation chunk;
+    // the serving loop's chunks are smaller and run side by side, where a
+    // forwarding tile faster by under 1 % on the sample measured slower)
+    for (size_t r = 0; r < order.size(); ++r)
+      if (order[r].first < 1e30 && !cands[order[r].second].fwd) {
+        if (std::find(again.begin(), again.end(), order[r].second) == again.end()) again.push_back(order[r].second);
+        break;
+      }
     best = 1e30;
+    double best_plain = 1e30;
+    int plain_i = -1;
     for (int i : again) {
       const double t = time_cand((size_t)i, 5);
       if (i == 0) def_ms = t;
       if (t < best) { best = t; best_i = i; }
+      if (!cands[i].fwd && t < best_plain) { best_plain = t; plain_i = i; }
+    }
+    if (cands[best_i].fwd && plain_i >= 0 && best_plain <= best * 1.03) {
+      best = best_plain;
+      best_i = plain_i;
     }
   }
   S.release();
