@@ -561,24 +561,8 @@ mea_status mea_create_process(const int* pdg, int n_ext, const mea_options* opts
   }
   if (P->jmap.ok && P->opts.helicity_sharing != 2 && P->opts.helicity_sharing != 3) {
     D.fwd_only = P->opts.helicity_sharing == 4;
-    // register forwarding for the amplitude-output interpreter: an input that
-    // the previous op produced (bit k), an output read only by the next op (bit 4)
-    const int n_ops = (int)G.ops.size();
-    std::vector<uint8_t> fw(n_ops, 0);
-    std::vector<int> holder(G.n_slots, -1), reads(n_ops, 0), last_read(n_ops, -1);
-    for (int i = 0; i < n_ops; ++i) {
-      const mea::Op& op = G.ops[i];
-      const int n_in = op.type == mea::OP_EXT ? 0 : op.n_in;
-      const bool prev_out = i > 0 && !mea::is_amp_op(G.ops[i - 1].type);
-      for (int k = 0; k < n_in; ++k) {
-        const int src = holder[op.in[k]];
-        if (src >= 0) { ++reads[src]; last_read[src] = i; }
-        if (prev_out && src == i - 1) fw[i] |= (uint8_t)(1u << k);
-      }
-      if (!mea::is_amp_op(op.type)) holder[op.out] = i;
-    }
-    for (int i = 0; i + 1 < n_ops; ++i)
-      if (!mea::is_amp_op(G.ops[i].type) && reads[i] == 1 && last_read[i] == i + 1) fw[i] |= 16u;
+    // register forwarding for the amplitude-output interpreter (helshare.h)
+    const std::vector<uint8_t> fw = mea::build_forwarding_flags(G);
     const uint8_t* dfw = nullptr;
     if ((e = upload(P, fw, &dfw)) != cudaSuccess) {
       destroy(P);

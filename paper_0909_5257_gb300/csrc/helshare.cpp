@@ -105,6 +105,29 @@ HsProgram build_helicity_shared(const Program& P, int H) {
   return Q;
 }
 
+std::vector<uint8_t> build_forwarding_flags(const Program& P) {
+  const int n_ops = (int)P.ops.size();
+  std::vector<uint8_t> fw(n_ops, 0);
+  std::vector<int> holder(P.n_slots, -1), reads(n_ops, 0), last_read(n_ops, -1);
+  for (int i = 0; i < n_ops; ++i) {
+    const Op& op = P.ops[i];
+    const int n_in = op.type == OP_EXT ? 0 : op.n_in;
+    const bool prev_out = i > 0 && !is_amp_op(P.ops[i - 1].type);
+    for (int k = 0; k < n_in; ++k) {
+      const int src = holder.at(op.in[k]);
+      if (src >= 0) {
+        ++reads[src];
+        last_read[src] = i;
+      }
+      if (prev_out && src == i - 1) fw[i] |= (uint8_t)(1u << k);
+    }
+    if (!is_amp_op(op.type)) holder.at(op.out) = i;
+  }
+  for (int i = 0; i + 1 < n_ops; ++i)
+    if (!is_amp_op(P.ops[i].type) && reads[i] == 1 && last_read[i] == i + 1) fw[i] |= 16u;
+  return fw;
+}
+
 HsSplitProgram build_split_shared(const Program& P, int H) {
   if (P.n_ext > 8 || P.n_ext < 5) throw std::runtime_error("split sharing: 5 to 8 legs");
   const int n_ops = (int)P.ops.size();

@@ -81,4 +81,10 @@ struct HsSplitProgram {
 // variants.
 HsSplitProgram build_split_shared(const Program& P, int H);
 
+// Register forwarding in the per-lane interpreter: per op, bit k (0..3) when
+// input k is the output of the op just before (read from the register that
+// holds it), bit 4 when the op's output is read by nothing but the next op
+// (kept in that register only, never stored to its slot).
+std::vector<uint8_t> build_forwarding_flags(const Program& P);
+
 }  // namespace mea

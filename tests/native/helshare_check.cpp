@@ -13,8 +13,9 @@
 // helicity pattern, level by level; the rest per combination with one
 // transient current) is checked the same way.  Prints per process: name,
 // amplitudes compared, mismatches, arena variants, and the same for the split
-// layout (area variants; -1 for processes of 4 legs); exit status 1 on any
-// mismatch.
+// layout (area variants; -1 for processes of 4 legs), and for the per-lane
+// evaluation with register forwarding (skipped stores poisoned); exit status
+// 1 on any mismatch.
 #define MEA_HD inline
 #include <cmath>
 #include <cstdint>
@@ -228,9 +229,41 @@ int main(int argc, char** argv) {
         if (dd != P.n_diagrams) { std::printf("split: %d amplitudes, %d diagrams\n", dd, P.n_diagrams); bad = 1; }
       }
     }
-    if (mismatched || split_mismatched) bad = 1;
-    std::printf("%s %lld %lld %d %lld %lld %d\n", argv[a], (long long)compared, (long long)mismatched, Q.arena,
-                (long long)split_compared, (long long)split_mismatched, split_area);
+    // per combination through the slots with register forwarding: a skipped
+    // store leaves its slot poisoned (NaN), so a read of it anywhere but from
+    // the register changes the amplitude
+    int64_t fwd_compared = 0, fwd_mismatched = 0;
+    {
+      const std::vector<uint8_t> fw = build_forwarding_flags(P);
+      const double qnan = std::nan("");
+      for (int h = 0; h < P.n_hel; ++h) {
+        std::vector<W4<double>> slots(P.n_slots);
+        for (auto& w : slots)
+          for (int k = 0; k < 4; ++k) w.c[k] = {qnan, qnan};
+        W4<double> last;
+        for (int k = 0; k < 4; ++k) last.c[k] = {qnan, qnan};
+        int dd = 0;
+        for (int i = 0; i < n_ops; ++i) {
+          const Op& op = P.ops[i];
+          W4<double> x[4];
+          const int n_in = op.type == OP_EXT ? 0 : op.n_in;
+          for (int k = 0; k < n_in; ++k) x[k] = (fw[i] >> k & 1u) ? last : slots[op.in[k]];
+          if (is_amp_op(op.type)) {
+            const cx<double> z = amplitude(op, x, in);
+            const cx<double>& r = ref[(size_t)h * P.n_diagrams + dd++];
+            ++fwd_compared;
+            if (std::memcmp(&z, &r, sizeof(z)) != 0) ++fwd_mismatched;
+          } else {
+            last = produce(op, x, in, lam[h]);
+            if (!(fw[i] & 16u)) slots[op.out] = last;
+          }
+        }
+      }
+    }
+    if (mismatched || split_mismatched || fwd_mismatched) bad = 1;
+    std::printf("%s %lld %lld %d %lld %lld %d %lld %lld\n", argv[a], (long long)compared, (long long)mismatched, Q.arena,
+                (long long)split_compared, (long long)split_mismatched, split_area, (long long)fwd_compared,
+                (long long)fwd_mismatched);
   }
   return bad;
 }

@@ -59,7 +59,8 @@ def test_helicity_shared_layout_gives_the_per_lane_amplitudes(tmp_path):
     amplitude of every summed helicity combination bit for bit as the
     per-combination evaluation through the program's slots (host, FP64, random
     inputs); every block lies in its arena and no op's output block overlaps
-    its inputs."""
+    its inputs.  So does the per-combination evaluation with register
+    forwarding, its skipped stores leaving their slots NaN."""
     cxx = shutil.which("g++")
     if cxx is None:
         pytest.skip("no host C++ compiler")
@@ -74,8 +75,9 @@ def test_helicity_shared_layout_gives_the_per_lane_amplitudes(tmp_path):
     assert r.returncode == 0, r.stdout + r.stderr
     rows = [line.split() for line in r.stdout.splitlines()]
     assert [row[0] for row in rows] == procs
-    for name, compared, mismatched, arena, s_compared, s_mismatched, s_area in rows:
+    for name, compared, mismatched, arena, s_compared, s_mismatched, s_area, f_compared, f_mismatched in rows:
         assert int(compared) > 0 and int(mismatched) == 0, name
+        assert int(f_compared) == int(compared) and int(f_mismatched) == 0, name
         if len(name.split(",")) >= 5:
             assert int(s_compared) == int(compared) and int(s_mismatched) == 0, name
     # g g -> 5g: 112 combinations x 7245 diagrams compared; prologue area of
