@@ -70,7 +70,10 @@ def test_helicity_shared_layout_gives_the_per_lane_amplitudes(tmp_path):
                     os.path.join(CSRC, "generator.cpp"), os.path.join(CSRC, "helshare.cpp")], check=True)
     procs = ["21,21,21,21", "2,-2,21,21", "21,21,21,21,21", "2,2,2,2,21", "21,21,21,21,21,21",
              "2,-2,21,21,21,21", "2,2,2,2,21,21", "2,2,2,2,21,21,21", "2,-2,21,21,21,21,21",
-             "21,21,21,21,21,21,21", "2,21,2,21,21", "2,-2,1,-1,21"]
+             "21,21,21,21,21,21,21", "2,21,2,21,21", "2,-2,1,-1,21",
+             # crossings and other flavours
+             "2,1,2,1,21", "2,-2,2,-2,21", "-1,-1,-1,-1,21", "21,2,2,21,21", "2,21,2,21",
+             "2,21,2,21,21,21", "2,1,2,1,21,21", "2,-2,1,-1,21,21"]
     r = subprocess.run([exe] + procs, capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     rows = [line.split() for line in r.stdout.splitlines()]
