@@ -93,7 +93,14 @@ static cx<double> amplitude(const Op& op, const W4<double>* x, const Inputs& in)
 
 int main(int argc, char** argv) {
   int bad = 0;
+  // --all: every one of the 2^n_ext helicity combinations (the full helicity
+  // sum), not only those the selection rules keep
+  bool all = false;
   for (int a = 1; a < argc; ++a) {
+    if (std::string(argv[a]) == "--all") {
+      all = true;
+      continue;
+    }
     std::vector<int> pdg;
     std::string s = argv[a];
     for (size_t p = 0; p < s.size();) {
@@ -123,14 +130,16 @@ int main(int argc, char** argv) {
       for (int m = 0; m < 4; ++m) in.mt[5 * r + m] = q[m];
       in.mt[5 * r + 4] = 1.0 / (q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3]);
     }
-    std::vector<uint32_t> lam(P.n_hel);
-    for (int h = 0; h < P.n_hel; ++h)
+    const int n_hel = all ? (1 << P.n_ext) : P.n_hel;
+    const std::vector<int8_t>& hel = all ? P.hel_all : P.hel;
+    std::vector<uint32_t> lam(n_hel);
+    for (int h = 0; h < n_hel; ++h)
       for (int l = 0; l < P.n_ext; ++l)
-        if (P.hel[h * P.n_ext + l] > 0) lam[h] |= 1u << l;
+        if (hel[h * P.n_ext + l] > 0) lam[h] |= 1u << l;
 
     // per combination through the slots
-    std::vector<cx<double>> ref((size_t)P.n_hel * P.n_diagrams);
-    for (int h = 0; h < P.n_hel; ++h) {
+    std::vector<cx<double>> ref((size_t)n_hel * P.n_diagrams);
+    for (int h = 0; h < n_hel; ++h) {
       std::vector<W4<double>> slots(P.n_slots);
       int d = 0;
       for (const Op& op : P.ops) {
@@ -175,7 +184,7 @@ int main(int argc, char** argv) {
           arena[q.out_off + v] = produce(op, x, in, lf);
         }
       } else {
-        for (int h = 0; h < P.n_hel; ++h) {
+        for (int h = 0; h < n_hel; ++h) {
           W4<double> x[4];
           for (int k = 0; k < n_in; ++k) x[k] = arena[q.in_off[k] + pext(lam[h], q.in_mask[k])];
           const cx<double> z = amplitude(op, x, in);
@@ -208,7 +217,7 @@ int main(int argc, char** argv) {
         if (q.out_off + (1 << __builtin_popcount(q.out_mask)) > S.area) { std::printf("prologue block outside\n"); bad = 1; continue; }
         area[q.out_off + v] = produce(op, x, in, lf);
       }
-      for (int h = 0; h < P.n_hel; ++h) {
+      for (int h = 0; h < n_hel; ++h) {
         W4<double> tr;
         int dd = 0;
         for (size_t j = 0; j < S.main_ops.size(); ++j) {
@@ -236,7 +245,7 @@ int main(int argc, char** argv) {
     {
       const std::vector<uint8_t> fw = build_forwarding_flags(P);
       const double qnan = std::nan("");
-      for (int h = 0; h < P.n_hel; ++h) {
+      for (int h = 0; h < n_hel; ++h) {
         std::vector<W4<double>> slots(P.n_slots);
         for (auto& w : slots)
           for (int k = 0; k < 4; ++k) w.c[k] = {qnan, qnan};

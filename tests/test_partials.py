@@ -86,3 +86,12 @@ def test_helicity_shared_layout_gives_the_per_lane_amplitudes(tmp_path):
     # g g -> 5g: 112 combinations x 7245 diagrams compared; prologue area of
     # the wavefunctions of up to 4 legs
     assert int(rows[9][1]) == 112 * 7245 and int(rows[9][6]) == 16180
+    # the full helicity sum: every one of the 2^n combinations, the vanishing ones included
+    full = ["21,21,21,21,21,21", "2,-2,21,21,21,21,21", "21,21,21,21,21,21,21", "2,2,2,2,21,21,21"]
+    r = subprocess.run([exe, "--all"] + full, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    for line, name in zip(r.stdout.splitlines(), full):
+        f = line.split()
+        n_ext = len(name.split(","))
+        assert f[0] == name and int(f[1]) % (1 << n_ext) == 0
+        assert int(f[2]) == int(f[5]) == int(f[8]) == 0 and int(f[1]) == int(f[4]) == int(f[7]), line
